@@ -1,0 +1,24 @@
+"""FP64 CPU oracle for the TT-UTV sweep -- TEST INFRASTRUCTURE ONLY.
+
+This package is a plain, slow, deliberately unoptimised restatement of the
+paper's method ("Effective algorithms for tensor-train decomposition via the
+UTV framework", arXiv 2501.07904) in numpy FP64.  It exists to check the CUDA
+path.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it; the library itself never does, and it shares no
+code with the CUDA path (only the seeded input generators in ``synth`` are
+common to both).
+
+Modules
+-------
+linalg  Householder QR (optionally column-pivoted) and one-sided Jacobi SVD.
+philox  Philox4x32-10 counter-based generator and the Rademacher sketch matrix.
+tt      TT format (Eq. TT), TT-ULV (Alg. 1/2), TT-URV (Alg. 3 and its
+        prescribed-accuracy analogue), TT-SVD, masked evaluation and gradients.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``
+against closed forms, LAPACK, brute force or the paper's Table (tab: Beps),
+except ``philox`` (no published vectors are used; pinned only by statistical
+properties and cross-implementation equality) -- parity unpinned for the exact
+bit stream of ``philox``.
+"""
+from . import linalg, philox, tt  # noqa: F401

@@ -1,0 +1,310 @@
+"""TT-UTV, TT-SVD and masked TT evaluation in plain FP64 (test infrastructure only).
+
+Notation follows the paper (arXiv 2501.07904): A in R^{I_1 x ... x I_d}, TT
+cores G^(k) in R^{r_{k-1} x I_k x r_k} with r_0 = r_d = 1 (Eq. TT), unfoldings
+A_k (Def. 2.1), ULV / URV decompositions (Eqs. ulv, urv), Algorithm 1/2
+(TT-ULV, left-to-right) and Algorithm 3 (TT-URV, right-to-left) with the
+prescribed-accuracy rule of Sec. 3.1 (smallest r_k with ||E||_F <= eps_k,
+eps_k = w_k eps ||A||_F).
+
+Storage is row-major (C order): the paper's reverse-lexicographic ivec only
+permutes the rows and columns of every unfolding, which leaves singular
+values, ranks, truncation errors and the represented tensor unchanged.
+
+Readings where the paper is silent (each listed in the design doc):
+
+* inner UTV (the paper names the family, Sec. 2.2): a range step (identity
+  when the basis side has <= l_full columns, else a Rademacher sketch
+  Y = X^T Omega, W = Householder-QR(Y).Q, B = X W), then Stewart's pivoted QLP
+  of B (pivoted QR of B, pivoted QR of R_1^T, L = R_2^T, Z = Pi_1 Q_2), then a
+  QR of L for the URV form (T upper).  Truncation error for rank r:
+  tail(r) = mu^2 + sum_{j>r} ||L(:,j)||^2, mu^2 = ||X - B W^T||_F^2.
+* TT-SVD: the same range step and pivoted QR, then one-sided Jacobi on R_1.
+* rank rule: smallest r >= 1 with tail(r) <= delta^2 (<= passes); fixed ranks
+  are clamped to the size of the factored matrix.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .linalg import householder_qr, jacobi_svd
+from .philox import rademacher
+
+L_FULL = 256
+OVERSAMPLE = 16
+
+
+def _roundup(x, m):
+    return ((x + m - 1) // m) * m
+
+
+def sketch_size(n_basis, n_other, r_prev, p=OVERSAMPLE, fixed_r=None):
+    """Number of sketch columns l (reading S9): r+p for a fixed rank, else
+    roundup16(max(2 r_prev, r_prev + p, 32)); never more than either side."""
+    if fixed_r is not None:
+        l = fixed_r + p
+    else:
+        l = _roundup(max(2 * r_prev, r_prev + p, 32), 16)
+    return int(min(l, n_basis, n_other))
+
+
+def range_step(X, l, seed, step):
+    """Range of the basis side of X (N_o x N_b): returns (W, B, mu2).
+
+    l >= N_o uses Omega = I (the sketch then spans the whole row space);
+    otherwise Omega is the Philox Rademacher matrix of this step.
+    """
+    n_o, n_b = X.shape
+    if l >= n_o:
+        Y = X.T.copy()
+    else:
+        Y = X.T @ rademacher(n_o, l, seed, step)
+    W, _, _ = householder_qr(Y)
+    B = X @ W
+    E = X - B @ W.T
+    mu2 = float(np.sum(E * E))
+    return W, B, mu2
+
+
+def qlp(B):
+    """Pivoted QLP of B (N_o x N'): B = (Q_1 Pi_2) L (Pi_1 Q_2)^T (Stewart, cited in Sec. 2.2).
+
+    Returns (Z, L, Q1P2) with Z = Pi_1 Q_2 (N' x N' orthogonal) and L lower
+    trapezoidal (k x N', k = min(N_o, N')).
+    """
+    Q1, R1, p1 = householder_qr(B, pivoting=True)
+    Q2, R2, p2 = householder_qr(R1.T, pivoting=True, full_q=True)
+    L = R2.T                                   # k x N', L[:, j] = R2[j, :]
+    Z = np.empty_like(Q2)
+    Z[p1, :] = Q2
+    Q1P2 = Q1[:, p2]                           # (Q_1 Pi_2)[:, j] = Q_1[:, p2[j]]
+    return Z, L, Q1P2
+
+
+def utv_of(X, variant="URV"):
+    """Full rank-revealing UTV of a matrix via pivoted QLP (the exact path, no sketch).
+
+    URV: X = U T V^T with T upper trapezoidal (QR of L, T = R_3).
+    ULV: computed as the URV of X^T, transposed, so T is lower.
+    Returns (U, T, V).
+    """
+    if variant == "ULV":
+        U, T, V = utv_of(X.T, "URV")
+        return V, T.T, U
+    Z, L, Q1P2 = qlp(X)
+    Q3, R3, _ = householder_qr(L)
+    return Q1P2 @ Q3, R3, Z
+
+
+def qlp_tails(L):
+    """tail_B(r) = sum_{j>=r} ||L(:,j)||^2 for r = 0..N' (length N'+1)."""
+    c = np.sum(L * L, axis=0)
+    return np.concatenate([np.cumsum(c[::-1])[::-1], [0.0]])
+
+
+def choose_rank(tails, delta2, r_fixed, r_max):
+    """Reading S3 of the rule in Sec. 3.1: smallest r >= 1 with tail(r) <= delta^2."""
+    if r_fixed is not None:
+        return int(max(1, min(r_fixed, r_max)))
+    for r in range(1, r_max + 1):
+        if tails[r] <= delta2:
+            return r
+    return r_max
+
+
+def factor_step(X, delta2, r_fixed, r_prev, seed, step, kind="qlp",
+                l_full=L_FULL, p=OVERSAMPLE):
+    """One truncated UTV of X (N_o x N_b, basis on the column side).
+
+    Returns dict(r, basis (N_b x r), carry (N_o x r) = X basis, tail, l, path).
+    The truncation residual E = X - carry basis^T satisfies E basis = 0, and
+    ||E||_F^2 = tail (EV_1 = 0 for URV, U_1^T E = 0 for ULV: Sec. 3.1-3.2).
+    """
+    n_o, n_b = X.shape
+    if n_b <= l_full or (kind == "svd" and n_b <= n_o):
+        W, B, mu2, l, path = None, X, 0.0, n_b, "exact"
+    elif kind == "svd":
+        # TT-SVD takes no random sketch: the identity range (l = N_o) is exact
+        l, path = n_o, "sketch"
+    else:
+        l = sketch_size(n_b, n_o, r_prev, p, r_fixed)
+        path = "sketch"
+    while True:
+        if path == "sketch":
+            W, B, mu2 = range_step(X, l, seed, step)
+        if kind == "qlp":
+            Z, L, _ = qlp(B)
+            tails = mu2 + qlp_tails(L)
+        else:
+            _, R1, p1 = householder_qr(B, pivoting=True)
+            sig, VJ = jacobi_svd(R1)
+            Z = np.empty_like(VJ)
+            Z[p1, :] = VJ
+            s2 = sig * sig
+            tails = mu2 + np.concatenate([np.cumsum(s2[::-1])[::-1], [0.0]])
+        r_max = min(Z.shape[1], n_o, n_b)
+        tails = tails[: r_max + 1]
+        r = choose_rank(tails, delta2, r_fixed, r_max)
+        can_grow = (path == "sketch" and kind == "qlp" and l < min(n_b, n_o)
+                    and r_fixed is None)
+        if can_grow and (r > l - p or tails[r] > delta2):
+            l = min(2 * l, n_b, n_o)
+            continue
+        break
+    Z1 = Z[:, :r]
+    basis = Z1 if W is None else W @ Z1
+    carry = B @ Z1
+    return dict(r=r, basis=basis, carry=carry, tail=float(tails[r]), l=l, path=path,
+                tails=tails)
+
+
+def _weights(d, weights):
+    if weights is None:
+        return np.full(d - 1, 1.0 / math.sqrt(d - 1))
+    w = np.asarray(weights, dtype=np.float64)
+    assert w.shape == (d - 1,)
+    return w
+
+
+def tt_sweep(A, eps=None, ranks=None, variant="URV", kind="qlp", direction=None,
+             weights=None, l_full=L_FULL, p=OVERSAMPLE, seed=0):
+    """TT decomposition by a sweep of truncated UTVs.
+
+    variant 'URV' -> right-to-left (Alg. 3), right-orthogonal cores;
+    variant 'ULV' -> left-to-right (Alg. 1/2), left-orthogonal cores;
+    kind 'svd' turns either sweep into TT-SVD (direction from ``direction``).
+    Exactly one of ``eps`` (prescribed accuracy, eps_k = w_k eps ||A||_F) or
+    ``ranks`` (r_1..r_{d-1}) is given.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    dims = A.shape
+    d = len(dims)
+    assert d >= 2
+    if direction is None:
+        direction = "RL" if variant == "URV" else "LR"
+    assert (eps is None) != (ranks is None)
+    normA2 = float(np.sum(A * A))
+    w = _weights(d, weights)
+    cores = [None] * d
+    rk = [1] * (d + 1)
+    tails = [0.0] * (d - 1)          # indexed by unfolding number k-1 (k = 1..d-1)
+    steps = []
+    r_prev = 0
+
+    def delta2_of(u):                # u = unfolding number 1..d-1
+        if eps is None:
+            return None
+        return (w[u - 1] * eps) ** 2 * normA2
+
+    def fixed_of(u):
+        return None if ranks is None else int(ranks[u - 1])
+
+    if direction == "RL":
+        C = A.reshape(-1, dims[-1])
+        r_next = 1
+        for k in range(d, 1, -1):
+            m = int(np.prod(dims[: k - 1]))
+            n = dims[k - 1] * r_next
+            C = C.reshape(m, n)
+            u = k - 1
+            st = factor_step(C, delta2_of(u) if eps is not None else 0.0, fixed_of(u), r_prev,
+                             seed, k, kind, l_full, p)
+            r = st["r"]
+            cores[k - 1] = st["basis"].T.reshape(r, dims[k - 1], r_next)
+            C = st["carry"]
+            rk[k - 1] = r
+            tails[u - 1] = st["tail"]
+            steps.append(dict(k=k, m=m, n=n, **{x: st[x] for x in ("r", "tail", "l", "path")}))
+            r_next = r
+            r_prev = r
+        cores[0] = C.reshape(1, dims[0], r_next)
+    else:
+        C = A.reshape(dims[0], -1)
+        r_left = 1
+        for k in range(1, d):
+            m = r_left * dims[k - 1]
+            n = int(np.prod(dims[k:]))
+            C = C.reshape(m, n)
+            u = k
+            st = factor_step(C.T, delta2_of(u) if eps is not None else 0.0, fixed_of(u), r_prev,
+                             seed, k, kind, l_full, p)
+            r = st["r"]
+            cores[k - 1] = st["basis"].reshape(r_left, dims[k - 1], r)
+            C = st["carry"].T
+            rk[k] = r
+            tails[u - 1] = st["tail"]
+            steps.append(dict(k=k, m=m, n=n, **{x: st[x] for x in ("r", "tail", "l", "path")}))
+            r_left = r
+            r_prev = r
+        cores[d - 1] = C.reshape(r_left, dims[d - 1], 1)
+    delta2 = None if eps is None else [delta2_of(u) for u in range(1, d)]
+    return dict(cores=cores, ranks=rk, tails=tails, normA2=normA2, delta2=delta2, steps=steps,
+                orth="right" if direction == "RL" else "left")
+
+
+def tt_utv(A, eps=None, ranks=None, variant="URV", **kw):
+    """TT-URV (right-to-left, Alg. 3) or TT-ULV (left-to-right, Alg. 1/2)."""
+    return tt_sweep(A, eps=eps, ranks=ranks, variant=variant, kind="qlp", **kw)
+
+
+def tt_svd(A, eps=None, ranks=None, direction="LR", **kw):
+    """TT-SVD (Oseledets), the paper's comparison method, by the same sweep."""
+    variant = "ULV" if direction == "LR" else "URV"
+    return tt_sweep(A, eps=eps, ranks=ranks, variant=variant, kind="svd", direction=direction, **kw)
+
+
+def tt_full(cores):
+    """Contract the cores into the full tensor (Eq. TT)."""
+    t = cores[0].reshape(cores[0].shape[1], cores[0].shape[2])
+    for g in cores[1:]:
+        r0, n, r1 = g.shape
+        t = (t.reshape(-1, r0) @ g.reshape(r0, n * r1)).reshape(-1, r1)
+    return t.reshape([g.shape[1] for g in cores])
+
+
+def rse(A, cores):
+    """Relative error ||A_hat - A||_F / ||A||_F (Sec. 4)."""
+    A = np.asarray(A, dtype=np.float64)
+    D = tt_full(cores) - A
+    return float(np.sqrt(np.sum(D * D) / np.sum(A * A)))
+
+
+def tt_eval_at(cores, lin_idx):
+    """x(i) = G_1[i_1] G_2[:, i_2, :] ... G_d[:, i_d] at row-major linear indices."""
+    dims = [g.shape[1] for g in cores]
+    multi = np.unravel_index(np.asarray(lin_idx, dtype=np.int64), dims)
+    v = np.ones((len(lin_idx), 1))
+    for k, g in enumerate(cores):
+        v = np.einsum("na,anb->nb", v, g[:, multi[k], :])
+    return v[:, 0]
+
+
+def tt_eval_grad(cores, lin_idx, gout):
+    """Gradient of sum_e gout_e x(i_e) with respect to every core.
+
+    dG_k[:, i, :] = sum_{e: i_k(e) = i} gout_e (G_1[i_1]...G_{k-1}[i_{k-1}])^T
+                                         (G_{k+1}[i_{k+1}]...G_d[i_d])^T.
+    """
+    dims = [g.shape[1] for g in cores]
+    d = len(cores)
+    n = len(lin_idx)
+    multi = np.unravel_index(np.asarray(lin_idx, dtype=np.int64), dims)
+    left = [np.ones((n, 1))]
+    for k in range(d - 1):
+        left.append(np.einsum("na,anb->nb", left[-1], cores[k][:, multi[k], :]))
+    right = [None] * d
+    right[d - 1] = np.ones((n, 1))
+    for k in range(d - 1, 0, -1):
+        right[k - 1] = np.einsum("anb,nb->na", cores[k][:, multi[k], :], right[k])
+    grads = []
+    gout = np.asarray(gout, dtype=np.float64)
+    for k in range(d):
+        g = np.zeros_like(cores[k])
+        contrib = gout[:, None, None] * left[k][:, :, None] * right[k][:, None, :]
+        gt = np.zeros((dims[k],) + (cores[k].shape[0], cores[k].shape[2]))
+        np.add.at(gt, multi[k], contrib)
+        g[:] = gt.transpose(1, 0, 2)
+        grads.append(g)
+    return grads

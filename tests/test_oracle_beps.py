@@ -1,0 +1,39 @@
+"""Pin the oracle's TT-SVD against the paper's printed worked example.
+
+Table (tab: Beps), Example 2 of Sec. 4.1: the TT ranks of B(i) =
+sin(sqrt(sum_k ((i_k-1)/(I-1))^2)), I = 160, d = 4, computed by TT-SVD
+left-to-right with equal weights w_k = 1/sqrt(3), are (2,2,2), (3,3,3),
+(5,5,5), (7,7,6) for eps = 1e-2 .. 1e-5.  Golden values: tests/golden/beps_ranks.txt.
+
+Minutes of CPU (the tensor is 160^4 in FP64), so it runs only with TT_SLOW=1.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import tt
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "beps_ranks.txt")
+
+
+def load_gold():
+    rows = {}
+    for line in open(GOLD):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        eps, method, ranks = line.split()
+        rows[(float(eps), method)] = tuple(int(x) for x in ranks.split(","))
+    return rows
+
+
+@pytest.mark.slow
+def test_table_beps_tt_svd_ranks():
+    gold = load_gold()
+    B = synth.example2(160, 4, np.float64)
+    for eps in (1e-2, 1e-3, 1e-4, 1e-5):
+        res = tt.tt_svd(B, eps=eps, direction="LR")
+        assert tuple(res["ranks"][1:-1]) == gold[(eps, "TT-SVD")], (eps, res["ranks"])
+        assert tt.rse(B, res["cores"]) < eps
