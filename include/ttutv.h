@@ -1,0 +1,183 @@
+/*
+ * ttutv.h -- C ABI of the GB300 (sm_103a) TT-UTV library.
+ *
+ * Implements the tensor-train decompositions of "Effective algorithms for
+ * tensor-train decomposition via the UTV framework" (arXiv 2501.07904):
+ * TT-URV right-to-left (Alg. 3 and its prescribed-accuracy analogue,
+ * Sec. 3.2), TT-ULV left-to-right (Alg. 1 and Alg. 2, Sec. 3.1), and TT-SVD
+ * (the paper's comparison method, Sec. 4), plus contraction of a TT back to a
+ * full tensor (Eq. TT) and masked evaluation of a TT with its gradient (the
+ * observation operator P_Omega of the completion experiment, Sec. 4.2.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Tensors and cores are dense, row-major (C order; the last index is
+ *   fastest).  Core k is an array [r_{k-1}][I_k][r_k] with r_0 = r_d = 1.
+ *   Row-major order permutes the rows and columns of every unfolding
+ *   (Def. 2.1) relative to the paper's reverse-lexicographic ivec; ranks,
+ *   truncation errors and the represented tensor are unchanged.
+ * - "device" pointers are CUDA global memory of the current device; "host"
+ *   pointers are ordinary (preferably pinned) host memory.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   All work is enqueued on it.  tt_utv / tt_svd synchronize that stream
+ *   once per sweep step to read the chosen rank (the next step's shapes
+ *   depend on it); the other calls are asynchronous.
+ * - Every function returns a tt_status; on failure tt_last_error() returns a
+ *   thread-local message.  No function aborts or traps.
+ */
+#ifndef TTUTV_H
+#define TTUTV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TT_MAXD 16
+
+typedef enum {
+  TT_OK = 0,
+  TT_EINVAL = 1,        /* bad argument: d < 2, a dim <= 0, eps <= 0, rank < 1, NULL pointer */
+  TT_ENONFINITE = 2,    /* the input holds a NaN or an Inf (||A||_F^2 is not finite) */
+  TT_ENOMEM = 3,        /* the allocator returned NULL */
+  TT_ECUDA = 4,         /* a CUDA runtime call failed (message has the CUDA error) */
+  TT_ENOCONV = 5,       /* Jacobi (TT-SVD) did not converge within its sweep cap */
+  TT_ETIMEOUT = 6,      /* reserved: a bounded device-side wait ran out */
+  TT_EUNSUPPORTED = 7   /* valid request outside what this build implements */
+} tt_status;
+
+typedef enum { TT_F32 = 0, TT_F64 = 1 } tt_dtype;
+typedef enum { TT_URV = 0, TT_ULV = 1 } tt_variant;
+typedef enum { TT_RL = 0, TT_LR = 1 } tt_direction;
+
+/* Arithmetic of the sweep.
+ *  TT_P_FP64 : everything in FP64 (an FP32 input is widened first).
+ *  TT_P_FP32 : FP32 data and FFMA products; FP64 for every cross-block sum,
+ *              Gram matrix, norm and truncation-error accumulation.
+ *  TT_P_MIXED: like TT_P_FP32 (reserved for tensor-core range finding). */
+typedef enum { TT_P_FP64 = 0, TT_P_FP32 = 1, TT_P_MIXED = 2 } tt_precision;
+
+/* Arithmetic of the small (<= 256 x 256) factorizations:
+ *  TT_SMALL_AUTO picks FP32 when eps^2 w_k^2 >= 2 n u_fp32 (the Gram-based
+ *  truncation error is then resolved with margin) or the ranks are fixed,
+ *  FP64 otherwise; TT_SMALL_FP32 / TT_SMALL_FP64 force one. */
+typedef enum { TT_SMALL_AUTO = 0, TT_SMALL_FP32 = 1, TT_SMALL_FP64 = 2 } tt_small_precision;
+
+typedef struct {
+  int32_t precision;        /* tt_precision, default TT_P_FP32 */
+  int32_t small_precision;  /* tt_small_precision, default TT_SMALL_AUTO */
+  int32_t oversample;       /* sketch oversampling p, default 16 */
+  int32_t l_full;           /* basis side <= l_full columns -> exact Gram path, default 256 (max 256) */
+  uint64_t seed;            /* Philox key of the Rademacher sketch, default 0 */
+  const double* weights;    /* host, d-1 error weights w_k with sum w_k^2 = 1; NULL = equal 1/sqrt(d-1) */
+} tt_opts;
+
+/* Fill *o with the defaults listed above. */
+void tt_opts_default(tt_opts* o);
+
+/* Caller-supplied stream-ordered allocator (e.g. PyTorch's caching
+ * allocator).  alloc returns device memory of at least `bytes` bytes usable
+ * on `stream`, or NULL; free releases it after the work already enqueued on
+ * `stream`.  Passing NULL for both selects cudaMallocAsync / cudaFreeAsync. */
+typedef void* (*tt_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*tt_free_fn)(void* ptr, void* stream, void* ctx);
+
+/* Result of a sweep.  Filled by tt_utv / tt_svd; cores are device memory
+ * obtained from the caller's allocator, released by tt_result_free (or by
+ * the caller directly, core by core, through its own allocator). */
+typedef struct {
+  int32_t d;
+  int32_t dtype;                 /* tt_dtype of the cores */
+  int32_t orth;                  /* 0 = right-orthogonal cores 2..d (RL), 1 = left-orthogonal 1..d-1 (LR) */
+  int32_t pad_;
+  int64_t dims[TT_MAXD];
+  int64_t ranks[TT_MAXD + 1];    /* r_0 .. r_d, r_0 = r_d = 1 */
+  void* cores[TT_MAXD];          /* device, row-major [r_{k-1}][I_k][r_k] */
+  double norm_sq;                /* ||A||_F^2 (FP64) */
+  double tail_sq[TT_MAXD];       /* per unfolding k = 1..d-1 (index k-1): ||E_k||_F^2 of its truncation */
+  double delta_sq[TT_MAXD];      /* per unfolding: the tolerance eps_k^2 (0 for fixed ranks) */
+  int32_t sketch_l[TT_MAXD];     /* per unfolding: 0 = exact Gram path, else sketch width l */
+  int32_t small_fp64[TT_MAXD];   /* per unfolding: 1 if its small factor ran in FP64 */
+} tt_result;
+
+/* TT-UTV decomposition (Sec. 3).
+ *   A          device, prod(dims) elements of `dtype`, row-major.
+ *   d, dims    order 2 <= d <= TT_MAXD and mode sizes I_1..I_d (host).
+ *   eps        prescribed relative accuracy (Alg. 2): each unfolding k is cut
+ *              at the smallest rank with ||E_k||_F <= w_k eps ||A||_F, which
+ *              by Cor. 3.1 / Thm 3.2 gives ||A - A_hat||_F <= eps ||A||_F.
+ *              Ignored when fixed_ranks != NULL.
+ *   fixed_ranks host, d-1 ranks r_1..r_{d-1} (Alg. 1 / Alg. 3), or NULL.  A
+ *              rank above the size of its unfolding is clamped; the ranks
+ *              actually used are returned.
+ *   variant/direction  TT_URV with TT_RL (Alg. 3) or TT_ULV with TT_LR
+ *              (Alg. 1/2).  The other two pairings return TT_EUNSUPPORTED.
+ *   opts       host, may be NULL (defaults).
+ * Each unfolding step: if the basis side (columns for URV, rows for ULV) has
+ * at most l_full entries, its Gram matrix is factored exactly; otherwise a
+ * Rademacher sketch of width l (grown if the rank needs it) gives an
+ * orthonormal range basis first.  The small factor is Stewart's pivoted QLP
+ * (a rank-revealing UTV, Sec. 2.2) of the projected matrix.
+ * out receives cores, ranks and per-step truncation errors. */
+tt_status tt_utv(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
+                 const int64_t* fixed_ranks, int32_t variant, int32_t direction,
+                 const tt_opts* opts, tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx,
+                 void* stream, tt_result* out);
+
+/* TT-SVD (the comparison method of Sec. 4) through the same sweep: the small
+ * factor is a Jacobi eigen-decomposition of the Gram matrix, so the kept
+ * basis is the leading singular subspace and ||E_k||^2 = sum of the dropped
+ * sigma_i^2.  direction TT_LR (left-orthogonal, as in the paper) or TT_RL.
+ * A step whose two sides both exceed l_full returns TT_EUNSUPPORTED. */
+tt_status tt_svd(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
+                 const int64_t* fixed_ranks, int32_t direction, const tt_opts* opts,
+                 tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx, void* stream,
+                 tt_result* out);
+
+/* Release the cores of *r through free_fn (NULL = cudaFreeAsync) and zero it. */
+void tt_result_free(tt_result* r, tt_free_fn free_fn, void* alloc_ctx, void* stream);
+
+/* Contract TT cores into the full tensor (Eq. TT).
+ *   d, dims, ranks  host (ranks has d+1 entries, r_0 = r_d = 1);
+ *   cores           host array of d device pointers, each [r_{k-1}][I_k][r_k] of `dtype`;
+ *   out             device, prod(dims) elements of `dtype` (caller-allocated);
+ *   work            device scratch of at least tt_full_work_bytes(...) bytes. */
+size_t tt_full_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks, int32_t dtype);
+tt_status tt_full(int32_t d, const int64_t* dims, const int64_t* ranks, const void* const* cores,
+                  int32_t dtype, void* out, void* work, void* stream);
+
+/* Masked TT evaluation x_e = G_1[i_1] G_2[:, i_2, :] ... G_d[:, i_d] at n
+ * row-major linear indices idx[e] (device int64, 0 <= idx < prod(dims)).
+ * FP32 only.  out: device float[n]. */
+tt_status tt_eval_at(int32_t d, const int64_t* dims, const int64_t* ranks,
+                     const float* const* cores, const int64_t* idx, int64_t n, float* out,
+                     void* stream);
+
+/* Gradient of sum_e gout[e] x_e with respect to every core: for each entry,
+ * dG_k[:, i_k, :] += gout_e * (G_1[i_1]..G_{k-1}[i_{k-1}])^T (G_{k+1}[i_{k+1}]..G_d[i_d])^T,
+ * the left and right interface products recomputed per entry (nothing
+ * stored).  grads: host array of d device pointers shaped like the cores;
+ * they are ACCUMULATED into (zero them first for a plain gradient).
+ * Accumulation uses FP32 atomics, so the summation order is unspecified. */
+tt_status tt_eval_at_backward(int32_t d, const int64_t* dims, const int64_t* ranks,
+                              const float* const* cores, const int64_t* idx, int64_t n,
+                              const float* gout, float* const* grads, void* stream);
+
+/* Diagnostics used by the tests: write the Rademacher sketch matrix of sweep
+ * step `step` (rows x cols, +-1 as `dtype`, row-major, device) exactly as the
+ * sweep draws it. */
+tt_status tt_sketch_matrix(int64_t rows, int64_t cols, uint64_t seed, int32_t step, int32_t dtype,
+                           void* out, void* stream);
+
+/* Thread-local message of the last failure ("" if none). */
+const char* tt_last_error(void);
+
+/* Library version string. */
+const char* tt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTUTV_H */

@@ -19,6 +19,19 @@ class NoConvergence(RuntimeError):
     pass
 
 
+_ROWS = 1 << 16
+
+
+def _rank1_update(R, j, tv, w, c0=None):
+    """R[j:, c0:] -= outer(tv, w) (c0 = j by default), applied in row slices
+    to bound temporaries."""
+    m = R.shape[0]
+    c0 = j if c0 is None else c0
+    for r0 in range(j, m, _ROWS):
+        r1 = min(m, r0 + _ROWS)
+        R[r0:r1, c0:] -= np.outer(tv[r0 - j:r1 - j], w)
+
+
 def householder_qr(A, pivoting=False, full_q=False):
     """Householder QR of an m x n matrix: A[:, perm] = Q R.
 
@@ -52,7 +65,7 @@ def householder_qr(A, pivoting=False, full_q=False):
         v[0] += s * alpha
         tau = 2.0 / (v @ v)
         w = v @ R[j:, j:]
-        R[j:, j:] -= tau * np.outer(v, w)
+        _rank1_update(R, j, tau * v, w)
         R[j + 1:, j] = 0.0
         R[j, j] = -s * alpha
         vs.append(v)
@@ -64,7 +77,7 @@ def householder_qr(A, pivoting=False, full_q=False):
         if taus[j] == 0.0:
             continue
         v = vs[j]
-        Q[j:, :] -= taus[j] * np.outer(v, v @ Q[j:, :])
+        _rank1_update(Q, j, taus[j] * v, v @ Q[j:, :], c0=0)
     if not full_q:
         R = R[:k, :]
     return Q, R, perm

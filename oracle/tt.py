@@ -19,7 +19,8 @@ Readings where the paper is silent (each listed in the design doc):
   of B (pivoted QR of B, pivoted QR of R_1^T, L = R_2^T, Z = Pi_1 Q_2), then a
   QR of L for the URV form (T upper).  Truncation error for rank r:
   tail(r) = mu^2 + sum_{j>r} ||L(:,j)||^2, mu^2 = ||X - B W^T||_F^2.
-* TT-SVD: the same range step and pivoted QR, then one-sided Jacobi on R_1.
+* TT-SVD: the same range step (no random sketch) and Householder QR, then
+  one-sided Jacobi on R_1.
 * rank rule: smallest r >= 1 with tail(r) <= delta^2 (<= passes); fixed ranks
   are clamped to the size of the factored matrix.
 """
@@ -138,10 +139,8 @@ def factor_step(X, delta2, r_fixed, r_prev, seed, step, kind="qlp",
             Z, L, _ = qlp(B)
             tails = mu2 + qlp_tails(L)
         else:
-            _, R1, p1 = householder_qr(B, pivoting=True)
-            sig, VJ = jacobi_svd(R1)
-            Z = np.empty_like(VJ)
-            Z[p1, :] = VJ
+            _, R1, _ = householder_qr(B)
+            sig, Z = jacobi_svd(R1)
             s2 = sig * sig
             tails = mu2 + np.concatenate([np.cumsum(s2[::-1])[::-1], [0.0]])
         r_max = min(Z.shape[1], n_o, n_b)

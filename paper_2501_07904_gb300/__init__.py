@@ -1,0 +1,316 @@
+"""Python binding of the GB300 TT-UTV library (libttutv.so, include/ttutv.h).
+
+Argument marshalling only: every step of the sweep runs in the library's CUDA
+kernels.  PyTorch provides device memory (the library allocates through
+callbacks into torch's caching allocator) and the stream.  If the library is
+not built this module raises; there is no CPU fallback.
+
+    import paper_2501_07904_gb300 as tu
+    res = tu.tt_utv(A_cuda, eps=1e-2, variant="URV")      # TT-URV, right-to-left
+    res.cores, res.ranks, res.tail_sq
+    X = tu.tt_full(res.cores)                             # Eq. TT
+    x = tu.TTEvalMasked.apply(idx, *cores)                # masked evaluation, autograd
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libttutv.so")
+TT_MAXD = 16
+
+STATUS = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENONFINITE", 3: "TT_ENOMEM", 4: "TT_ECUDA",
+          5: "TT_ENOCONV", 6: "TT_ETIMEOUT", 7: "TT_EUNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
+SMALL = {"auto": 0, "fp32": 1, "fp64": 2}
+TT_F32, TT_F64 = 0, 1
+TT_URV, TT_ULV = 0, 1
+TT_RL, TT_LR = 0, 1
+
+# Every symbol include/ttutv.h declares.
+EXPORTS = ["tt_opts_default", "tt_utv", "tt_svd", "tt_result_free", "tt_full_work_bytes",
+           "tt_full", "tt_eval_at", "tt_eval_at_backward", "tt_sketch_matrix", "tt_last_error",
+           "tt_version"]
+
+
+class TTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class tt_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("small_precision", ctypes.c_int32),
+                ("oversample", ctypes.c_int32), ("l_full", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("weights", ctypes.POINTER(ctypes.c_double))]
+
+
+class tt_result(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("dtype", ctypes.c_int32), ("orth", ctypes.c_int32),
+                ("pad_", ctypes.c_int32),
+                ("dims", ctypes.c_int64 * TT_MAXD), ("ranks", ctypes.c_int64 * (TT_MAXD + 1)),
+                ("cores", ctypes.c_void_p * TT_MAXD), ("norm_sq", ctypes.c_double),
+                ("tail_sq", ctypes.c_double * TT_MAXD), ("delta_sq", ctypes.c_double * TT_MAXD),
+                ("sketch_l", ctypes.c_int32 * TT_MAXD), ("small_fp64", ctypes.c_int32 * TT_MAXD)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib_handle = None
+
+
+def lib():
+    """Load libttutv.so (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2501_07904_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U64, D, SZ = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                               ctypes.c_double, ctypes.c_size_t)
+    PI64 = ctypes.POINTER(ctypes.c_int64)
+    L.tt_opts_default.argtypes = [ctypes.POINTER(tt_opts)]
+    L.tt_opts_default.restype = None
+    L.tt_utv.argtypes = [P, I32, I32, PI64, D, PI64, I32, I32, ctypes.POINTER(tt_opts), ALLOC_FN,
+                         FREE_FN, P, P, ctypes.POINTER(tt_result)]
+    L.tt_utv.restype = I32
+    L.tt_svd.argtypes = [P, I32, I32, PI64, D, PI64, I32, ctypes.POINTER(tt_opts), ALLOC_FN,
+                         FREE_FN, P, P, ctypes.POINTER(tt_result)]
+    L.tt_svd.restype = I32
+    L.tt_result_free.argtypes = [ctypes.POINTER(tt_result), FREE_FN, P, P]
+    L.tt_result_free.restype = None
+    L.tt_full_work_bytes.argtypes = [I32, PI64, PI64, I32]
+    L.tt_full_work_bytes.restype = SZ
+    L.tt_full.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), I32, P, P, P]
+    L.tt_full.restype = I32
+    L.tt_eval_at.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P, P]
+    L.tt_eval_at.restype = I32
+    L.tt_eval_at_backward.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P,
+                                      ctypes.POINTER(P), P]
+    L.tt_eval_at_backward.restype = I32
+    L.tt_sketch_matrix.argtypes = [I64, I64, U64, I32, I32, P, P]
+    L.tt_sketch_matrix.restype = I32
+    L.tt_last_error.argtypes = []
+    L.tt_last_error.restype = ctypes.c_char_p
+    L.tt_version.argtypes = []
+    L.tt_version.restype = ctypes.c_char_p
+    _lib_handle = L
+    return L
+
+
+def _check(status):
+    if status != 0:
+        raise TTError(status, lib().tt_last_error().decode())
+
+
+def _i64(seq):
+    return (ctypes.c_int64 * max(1, len(seq)))(*[int(x) for x in seq])
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream, ctypes.c_void_p(stream.cuda_stream)
+
+
+class _TorchAllocator:
+    """Allocation callbacks into torch's caching allocator (stream-ordered)."""
+
+    def __init__(self, device):
+        self.device = device
+        self.live = {}
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+
+    def _do_alloc(self, nbytes, stream, ctx):
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        except RuntimeError:
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _do_free(self, p, stream, ctx):
+        self.live.pop(p, None)
+
+    def take(self, ptr, shape, dtype):
+        buf = self.live.pop(ptr)
+        n = math.prod(shape)
+        el = torch.empty((), dtype=dtype).element_size()
+        return buf[: n * el].view(dtype).view(shape)
+
+
+@dataclass
+class TTResult:
+    """Cores G_k (device, shape (r_{k-1}, I_k, r_k)) and per-unfolding records."""
+    cores: list
+    ranks: list
+    norm_sq: float
+    tail_sq: list           # ||E_k||_F^2 per unfolding k = 1..d-1
+    delta_sq: list          # eps_k^2 per unfolding (0 for fixed ranks)
+    sketch_l: list          # 0 = exact Gram path, else sketch width
+    small_fp64: list
+    orth: str               # "right" (cores 2..d) or "left" (cores 1..d-1)
+    info: dict = field(default_factory=dict)
+
+
+def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream):
+    if not isinstance(A, torch.Tensor):
+        raise TypeError("A must be a torch.Tensor")
+    if A.dtype not in (torch.float32, torch.float64):
+        raise TypeError("A must be float32 or float64")
+    A = A.contiguous()
+    d = A.dim()
+    dev = A.device if A.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    st, st_ptr = _stream(stream)
+    opts = tt_opts()
+    lib().tt_opts_default(ctypes.byref(opts))
+    opts.precision = PRECISION[precision]
+    opts.small_precision = SMALL[small]
+    opts.oversample = int(oversample)
+    opts.l_full = int(l_full)
+    opts.seed = int(seed)
+    wbuf = None
+    if weights is not None:
+        wbuf = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
+        opts.weights = ctypes.cast(wbuf, ctypes.POINTER(ctypes.c_double))
+    dims = _i64(A.shape)
+    fr = _i64(ranks) if ranks is not None else None
+    alloc = _TorchAllocator(dev)
+    res = tt_result()
+    dtype = TT_F64 if A.dtype == torch.float64 else TT_F32
+    with torch.cuda.device(dev), torch.cuda.stream(st):
+        status = fn(ctypes.c_void_p(A.data_ptr()), dtype, d, dims,
+                    float(eps) if eps is not None else 0.0, fr, *extra, ctypes.byref(opts),
+                    alloc._alloc, alloc._free, None, st_ptr, ctypes.byref(res))
+        if status != 0:
+            msg = lib().tt_last_error().decode()
+            alloc.live.clear()
+            raise TTError(status, msg)
+        out_dtype = torch.float64 if res.dtype == TT_F64 else torch.float32
+        rk = [int(res.ranks[k]) for k in range(d + 1)]
+        cores = [alloc.take(res.cores[k], (rk[k], int(res.dims[k]), rk[k + 1]), out_dtype)
+                 for k in range(d)]
+    alloc.live.clear()
+    return TTResult(cores=cores, ranks=rk, norm_sq=float(res.norm_sq),
+                    tail_sq=[float(res.tail_sq[k]) for k in range(d - 1)],
+                    delta_sq=[float(res.delta_sq[k]) for k in range(d - 1)],
+                    sketch_l=[int(res.sketch_l[k]) for k in range(d - 1)],
+                    small_fp64=[int(res.small_fp64[k]) for k in range(d - 1)],
+                    orth="right" if res.orth == 0 else "left")
+
+
+def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, oversample=16,
+           l_full=256, small="auto", weights=None, stream=None):
+    """TT-URV right-to-left (Alg. 3) or TT-ULV left-to-right (Alg. 1/2).
+
+    Give ``eps`` (prescribed relative accuracy, Alg. 2) or ``ranks``
+    (r_1..r_{d-1}).  ``A`` may live on the GPU or on the host (copied in).
+    """
+    if (eps is None) == (ranks is None):
+        raise ValueError("give exactly one of eps or ranks")
+    v = {"URV": (TT_URV, TT_RL), "ULV": (TT_ULV, TT_LR)}[variant]
+    return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
+                  weights, stream)
+
+
+def tt_svd(A, eps=None, ranks=None, direction="LR", precision="fp32", l_full=256, small="auto",
+           weights=None, stream=None):
+    """TT-SVD (the paper's comparison method) through the same sweep."""
+    if (eps is None) == (ranks is None):
+        raise ValueError("give exactly one of eps or ranks")
+    dr = {"LR": TT_LR, "RL": TT_RL}[direction]
+    return _sweep(lib().tt_svd, A, eps, ranks, (dr,), precision, 0, 16, l_full, small, weights,
+                  stream)
+
+
+def _core_meta(cores):
+    d = len(cores)
+    dims = [int(g.shape[1]) for g in cores]
+    ranks = [int(cores[0].shape[0])] + [int(g.shape[2]) for g in cores]
+    return d, dims, ranks
+
+
+def tt_full(cores, stream=None):
+    """Full tensor from TT cores (Eq. TT), computed by the library's GEMM."""
+    d, dims, ranks = _core_meta(cores)
+    dtype = cores[0].dtype
+    cores = [g.contiguous() for g in cores]
+    st, st_ptr = _stream(stream)
+    code = TT_F64 if dtype == torch.float64 else TT_F32
+    D, R = _i64(dims), _i64(ranks)
+    nbytes = lib().tt_full_work_bytes(d, D, R, code)
+    dev = cores[0].device
+    with torch.cuda.device(dev), torch.cuda.stream(st):
+        out = torch.empty(dims, dtype=dtype, device=dev)
+        work = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=dev)
+        ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores])
+        _check(lib().tt_full(d, D, R, ptrs, code, ctypes.c_void_p(out.data_ptr()),
+                             ctypes.c_void_p(work.data_ptr()), st_ptr))
+    return out
+
+
+def tt_eval_at(cores, idx, stream=None):
+    """x_e = G_1[i_1] ... G_d[i_d] at int64 row-major linear indices (FP32)."""
+    d, dims, ranks = _core_meta(cores)
+    cores = [g.contiguous() for g in cores]
+    idx = idx.contiguous()
+    st, st_ptr = _stream(stream)
+    with torch.cuda.device(idx.device), torch.cuda.stream(st):
+        out = torch.empty(idx.numel(), dtype=torch.float32, device=idx.device)
+        ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores])
+        _check(lib().tt_eval_at(d, _i64(dims), _i64(ranks), ptrs, ctypes.c_void_p(idx.data_ptr()),
+                                idx.numel(), ctypes.c_void_p(out.data_ptr()), st_ptr))
+    return out
+
+
+def tt_eval_at_backward(cores, idx, gout, stream=None):
+    """Core gradients of sum_e gout_e x_e (FP32), fresh zeroed buffers."""
+    d, dims, ranks = _core_meta(cores)
+    cores = [g.contiguous() for g in cores]
+    st, st_ptr = _stream(stream)
+    with torch.cuda.device(idx.device), torch.cuda.stream(st):
+        grads = [torch.zeros_like(g) for g in cores]
+        ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores])
+        gptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in grads])
+        _check(lib().tt_eval_at_backward(d, _i64(dims), _i64(ranks), ptrs,
+                                         ctypes.c_void_p(idx.contiguous().data_ptr()), idx.numel(),
+                                         ctypes.c_void_p(gout.contiguous().data_ptr()), gptrs, st_ptr))
+    return grads
+
+
+class TTEvalMasked(torch.autograd.Function):
+    """Masked TT evaluation with the library's hand-written backward kernel."""
+
+    @staticmethod
+    def forward(ctx, idx, *cores):
+        ctx.save_for_backward(idx, *cores)
+        return tt_eval_at(list(cores), idx)
+
+    @staticmethod
+    def backward(ctx, gout):
+        idx, *cores = ctx.saved_tensors
+        grads = tt_eval_at_backward(cores, idx, gout.to(torch.float32))
+        return (None, *grads)
+
+
+def sketch_matrix(rows, cols, seed=0, step=0, dtype=torch.float32, device="cuda", stream=None):
+    """The Rademacher sketch matrix Omega the sweep draws at step ``step``."""
+    st, st_ptr = _stream(stream)
+    out = torch.empty((rows, cols), dtype=dtype, device=device)
+    code = TT_F64 if dtype == torch.float64 else TT_F32
+    _check(lib().tt_sketch_matrix(rows, cols, seed, step, code, ctypes.c_void_p(out.data_ptr()),
+                                  st_ptr))
+    return out
+
+
+def version():
+    return lib().tt_version().decode()

@@ -1,0 +1,694 @@
+// Host driver of the TT-UTV sweep and the C ABI declared in include/ttutv.h.
+//
+// One sweep step factors the current unfolding C (row-major m x n, a free
+// view of the previous carry).  The basis side is the column side for URV
+// (right-to-left, Alg. 3) and the row side for ULV (left-to-right, Alg. 1/2);
+// N_b is its size and N_o the other side's.
+//   exact path  (N_b <= l_full): G = Gram of the basis side (FP64), small
+//               factor of G -> Z_1, r; carry = C Z_1 (URV) or Z_1^T C (ULV).
+//   sketch path (N_b  > l_full): Y = C^T Omega (URV) / C Omega (ULV) with a
+//               Rademacher Omega (identity when l >= N_o), W = CholeskyQR2(Y),
+//               B = C W (URV) / C^T W (ULV), small factor of B^T B -> Z_1, r;
+//               core from W Z_1, carry from B Z_1.  l grows (x2) when the rank
+//               needs more than l - p columns or the tolerance is missed.
+// The rank of each step is read back through pinned host memory (the only
+// synchronization of the step); everything else stays on the stream.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "internal.h"
+#include "ttutv.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+tt_status fail(tt_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+tt_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(TT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TT_CK(expr, what)                         \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+struct Alloc {
+  tt_alloc_fn al;
+  tt_free_fn fr;
+  void* ctx;
+  cudaStream_t st;
+  void* get(size_t bytes) {
+    bytes = ((bytes ? bytes : 1) + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (al) {
+      p = al(bytes, (void*)st, ctx);
+    } else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    if (fr)
+      fr(p, (void*)st, ctx);
+    else
+      cudaFreeAsync(p, st);
+  }
+};
+
+// Device buffer released through the caller's allocator at scope exit.
+struct Buf {
+  Alloc* a;
+  void* p = nullptr;
+  explicit Buf(Alloc* a_) : a(a_) {}
+  Buf(const Buf&) = delete;
+  ~Buf() { reset(); }
+  void reset() {
+    if (p) a->put(p);
+    p = nullptr;
+  }
+  bool get(size_t bytes) {
+    reset();
+    p = a->get(bytes);
+    return p != nullptr;
+  }
+  void* release() {
+    void* q = p;
+    p = nullptr;
+    return q;
+  }
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+#define TT_ALLOC(buf, bytes)                                                         \
+  do {                                                                               \
+    if (!(buf).get(bytes)) return fail(TT_ENOMEM, "allocator returned NULL");        \
+  } while (0)
+
+ttk::StepInfo* pinned_info() {
+  thread_local ttk::StepInfo* h = nullptr;
+  thread_local ttk::StepInfo fallback;
+  if (!h) {
+    if (cudaMallocHost((void**)&h, sizeof(ttk::StepInfo)) != cudaSuccess) {
+      cudaGetLastError();
+      h = &fallback;
+    }
+  }
+  return h;
+}
+
+int64_t roundup(int64_t x, int64_t m) { return ((x + m - 1) / m) * m; }
+
+// TTUTV_DEBUG=1 prints one line per sweep step to stderr.
+bool debug_trace() {
+  static const bool on = [] {
+    const char* v = getenv("TTUTV_DEBUG");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
+// Sketch width l: r + p for a fixed rank, else roundup16(max(2 r_prev,
+// r_prev + p, 32)); never more than either side nor the small-factor limit.
+int64_t sketch_size(int64_t nb, int64_t no, int64_t r_prev, int64_t p, int64_t rfix) {
+  int64_t l = (rfix >= 1) ? rfix + p : roundup(std::max<int64_t>(std::max<int64_t>(2 * r_prev, r_prev + p), 32), 16);
+  l = std::min<int64_t>(l, std::min<int64_t>(nb, no));
+  return std::min<int64_t>(l, ttk::kMaxSmall);
+}
+
+struct SweepCfg {
+  bool urv;   // basis on the column side, right-to-left
+  bool svd;   // Jacobi small factor (TT-SVD)
+};
+
+template <typename W>
+tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* dims, double eps,
+                    const int64_t* fixed, SweepCfg cfg, const tt_opts& o, Alloc& al,
+                    tt_result* out) {
+  constexpr bool W64 = std::is_same<W, double>::value;
+  cudaStream_t st = al.st;
+  const int64_t p_over = o.oversample;
+  const int64_t l_full = o.l_full;
+
+  std::vector<double> w(d - 1, 1.0 / sqrt((double)(d - 1)));
+  if (o.weights)
+    for (int i = 0; i < d - 1; ++i) w[i] = o.weights[i];
+
+  int64_t total = 1;
+  for (int k = 0; k < d; ++k) total *= dims[k];
+
+  // Input in the working precision, on the device.
+  cudaPointerAttributes pa;
+  bool host_in = false;
+  if (cudaPointerGetAttributes(&pa, A_in) != cudaSuccess) {
+    cudaGetLastError();
+    host_in = true;
+  } else {
+    host_in = (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered);
+  }
+  const bool in64 = dtype_in == TT_F64;
+  const size_t in_el = in64 ? 8 : 4;
+  Buf staged(&al), conv(&al);
+  const void* src = A_in;
+  if (host_in) {
+    TT_ALLOC(staged, total * in_el);
+    TT_CK(cudaMemcpyAsync(staged.p, A_in, total * in_el, cudaMemcpyHostToDevice, st), "copy input");
+    src = staged.p;
+  }
+  const W* A = (const W*)src;
+  if (in64 != W64) {
+    TT_ALLOC(conv, total * sizeof(W));
+    TT_CK(ttk::cast_copy(src, in64, conv.p, W64, total, st), "widen/narrow input");
+    A = conv.as<W>();
+    staged.reset();
+  }
+
+  Buf scal(&al);
+  TT_ALLOC(scal, sizeof(double) * (4 + 2 * TT_MAXD));
+  double* d_scal = scal.as<double>();
+  double* d_x2first = d_scal;            // ||A||^2 when the first step is sketched
+  double* d_carry2 = d_scal + 4;         // per step: ||carry||^2 (sum of squares of stored values)
+  TT_CK(cudaMemsetAsync(d_scal, 0, sizeof(double) * (4 + 2 * TT_MAXD), st), "memset");
+  Buf dinfo(&al);
+  TT_ALLOC(dinfo, sizeof(ttk::StepInfo));
+  ttk::StepInfo* hinfo = pinned_info();
+
+  memset(out, 0, sizeof(*out));
+  out->d = d;
+  out->dtype = W64 ? TT_F64 : TT_F32;
+  out->orth = cfg.urv ? 0 : 1;
+  for (int k = 0; k < d; ++k) out->dims[k] = dims[k];
+  out->ranks[0] = out->ranks[d] = 1;
+
+  std::vector<void*> cores(d, nullptr);
+  struct CoreGuard {
+    std::vector<void*>& c;
+    Alloc& a;
+    bool ok = false;
+    ~CoreGuard() {
+      if (!ok)
+        for (void* p : c) a.put(p);
+    }
+  } guard{cores, al};
+
+  std::vector<double> x2s(d, 0.0);
+  const W* C = A;
+  Buf cbuf(&al);
+  double normA2 = -1.0;
+  int64_t r_carry = 1, r_prev = 0;
+
+  for (int s = 0; s < d - 1; ++s) {
+    const int k = cfg.urv ? d - s : s + 1;  // core being separated (1-based)
+    int64_t m, n;
+    if (cfg.urv) {
+      m = 1;
+      for (int t = 0; t < k - 1; ++t) m *= dims[t];
+      n = dims[k - 1] * r_carry;
+    } else {
+      m = r_carry * dims[k - 1];
+      n = 1;
+      for (int t = k; t < d; ++t) n *= dims[t];
+    }
+    const int u = cfg.urv ? k - 1 : k;  // unfolding number 1..d-1
+    const int64_t nb = cfg.urv ? n : m, no = cfg.urv ? m : n;
+    const double dscale = fixed ? 0.0 : (w[u - 1] * eps) * (w[u - 1] * eps);
+    const int64_t rfix = fixed ? fixed[u - 1] : -1;
+    const int64_t rcap = std::min<int64_t>(std::min<int64_t>(nb, no), ttk::kMaxSmall);
+    const bool exact = nb <= l_full;
+    const bool first = (s == 0);
+    if (cfg.svd && !exact && no > ttk::kMaxSmall)
+      return fail(TT_EUNSUPPORTED, "TT-SVD step with both unfolding sides above 256");
+
+    // A tolerance below ~n u_fp32 of ||C||^2 cannot be resolved from an
+    // FP32-accumulated Gram or an FP32 factorization: such steps form the
+    // Gram with exact products and FP64 sums, and factor it in FP64.
+    auto tight = [&](int64_t nsz) {
+      return !fixed && !(dscale >= 2.0 * (double)nsz * 5.9604644775390625e-08);
+    };
+    auto choose_small64 = [&](int64_t nsz) {
+      if (o.small_precision == TT_SMALL_FP64) return true;
+      if (o.small_precision == TT_SMALL_FP32) return false;
+      if (W64) return true;
+      return tight(nsz);
+    };
+
+    ttk::SmallParams prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.mode = cfg.svd ? ttk::SM_JACOBI : ttk::SM_QLP;
+    prm.r_fixed = (int)rfix;
+    prm.r_cap = (int)rcap;
+    prm.delta2_scale = dscale;
+    prm.delta2 = (normA2 >= 0.0) ? dscale * normA2 : 0.0;
+
+    Buf zb(&al), carry(&al), core(&al), ws(&al), ws2(&al), gb(&al);
+    Buf omega(&al), yb(&al), s1b(&al), w1b(&al), wb(&al), bb(&al), gy(&al), gwb(&al);
+    int64_t r = 1, l = 0;
+    bool small64 = false;
+    const W* Zp = nullptr;
+    int64_t ldz = 0;
+
+    if (exact) {
+      TT_ALLOC(gb, (size_t)nb * nb * sizeof(double));
+      TT_ALLOC(ws, std::max(ttk::gemm_ws_bytes<W>(nb, nb, no, true), ttk::small_ws_bytes((int)nb, true)));
+      const bool acc = !W64 && tight(nb);
+      if (cfg.urv)
+        TT_CK(ttk::gemm<W>({C, n, false}, {C, n, true}, n, n, m, nullptr, 0, gb.as<double>(), true,
+                           nullptr, ws.p, st, acc), "Gram C^T C");
+      else
+        TT_CK(ttk::gemm<W>({C, n, true}, {C, n, false}, m, m, n, nullptr, 0, gb.as<double>(), true,
+                           nullptr, ws.p, st, acc), "Gram C C^T");
+      small64 = choose_small64(nb);
+      prm.n = (int)nb;
+      if (first) {
+        prm.normA2_dev = d_scal;  // any non-null pointer: the value is this Gram's trace
+        prm.normA2_is_trace = 1;
+      }
+      prm.x2_dev = nullptr;
+      prm.piv_tol = small64 ? 1e-15 : 1e-6;
+      TT_ALLOC(zb, (size_t)nb * nb * sizeof(W));
+      ldz = nb;
+      TT_CK(ttk::small_factor(gb.as<double>(), prm, small64, zb.p, W64, (int)ldz, ws.p,
+                              dinfo.as<ttk::StepInfo>(), st), "small factor");
+      TT_CK(cudaMemcpyAsync(hinfo, dinfo.p, sizeof(ttk::StepInfo), cudaMemcpyDeviceToHost, st), "info");
+      TT_CK(cudaStreamSynchronize(st), "step sync");
+      if (hinfo->status & 1) return fail(TT_ENONFINITE, "input holds NaN or Inf");
+      if (hinfo->status & 2) return fail(TT_ENOCONV, "Jacobi eigen-solver did not converge");
+      r = hinfo->r;
+      Zp = zb.as<W>();
+    } else {
+      l = cfg.svd ? std::min<int64_t>(no, ttk::kMaxSmall)
+                  : sketch_size(nb, no, r_prev, p_over, rfix);
+      const double* x2_dev = first ? d_x2first : (d_carry2 + (s - 1));
+      if (first) {
+        Buf sw(&al);
+        TT_ALLOC(sw, ttk::sumsq_ws_bytes(total));
+        TT_CK(ttk::sumsq(C, W64, m * n, d_x2first, sw.p, st), "sum of squares");
+        prm.normA2_dev = d_x2first;
+        prm.normA2_is_trace = 0;
+      }
+      while (true) {
+        const bool identity = l >= no;
+        small64 = choose_small64(l);
+        TT_ALLOC(omega, (size_t)no * l * sizeof(W));
+        TT_CK(ttk::fill_sketch(omega.p, W64, no, l, o.seed, (uint32_t)k, identity, st), "sketch matrix");
+        TT_ALLOC(yb, (size_t)nb * l * sizeof(W));
+        size_t wsz = 0;
+        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(nb, l, no, false));
+        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(l, l, nb, true));
+        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(nb, l, l, false));
+        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(no, l, nb, false));
+        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(l, l, no, true));
+        TT_ALLOC(ws, wsz);
+        TT_ALLOC(ws2, ttk::small_ws_bytes((int)l, true));
+        if (cfg.urv)
+          TT_CK(ttk::gemm<W>({C, n, false}, {omega.as<W>(), l, true}, n, l, m, yb.as<W>(), l,
+                             nullptr, false, nullptr, ws.p, st), "sketch C^T Omega");
+        else
+          TT_CK(ttk::gemm<W>({C, n, true}, {omega.as<W>(), l, true}, m, l, n, yb.as<W>(), l,
+                             nullptr, false, nullptr, ws.p, st), "sketch C Omega");
+        omega.reset();
+        // W = shifted Cholesky-QR3(Y): a shifted pass that cannot break
+        // down, then two plain passes; span(W[:, :j]) = span(Y[:, :j]).
+        TT_ALLOC(gy, (size_t)l * l * sizeof(double));
+        TT_ALLOC(s1b, (size_t)l * l * sizeof(W));
+        TT_ALLOC(w1b, (size_t)nb * l * sizeof(W));
+        TT_ALLOC(wb, (size_t)nb * l * sizeof(W));
+        ttk::SmallParams po;
+        memset(&po, 0, sizeof(po));
+        po.n = (int)l;
+        po.mode = ttk::SM_ORTH;
+        po.r_fixed = -1;
+        po.r_cap = (int)l;
+        // With a tight tolerance the sketch may carry directions near the
+        // FP32 floor; W_1 is then too ill-conditioned for an FP32-summed
+        // Gram to stay positive definite, so those Grams use exact products
+        // and FP64 sums and the Cholesky runs in FP64.
+        const bool orth64 = small64 || W64;
+        const double u_c = orth64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        const W* src_pass = yb.as<W>();
+        W* dst_pass[3] = {w1b.as<W>(), wb.as<W>(), w1b.as<W>()};
+        for (int pass = 0; pass < 3; ++pass) {
+          po.shift_rel = pass == 0 ? 64.0 * (double)l * u_c : 0.0;
+          po.piv_tol = pass == 0 ? 0.0 : 64.0 * (double)l * u_c * u_c;
+          TT_CK(ttk::gemm<W>({src_pass, l, false}, {src_pass, l, true}, l, l, nb, nullptr, 0,
+                             gy.as<double>(), true, nullptr, ws.p, st, !W64 && small64),
+                "Gram of sketch");
+          TT_CK(ttk::small_factor(gy.as<double>(), po, orth64, s1b.p, W64, (int)l, ws2.p,
+                                  dinfo.as<ttk::StepInfo>(), st), "orthonormalize");
+          TT_CK(ttk::gemm<W>({src_pass, l, true}, {s1b.as<W>(), l, true}, nb, l, l, dst_pass[pass],
+                             l, nullptr, false, nullptr, ws.p, st), "apply R^-1");
+          src_pass = dst_pass[pass];
+        }
+        const W* Wm = w1b.as<W>();
+        TT_ALLOC(bb, (size_t)no * l * sizeof(W));
+        if (cfg.urv)
+          TT_CK(ttk::gemm<W>({C, n, true}, {Wm, l, true}, m, l, n, bb.as<W>(), l, nullptr, false,
+                             nullptr, ws.p, st), "project C W");
+        else
+          TT_CK(ttk::gemm<W>({C, n, false}, {Wm, l, true}, n, l, m, bb.as<W>(), l, nullptr, false,
+                             nullptr, ws.p, st), "project C^T W");
+        TT_CK(ttk::gemm<W>({bb.as<W>(), l, false}, {bb.as<W>(), l, true}, l, l, no, nullptr, 0,
+                           gy.as<double>(), true, nullptr, ws.p, st, !W64 && tight(l)), "Gram B^T B");
+        // FP32 W is orthonormal only to ~1e-7, which biases ||X W||^2 and so
+        // the range miss mu^2; with a tight tolerance the small factor
+        // whitens by W^T W (exact products, FP64 sums).
+        const bool whiten = !W64 && small64;
+        if (whiten) {
+          TT_ALLOC(gwb, (size_t)l * l * sizeof(double));
+          TT_CK(ttk::gemm<W>({Wm, l, false}, {Wm, l, true}, l, l, nb, nullptr, 0, gwb.as<double>(),
+                             true, nullptr, ws.p, st, true), "Gram W^T W");
+        }
+        prm.Gw = whiten ? gwb.as<double>() : nullptr;
+        prm.n = (int)l;
+        prm.r_cap = (int)std::min<int64_t>(rcap, l);
+        prm.x2_dev = x2_dev;
+        prm.piv_tol = small64 ? 1e-15 : 1e-6;
+        TT_ALLOC(zb, (size_t)l * l * sizeof(W));
+        ldz = l;
+        TT_CK(ttk::small_factor(gy.as<double>(), prm, small64, zb.p, W64, (int)ldz, ws2.p,
+                                dinfo.as<ttk::StepInfo>(), st), "small factor");
+        TT_CK(cudaMemcpyAsync(hinfo, dinfo.p, sizeof(ttk::StepInfo), cudaMemcpyDeviceToHost, st), "info");
+        TT_CK(cudaStreamSynchronize(st), "step sync");
+        if (hinfo->status & 1) return fail(TT_ENONFINITE, "input holds NaN or Inf");
+        if (hinfo->status & 2) return fail(TT_ENOCONV, "Jacobi eigen-solver did not converge");
+        r = hinfo->r;
+        const double d2 = hinfo->delta2;
+        const int64_t lmax = std::min<int64_t>(std::min<int64_t>(nb, no), ttk::kMaxSmall);
+        if (!fixed && !cfg.svd && (r > l - p_over || hinfo->tail > d2)) {
+          if (l < lmax) {
+            l = std::min<int64_t>(2 * l, lmax);
+            continue;
+          }
+          if (hinfo->tail > d2)
+            return fail(TT_EUNSUPPORTED, "prescribed accuracy needs a rank above the 256-column sketch");
+        }
+        break;
+      }
+      Zp = zb.as<W>();
+    }
+
+    if (first) normA2 = hinfo->normA2;
+    x2s[s] = hinfo->x2;
+    if (debug_trace())
+      fprintf(stderr,
+              "[ttutv] step k=%d %s m=%lld n=%lld l=%lld small=%s r=%d k1=%d nsteps=%d x2=%.6e "
+              "trace=%.6e mu2=%.3e s1=%.3e delta2=%.3e tail=%.3e status=%d\n",
+              k, exact ? "exact" : "sketch", (long long)m, (long long)n, (long long)l,
+              small64 ? "fp64" : "fp32", hinfo->r, hinfo->k1, hinfo->nsteps, hinfo->x2,
+              hinfo->trace, hinfo->mu2, hinfo->s1, hinfo->delta2, hinfo->tail, hinfo->status);
+    out->delta_sq[u - 1] = fixed ? 0.0 : hinfo->delta2;
+    out->sketch_l[u - 1] = exact ? 0 : (int32_t)l;
+    out->small_fp64[u - 1] = small64 ? 1 : 0;
+
+    // carry and core
+    const int64_t crow = cfg.urv ? m : r, ccol = cfg.urv ? r : n;
+    TT_ALLOC(carry, (size_t)crow * ccol * sizeof(W));
+    const int64_t corerows = cfg.urv ? r : m, corecols = cfg.urv ? n : r;
+    TT_ALLOC(core, (size_t)corerows * corecols * sizeof(W));
+    {
+      size_t wsz = 0;
+      if (exact) {
+        wsz = cfg.urv ? ttk::gemm_ws_bytes<W>(m, r, n, false) : ttk::gemm_ws_bytes<W>(r, n, m, false);
+      } else {
+        wsz = std::max(cfg.urv ? ttk::gemm_ws_bytes<W>(m, r, l, false) : ttk::gemm_ws_bytes<W>(r, n, l, false),
+                       cfg.urv ? ttk::gemm_ws_bytes<W>(r, n, l, false) : ttk::gemm_ws_bytes<W>(m, r, l, false));
+      }
+      TT_ALLOC(ws, wsz);
+    }
+    if (exact) {
+      if (cfg.urv) {
+        TT_CK(ttk::gemm<W>({C, n, true}, {Zp, ldz, true}, m, r, n, carry.as<W>(), r, nullptr, false,
+                           d_carry2 + s, ws.p, st), "carry C Z1");
+        TT_CK(ttk::copy2d(Zp, ldz, true, core.p, n, r, n, W64, st), "core Z1^T");
+      } else {
+        TT_CK(ttk::gemm<W>({Zp, ldz, false}, {C, n, true}, r, n, m, carry.as<W>(), n, nullptr, false,
+                           d_carry2 + s, ws.p, st), "carry Z1^T C");
+        TT_CK(ttk::copy2d(Zp, ldz, false, core.p, r, m, r, W64, st), "core Z1");
+      }
+    } else {
+      const W* Bm = bb.as<W>();
+      const W* Wm = w1b.as<W>();
+      if (cfg.urv) {
+        TT_CK(ttk::gemm<W>({Bm, l, true}, {Zp, ldz, true}, m, r, l, carry.as<W>(), r, nullptr, false,
+                           d_carry2 + s, ws.p, st), "carry B Z1");
+        TT_CK(ttk::gemm<W>({Zp, ldz, false}, {Wm, l, false}, r, n, l, core.as<W>(), n, nullptr, false,
+                           nullptr, ws.p, st), "core (W Z1)^T");
+      } else {
+        TT_CK(ttk::gemm<W>({Zp, ldz, false}, {Bm, l, false}, r, n, l, carry.as<W>(), n, nullptr, false,
+                           d_carry2 + s, ws.p, st), "carry (B Z1)^T");
+        TT_CK(ttk::gemm<W>({Wm, l, true}, {Zp, ldz, true}, m, r, l, core.as<W>(), r, nullptr, false,
+                           nullptr, ws.p, st), "core W Z1");
+      }
+    }
+    cores[k - 1] = core.release();
+    if (cfg.urv)
+      out->ranks[k - 1] = r;
+    else
+      out->ranks[k] = r;
+    // the carry becomes the next unfolding; the previous one is released
+    cbuf.reset();
+    if (s == 0) {
+      conv.reset();
+      staged.reset();
+    }
+    cbuf.p = carry.release();
+    C = cbuf.as<W>();
+    r_carry = r;
+    r_prev = r;
+  }
+  // last core: the final carry (Alg. 3 step 8 / Alg. 1 step 8)
+  cores[cfg.urv ? 0 : d - 1] = cbuf.release();
+  double h_carry2[TT_MAXD];
+  TT_CK(cudaMemcpyAsync(h_carry2, d_carry2, sizeof(double) * (d - 1), cudaMemcpyDeviceToHost, st), "tails");
+  TT_CK(cudaStreamSynchronize(st), "final sync");
+  for (int s = 0; s < d - 1; ++s) {
+    const int k = cfg.urv ? d - s : s + 1;
+    const int u = cfg.urv ? k - 1 : k;
+    const double t = x2s[s] - h_carry2[s];
+    out->tail_sq[u - 1] = t > 0.0 ? t : 0.0;
+  }
+  out->norm_sq = normA2;
+  for (int k = 0; k < d; ++k) out->cores[k] = cores[k];
+  guard.ok = true;
+  return TT_OK;
+}
+
+tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
+                   const int64_t* fixed, const tt_opts& o, tt_result* out) {
+  if (!A || !dims || !out) return fail(TT_EINVAL, "NULL argument");
+  if (d < 2 || d > TT_MAXD) return fail(TT_EINVAL, "order d must be in [2, 16]");
+  if (dtype != TT_F32 && dtype != TT_F64) return fail(TT_EINVAL, "dtype must be TT_F32 or TT_F64");
+  double total = 1.0;
+  for (int k = 0; k < d; ++k) {
+    if (dims[k] < 1) return fail(TT_EINVAL, "every mode size must be >= 1");
+    total *= (double)dims[k];
+  }
+  if (total > 4.0e18) return fail(TT_EINVAL, "tensor too large");
+  if (fixed) {
+    for (int k = 0; k < d - 1; ++k)
+      if (fixed[k] < 1) return fail(TT_EINVAL, "fixed ranks must be >= 1");
+  } else if (!(eps > 0.0) || !isfinite(eps)) {
+    return fail(TT_EINVAL, "eps must be positive and finite");
+  }
+  if (o.oversample < 0 || o.oversample > 128) return fail(TT_EINVAL, "oversample must be in [0, 128]");
+  if (o.l_full < 1 || o.l_full > ttk::kMaxSmall) return fail(TT_EINVAL, "l_full must be in [1, 256]");
+  if (o.precision < TT_P_FP64 || o.precision > TT_P_MIXED) return fail(TT_EINVAL, "bad precision");
+  if (o.small_precision < TT_SMALL_AUTO || o.small_precision > TT_SMALL_FP64)
+    return fail(TT_EINVAL, "bad small_precision");
+  if (o.weights) {
+    double s = 0.0;
+    for (int k = 0; k < d - 1; ++k) {
+      if (!(o.weights[k] > 0.0) || !isfinite(o.weights[k])) return fail(TT_EINVAL, "weights must be positive");
+      s += o.weights[k] * o.weights[k];
+    }
+    if (fabs(s - 1.0) > 1e-6) return fail(TT_EINVAL, "weights must satisfy sum w_k^2 = 1");
+  }
+  return TT_OK;
+}
+
+tt_status sweep_entry(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
+                      const int64_t* fixed, SweepCfg cfg, const tt_opts* opts, tt_alloc_fn alloc,
+                      tt_free_fn free_fn, void* ctx, void* stream, tt_result* out) {
+  g_err.clear();
+  tt_opts o;
+  tt_opts_default(&o);
+  if (opts) o = *opts;
+  tt_status v = validate(A, dtype, d, dims, eps, fixed, o, out);
+  if (v != TT_OK) return v;
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(TT_EINVAL, "alloc and free must both be given or both be NULL");
+  Alloc al{alloc, free_fn, ctx, (cudaStream_t)stream};
+  if (o.precision == TT_P_FP64)
+    return run_sweep<double>(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
+  return run_sweep<float>(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+void tt_opts_default(tt_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = TT_P_FP32;
+  o->small_precision = TT_SMALL_AUTO;
+  o->oversample = 16;
+  o->l_full = 256;
+  o->seed = 0;
+  o->weights = nullptr;
+}
+
+tt_status tt_utv(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
+                 const int64_t* fixed_ranks, int32_t variant, int32_t direction,
+                 const tt_opts* opts, tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx,
+                 void* stream, tt_result* out) {
+  SweepCfg cfg;
+  if (variant == TT_URV && direction == TT_RL)
+    cfg = {true, false};
+  else if (variant == TT_ULV && direction == TT_LR)
+    cfg = {false, false};
+  else if ((variant == TT_URV && direction == TT_LR) || (variant == TT_ULV && direction == TT_RL))
+    return fail(TT_EUNSUPPORTED, "only URV right-to-left and ULV left-to-right are built");
+  else
+    return fail(TT_EINVAL, "bad variant or direction");
+  return sweep_entry(A, dtype, d, dims, eps, fixed_ranks, cfg, opts, alloc, free_fn, alloc_ctx,
+                     stream, out);
+}
+
+tt_status tt_svd(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
+                 const int64_t* fixed_ranks, int32_t direction, const tt_opts* opts,
+                 tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx, void* stream,
+                 tt_result* out) {
+  if (direction != TT_RL && direction != TT_LR) return fail(TT_EINVAL, "bad direction");
+  SweepCfg cfg{direction == TT_RL, true};
+  return sweep_entry(A, dtype, d, dims, eps, fixed_ranks, cfg, opts, alloc, free_fn, alloc_ctx,
+                     stream, out);
+}
+
+void tt_result_free(tt_result* r, tt_free_fn free_fn, void* alloc_ctx, void* stream) {
+  if (!r) return;
+  for (int k = 0; k < TT_MAXD; ++k) {
+    if (!r->cores[k]) continue;
+    if (free_fn)
+      free_fn(r->cores[k], stream, alloc_ctx);
+    else
+      cudaFreeAsync(r->cores[k], (cudaStream_t)stream);
+  }
+  memset(r, 0, sizeof(*r));
+}
+
+size_t tt_full_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks, int32_t dtype) {
+  if (d < 2 || d > TT_MAXD || !dims || !ranks) return 0;
+  const size_t el = dtype == TT_F64 ? 8 : 4;
+  int64_t rows = dims[0];
+  size_t buf = 0, ws = 0;
+  for (int k = 1; k < d; ++k) {
+    const int64_t N = dims[k] * ranks[k + 1];
+    ws = std::max(ws, dtype == TT_F64 ? ttk::gemm_ws_bytes<double>(rows, N, ranks[k], false)
+                                      : ttk::gemm_ws_bytes<float>(rows, N, ranks[k], false));
+    if (k < d - 1) buf = std::max(buf, (size_t)(rows * N) * el);
+    rows *= dims[k];
+  }
+  buf = (buf + 255) & ~(size_t)255;
+  return 2 * buf + ws + 256;
+}
+
+tt_status tt_full(int32_t d, const int64_t* dims, const int64_t* ranks, const void* const* cores,
+                  int32_t dtype, void* out, void* work, void* stream) {
+  g_err.clear();
+  if (d < 2 || d > TT_MAXD || !dims || !ranks || !cores || !out || !work)
+    return fail(TT_EINVAL, "bad argument");
+  if (dtype != TT_F32 && dtype != TT_F64) return fail(TT_EINVAL, "bad dtype");
+  if (ranks[0] != 1 || ranks[d] != 1) return fail(TT_EINVAL, "r_0 and r_d must be 1");
+  for (int k = 0; k < d; ++k) {
+    if (dims[k] < 1 || ranks[k + 1] < 1 || !cores[k]) return fail(TT_EINVAL, "bad dims/ranks/cores");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t el = dtype == TT_F64 ? 8 : 4;
+  int64_t rows = dims[0];
+  size_t buf = 0;
+  {
+    int64_t rr = dims[0];
+    for (int k = 1; k < d - 1; ++k) {
+      buf = std::max(buf, (size_t)(rr * dims[k] * ranks[k + 1]) * el);
+      rr *= dims[k];
+    }
+  }
+  buf = (buf + 255) & ~(size_t)255;
+  char* b0 = (char*)work;
+  char* b1 = b0 + buf;
+  char* wsp = b1 + buf;
+  const void* cur = cores[0];
+  for (int k = 1; k < d; ++k) {
+    const int64_t K = ranks[k], N = dims[k] * ranks[k + 1];
+    void* nxt = (k == d - 1) ? out : (void*)((k & 1) ? b0 : b1);
+    cudaError_t e;
+    if (dtype == TT_F64)
+      e = ttk::gemm<double>({(const double*)cur, K, true}, {(const double*)cores[k], N, true}, rows, N,
+                            K, (double*)nxt, N, nullptr, false, nullptr, wsp, st);
+    else
+      e = ttk::gemm<float>({(const float*)cur, K, true}, {(const float*)cores[k], N, true}, rows, N,
+                           K, (float*)nxt, N, nullptr, false, nullptr, wsp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tt_full contraction");
+    cur = nxt;
+    rows *= dims[k];
+  }
+  return TT_OK;
+}
+
+tt_status tt_eval_at(int32_t d, const int64_t* dims, const int64_t* ranks,
+                     const float* const* cores, const int64_t* idx, int64_t n, float* out,
+                     void* stream) {
+  g_err.clear();
+  if (!dims || !ranks || !cores || (n > 0 && (!idx || !out)) || n < 0)
+    return fail(TT_EINVAL, "bad argument");
+  cudaError_t e = ttk::eval_at(d, dims, ranks, cores, idx, n, out, (cudaStream_t)stream);
+  if (e == cudaErrorInvalidValue) return fail(TT_EINVAL, "d in [1,16], ranks in [1,64], r_0 = r_d = 1");
+  if (e != cudaSuccess) return cuda_fail(e, "tt_eval_at");
+  return TT_OK;
+}
+
+tt_status tt_eval_at_backward(int32_t d, const int64_t* dims, const int64_t* ranks,
+                              const float* const* cores, const int64_t* idx, int64_t n,
+                              const float* gout, float* const* grads, void* stream) {
+  g_err.clear();
+  if (!dims || !ranks || !cores || !grads || (n > 0 && (!idx || !gout)) || n < 0)
+    return fail(TT_EINVAL, "bad argument");
+  cudaError_t e = ttk::eval_at_backward(d, dims, ranks, cores, idx, n, gout, grads, (cudaStream_t)stream);
+  if (e == cudaErrorInvalidValue) return fail(TT_EINVAL, "d in [1,16], ranks in [1,64], r_0 = r_d = 1");
+  if (e != cudaSuccess) return cuda_fail(e, "tt_eval_at_backward");
+  return TT_OK;
+}
+
+tt_status tt_sketch_matrix(int64_t rows, int64_t cols, uint64_t seed, int32_t step, int32_t dtype,
+                           void* out, void* stream) {
+  g_err.clear();
+  if (rows < 0 || cols < 0 || !out || (dtype != TT_F32 && dtype != TT_F64))
+    return fail(TT_EINVAL, "bad argument");
+  cudaError_t e = ttk::fill_sketch(out, dtype == TT_F64, rows, cols, seed, (uint32_t)step, false,
+                                   (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tt_sketch_matrix");
+  return TT_OK;
+}
+
+const char* tt_last_error(void) { return g_err.c_str(); }
+
+const char* tt_version(void) { return "ttutv-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

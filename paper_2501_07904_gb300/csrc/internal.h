@@ -1,0 +1,76 @@
+// Host-side launchers shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace ttk {
+
+// Matrix operand: element (i, j) is p[i*ld + j] (row) or p[i + j*ld] (!row).
+template <typename T>
+struct Mat {
+  const T* p;
+  int64_t ld;
+  bool row;
+};
+
+// D (M x N) = A (M x K) B (K x N), FP32 or FP64 data.  FP32 products are
+// summed in FP32 over 16 products, those sums in FP32 over 32 tiles, and the
+// result in FP64, so an output carries no more than ~1e-6 relative rounding
+// from long inner products.  When the M x N tile grid cannot fill the GPU the
+// K range is split and the FP64 partials are summed in a fixed order.
+//   out     T output (ld ldo), may be null when out64 is given;
+//   out64   FP64 output (ld N), may be null;
+//   sym     A = B^T (a Gram matrix): only tiles on or above the diagonal are
+//           computed and the result is mirrored;
+//   sumsq   if non-null, receives sum of squares of the T-rounded outputs (FP64);
+//   accurate FP32 data only: products formed and summed in FP64 (exact
+//           products), for Gram matrices whose truncation errors must be
+//           resolved below FP32 rounding.
+// Scratch comes from `ws` (gemm_ws_bytes); returns the first launch error.
+template <typename T>
+size_t gemm_ws_bytes(int64_t M, int64_t N, int64_t K, bool fp64_out_or_sym);
+template <typename T>
+cudaError_t gemm(Mat<T> A, Mat<T> B, int64_t M, int64_t N, int64_t K, T* out, int64_t ldo,
+                 double* out64, bool sym, double* sumsq, void* ws, cudaStream_t st,
+                 bool accurate = false);
+
+// Small single-CTA factorizations of an n x n FP64 Gram matrix (n <= 256).
+enum SmallMode { SM_QLP = 0, SM_JACOBI = 1, SM_ORTH = 2 };
+struct SmallParams {
+  int n;                  // Gram size
+  int mode;               // SmallMode
+  int r_fixed;            // -1: rank by tolerance
+  int r_cap;              // largest admissible rank
+  double delta2;          // tolerance (used when normA2_dev == null)
+  const double* normA2_dev;  // if set: delta2 = delta2_scale * (*normA2_dev or trace)
+  int normA2_is_trace;    // 1: ||A||^2 is this Gram's trace (first exact step)
+  double delta2_scale;
+  const double* x2_dev;   // ||X||^2 of the factored matrix, null on the exact path (x2 = trace)
+  double piv_tol;         // relative pivot tolerance of the (pivoted) Cholesky
+  double shift_rel;       // SM_ORTH: diagonal shift, relative to trace(G)
+  const double* Gw;       // QLP/Jacobi on a sketch: W^T W of the range basis, or null
+};
+size_t small_ws_bytes(int n, bool fp64);
+// Z (n x ldz, written as T_out = float/double per zfp64) receives the basis Z_1
+// (QLP/Jacobi) or the orthonormalizing factor S (ORTH).
+cudaError_t small_factor(const double* G, SmallParams prm, bool fp64_math, void* Z, bool z_fp64,
+                         int ldz, void* ws, StepInfo* info, cudaStream_t st);
+
+// Elementwise helpers.
+cudaError_t fill_sketch(void* out, bool fp64, int64_t rows, int64_t cols, uint64_t seed,
+                        uint32_t step, bool identity, cudaStream_t st);
+cudaError_t cast_copy(const void* in, bool in64, void* out, bool out64, int64_t n, cudaStream_t st);
+cudaError_t copy2d(const void* in, int64_t ldi, bool trans, void* out, int64_t ldo, int64_t rows,
+                   int64_t cols, bool fp64, cudaStream_t st);
+size_t sumsq_ws_bytes(int64_t n);
+cudaError_t sumsq(const void* x, bool fp64, int64_t n, double* out, void* ws, cudaStream_t st);
+cudaError_t eval_at(int d, const int64_t* dims, const int64_t* ranks, const float* const* cores,
+                    const int64_t* idx, int64_t n, float* out, cudaStream_t st);
+cudaError_t eval_at_backward(int d, const int64_t* dims, const int64_t* ranks,
+                             const float* const* cores, const int64_t* idx, int64_t n,
+                             const float* gout, float* const* grads, cudaStream_t st);
+
+}  // namespace ttk

@@ -1,0 +1,563 @@
+// Single-CTA factorizations of the small (n <= 256) Gram matrix of each
+// sweep step, in FP32 or FP64.
+//
+//  SM_QLP     rank-revealing UTV of the factored matrix X through its Gram
+//             G = X^T X: pivoted Cholesky (= the R factor of column-pivoted
+//             QR of X, the rank-revealing QR the paper lists as a UTV, Sec. 2.2),
+//             then Stewart's pivoted QLP step -- column-pivoted Householder QR
+//             of R_1^T, L = R_2^T, Z = Pi_1 Q_2 -- with the truncation error
+//             of rank j read off as the trailing Frobenius norm after j
+//             Householder steps (= sum_{i>j} ||L(:,i)||^2, the ||[R12;R22]||
+//             of Eq. urv / ||[L21 L22]|| of Eq. ulv).  The rank is the smallest
+//             j >= 1 with error <= delta^2 (Alg. 2, step 5), or fixed.
+//  SM_JACOBI  TT-SVD: cyclic Jacobi eigen-decomposition of G; the error of
+//             rank j is the sum of the dropped eigenvalues.
+//  SM_ORTH    one pass of (shifted) Cholesky-QR of a sketch Y from
+//             G = Y^T Y: R = chol(G + shift I) in column order, S = R^{-1},
+//             so that Y S spans Y[:, :j] for every j -- the basis Householder
+//             QR of Y gives, up to signs.  With a shift of a few n u ||G||
+//             the factorization cannot break down; two further unshifted
+//             passes make the columns orthonormal to working precision
+//             (shifted Cholesky-QR3).  A column with no positive pivot even
+//             then (an exactly dependent column) is dropped: zero in S.
+#include <math.h>
+
+#include "internal.h"
+
+namespace ttk {
+namespace {
+
+constexpr int NT = 512;
+
+template <typename T>
+__device__ __forceinline__ void swap_vals(T& a, T& b) {
+  T t = a;
+  a = b;
+  b = t;
+}
+
+// Block-cooperative pivoted Cholesky of the symmetric n x n matrix A (full
+// storage, row-major).  Pivot = largest remaining diagonal (lowest index on
+// ties); stops when it is not above tol_rel * (largest initial diagonal).
+// On return rows 0..k1-1 of A hold R_1 (upper trapezoidal, columns in pivot
+// order), everything else is zero; perm[i] = original index of position i;
+// rem = remaining Schur-complement diagonal (clamped at 0), in FP64.
+template <typename T>
+__device__ int pivoted_cholesky(T* A, int n, int* perm, double tol_rel, double& rem, T* redt,
+                                int* redi, double* redd) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) perm[i] = i;
+  T v = lowest_value<T>();
+  int idx = 0x7fffffff;
+  for (int i = tid; i < n; i += nt) {
+    const T a = A[i * n + i];
+    if (a > v) {
+      v = a;
+      idx = i;
+    }
+  }
+  T d0;
+  int i0;
+  block_argmax(v, idx, redt, redi, d0, i0);
+  (void)i0;
+  int j = 0;
+  for (; j < n; ++j) {
+    v = lowest_value<T>();
+    idx = 0x7fffffff;
+    for (int i = j + tid; i < n; i += nt) {
+      const T a = A[i * n + i];
+      if (a > v) {
+        v = a;
+        idx = i;
+      }
+    }
+    T dp;
+    int p;
+    block_argmax(v, idx, redt, redi, dp, p);
+    if (!(dp > T(0)) || !((double)dp > tol_rel * (double)d0)) break;
+    if (p != j) {
+      for (int c = tid; c < n; c += nt) swap_vals(A[j * n + c], A[p * n + c]);
+      __syncthreads();
+      for (int r = tid; r < n; r += nt) swap_vals(A[r * n + j], A[r * n + p]);
+      if (tid == 0) swap_vals(perm[j], perm[p]);
+      __syncthreads();
+    }
+    const T rjj = sqrt(A[j * n + j]);
+    __syncthreads();
+    for (int c = j + tid; c < n; c += nt) A[j * n + c] = (c == j) ? rjj : A[j * n + c] / rjj;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int r = j + 1 + e / m, c = j + 1 + e % m;
+      A[r * n + c] -= A[j * n + r] * A[j * n + c];
+    }
+    __syncthreads();
+  }
+  const int k1 = j;
+  double s = 0.0;
+  for (int i = k1 + tid; i < n; i += nt) {
+    const double a = (double)A[i * n + i];
+    s += a > 0.0 ? a : 0.0;
+  }
+  rem = block_sum(s, redd);
+  for (int e = tid; e < n * n; e += nt) {
+    const int r = e / n, c = e % n;
+    if (r >= k1 || c < r) A[e] = T(0);
+  }
+  __syncthreads();
+  return k1;
+}
+
+// Cholesky of the symmetric n x n matrix A in column order (no pivoting),
+// skipping every column whose remaining diagonal is not above
+// tol_rel * (largest initial diagonal).  Kept rows of A then hold R (upper);
+// keep[j] marks the kept columns.  Returns the number kept.
+template <typename T>
+__device__ int cholesky_drop(T* A, int n, int* keep, double tol_rel, T* redt, int* redi) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  T v = lowest_value<T>();
+  int idx = 0x7fffffff;
+  for (int i = tid; i < n; i += nt) {
+    const T a = A[i * n + i];
+    if (a > v) {
+      v = a;
+      idx = i;
+    }
+  }
+  T d0;
+  int i0;
+  block_argmax(v, idx, redt, redi, d0, i0);
+  (void)i0;
+  int kept = 0;
+  for (int j = 0; j < n; ++j) {
+    const T djj = A[j * n + j];
+    const bool k = (djj > T(0)) && ((double)djj > tol_rel * (double)d0);
+    __syncthreads();
+    if (!k) {
+      for (int c = j + tid; c < n; c += nt) A[j * n + c] = T(0);
+      if (tid == 0) keep[j] = 0;
+      __syncthreads();
+      continue;
+    }
+    ++kept;
+    const T rjj = sqrt(djj);
+    for (int c = j + tid; c < n; c += nt) A[j * n + c] = (c == j) ? rjj : A[j * n + c] / rjj;
+    if (tid == 0) keep[j] = 1;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int r = j + 1 + e / m, c = j + 1 + e % m;
+      A[r * n + c] -= A[j * n + r] * A[j * n + c];
+    }
+    __syncthreads();
+  }
+  return kept;
+}
+
+template <typename T, typename ZT>
+__global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G, SmallParams prm,
+                                                   T* __restrict__ work, int* __restrict__ iwork,
+                                                   ZT* __restrict__ Z, int ldz,
+                                                   StepInfo* __restrict__ info) {
+  __shared__ T redt[32];
+  __shared__ int redi[32];
+  __shared__ double redd[32];
+  __shared__ T rc[kMaxSmall / 2], rs[kMaxSmall / 2];
+  __shared__ int rp[kMaxSmall / 2], rq[kMaxSmall / 2];
+  __shared__ int order[kMaxSmall];
+
+  const int n = prm.n, tid = threadIdx.x, nt = blockDim.x;
+  T* A = work;
+  T* Mq = work + (size_t)n * n;
+  T* Qe = work + (size_t)2 * n * n;
+  T* cn = work + (size_t)3 * n * n;
+  T* tau = cn + n;
+  T* Ti = tau + n;                 // n x n: T^{-1} of the whitening (prm.Gw)
+  int* perm1 = iwork;
+
+  double tr = 0.0;
+  if (prm.Gw) {
+    // Whitening: G_W = W^T W = T^T T (Cholesky, column order); factor
+    // T^{-T} G T^{-1}, the Gram of X Q for the orthonormal Q = W T^{-1}.
+    for (int e = tid; e < n * n; e += nt) Mq[e] = (T)prm.Gw[e];
+    __syncthreads();
+    const int kw = cholesky_drop(Mq, n, iwork + n, 0.0, redt, redi);
+    (void)kw;
+    for (int c = tid; c < n; c += nt) {
+      for (int i = c + 1; i < n; ++i) Ti[i * n + c] = T(0);
+      if (!iwork[n + c]) {
+        for (int i = 0; i <= c; ++i) Ti[i * n + c] = T(0);
+        continue;
+      }
+      Ti[c * n + c] = T(1) / Mq[c * n + c];
+      for (int i = c - 1; i >= 0; --i) {
+        T acc = T(0);
+        if (iwork[n + i])
+          for (int k = i + 1; k <= c; ++k) acc += Mq[i * n + k] * Ti[k * n + c];
+        Ti[i * n + c] = iwork[n + i] ? -acc / Mq[i * n + i] : T(0);
+      }
+    }
+    __syncthreads();
+    // Qe = G T^{-1}, then A = T^{-T} Qe
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, c = e % n;
+      T acc = T(0);
+      for (int k = 0; k <= c; ++k) acc += (T)G[i * n + k] * Ti[k * n + c];
+      Qe[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, c = e % n;
+      T acc = T(0);
+      for (int k = 0; k <= i; ++k) acc += Ti[k * n + i] * Qe[k * n + c];
+      A[e] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) tr += (double)A[i * n + i];
+  } else {
+    for (int e = tid; e < n * n; e += nt) A[e] = (T)G[e];
+    for (int i = tid; i < n; i += nt) tr += G[i * n + i];
+  }
+  tr = block_sum(tr, redd);
+  const double x2 = prm.x2_dev ? *prm.x2_dev : tr;
+  double normA2 = -1.0, delta2 = prm.delta2;
+  if (prm.normA2_dev) {
+    normA2 = prm.normA2_is_trace ? tr : *prm.normA2_dev;
+    delta2 = prm.delta2_scale * normA2;
+  }
+  const double mu2 = prm.x2_dev ? fmax(0.0, x2 - tr) : 0.0;
+  const bool finite = isfinite(tr) && isfinite(x2) && (normA2 < 0.0 || isfinite(normA2));
+  if (tid == 0) {
+    info->x2 = x2;
+    info->trace = tr;
+    info->mu2 = mu2;
+    info->delta2 = delta2;
+    info->normA2 = normA2;
+    info->status = finite ? 0 : 1;
+  }
+  __syncthreads();
+  if (!finite) {
+    for (int e = tid; e < n * ldz; e += nt) Z[e] = ZT(0);
+    if (tid == 0) {
+      info->r = 1;
+      info->k1 = 0;
+      info->nsteps = 0;
+      info->s1 = 0.0;
+      info->tail = 0.0;
+    }
+    return;
+  }
+
+  if (prm.mode == SM_ORTH) {
+    int* keep = iwork;
+    if (prm.shift_rel > 0.0) {
+      const T sh = (T)(prm.shift_rel * tr);
+      for (int i = tid; i < n; i += nt) A[i * n + i] += sh;
+      __syncthreads();
+    }
+    const int kept = cholesky_drop(A, n, keep, prm.piv_tol, redt, redi);
+    // Qe = R^{-1} on the kept columns, one column per thread (back substitution).
+    for (int c = tid; c < n; c += nt) {
+      if (!keep[c]) {
+        for (int i = 0; i < n; ++i) Qe[i * n + c] = T(0);
+        continue;
+      }
+      for (int i = c + 1; i < n; ++i) Qe[i * n + c] = T(0);
+      Qe[c * n + c] = T(1) / A[c * n + c];
+      for (int i = c - 1; i >= 0; --i) {
+        if (!keep[i]) {
+          Qe[i * n + c] = T(0);
+          continue;
+        }
+        T s = T(0);
+        for (int k = i + 1; k <= c; ++k)
+          if (keep[k]) s += A[i * n + k] * Qe[k * n + c];
+        Qe[i * n + c] = -s / A[i * n + i];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < n * ldz; e += nt) {
+      const int j = e / ldz, c = e % ldz;
+      Z[(size_t)j * ldz + c] = (c < n) ? (ZT)Qe[j * n + c] : ZT(0);
+    }
+    if (tid == 0) {
+      info->r = kept;
+      info->k1 = kept;
+      info->nsteps = n;
+      info->s1 = 0.0;
+      info->tail = 0.0;
+    }
+    return;
+  }
+
+  const bool fixed = prm.r_fixed >= 1;
+  const int rt = fixed ? min(prm.r_fixed, prm.r_cap) : -1;
+
+  if (prm.mode == SM_JACOBI) {
+    T* V = Mq;
+    for (int e = tid; e < n * n; e += nt) V[e] = (e / n == e % n) ? T(1) : T(0);
+    const int nn = n + (n & 1);
+    const int npairs = nn / 2;
+    const double eps_t = sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920929e-07;
+    int sweep = 0;
+    bool conv = false;
+    for (; sweep < 60; ++sweep) {
+      double off = 0.0, dg = 0.0;
+      for (int e = tid; e < n * n; e += nt) {
+        const double a = (double)A[e];
+        if (e / n == e % n)
+          dg += a * a;
+        else
+          off += a * a;
+      }
+      off = block_sum(off, redd);
+      dg = block_sum(dg, redd);
+      if (off <= (double)n * n * eps_t * eps_t * dg) {
+        conv = true;
+        break;
+      }
+      for (int t = 0; t < nn - 1; ++t) {
+        for (int i = tid; i < npairs; i += nt) {
+          const int x = (i == 0) ? 0 : 1 + ((i - 1 + t) % (nn - 1));
+          const int y = 1 + ((nn - 2 - i + t) % (nn - 1));
+          const int p = min(x, y), q = max(x, y);
+          T c = T(1), s = T(0);
+          if (q < n) {
+            const T apq = A[p * n + q];
+            if (apq != T(0)) {
+              const T tt = (A[q * n + q] - A[p * n + p]) / (T(2) * apq);
+              const T sg = tt >= T(0) ? T(1) : T(-1);
+              const T t1 = sg / (fabs(tt) + sqrt(T(1) + tt * tt));
+              c = T(1) / sqrt(T(1) + t1 * t1);
+              s = t1 * c;
+            }
+          }
+          rc[i] = c;
+          rs[i] = s;
+          rp[i] = p;
+          rq[i] = q < n ? q : -1;
+        }
+        __syncthreads();
+        for (int e = tid; e < npairs * n; e += nt) {
+          const int i = e / n, k = e % n;
+          const int p = rp[i], q = rq[i];
+          if (q < 0 || rs[i] == T(0)) continue;
+          const T c = rc[i], s = rs[i];
+          const T ap = A[p * n + k], aq = A[q * n + k];
+          A[p * n + k] = c * ap - s * aq;
+          A[q * n + k] = s * ap + c * aq;
+        }
+        __syncthreads();
+        for (int e = tid; e < npairs * n; e += nt) {
+          const int i = e / n, k = e % n;
+          const int p = rp[i], q = rq[i];
+          if (q < 0 || rs[i] == T(0)) continue;
+          const T c = rc[i], s = rs[i];
+          const T ap = A[k * n + p], aq = A[k * n + q];
+          A[k * n + p] = c * ap - s * aq;
+          A[k * n + q] = s * ap + c * aq;
+          const T vp = V[k * n + p], vq = V[k * n + q];
+          V[k * n + p] = c * vp - s * vq;
+          V[k * n + q] = s * vp + c * vq;
+        }
+        __syncthreads();
+      }
+    }
+    // order eigenvalues descending (stable: lower index first on ties)
+    for (int i = tid; i < n; i += nt) {
+      const T li = A[i * n + i];
+      int rank = 0;
+      for (int k = 0; k < n; ++k) {
+        const T lk = A[k * n + k];
+        if (lk > li || (lk == li && k < i)) ++rank;
+      }
+      order[rank] = i;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double acc = mu2;
+      info->tails[n] = acc;
+      for (int k = n - 1; k >= 0; --k) {
+        const double l = (double)A[order[k] * n + order[k]];
+        acc += l > 0.0 ? l : 0.0;
+        info->tails[k] = acc;
+      }
+      int r;
+      if (fixed) {
+        r = rt;
+      } else {
+        r = prm.r_cap;
+        for (int k = 1; k <= prm.r_cap; ++k)
+          if (info->tails[k] <= delta2) {
+            r = k;
+            break;
+          }
+      }
+      info->r = r;
+      info->k1 = n;
+      info->nsteps = sweep;
+      info->s1 = 0.0;
+      info->tail = info->tails[r];
+      if (!conv) info->status |= 2;
+    }
+    __syncthreads();
+    const int r = info->r;
+    for (int e = tid; e < n * r; e += nt) {
+      const int i = e / r, c = e % r;
+      T z;
+      if (prm.Gw) {
+        z = T(0);
+        for (int k = i; k < n; ++k) z += Ti[i * n + k] * V[k * n + order[c]];
+      } else {
+        z = V[i * n + order[c]];
+      }
+      Z[(size_t)i * ldz + c] = (ZT)z;
+    }
+    return;
+  }
+
+  // ---- SM_QLP ----
+  double s1;
+  const int k1 = pivoted_cholesky(A, n, perm1, prm.piv_tol, s1, redt, redi, redd);
+  // M = R_1^T (n x k1): rows are pivoted columns of X, columns the Cholesky rows.
+  for (int e = tid; e < n * k1; e += nt) {
+    const int i = e / k1, c = e % k1;
+    Mq[i * n + c] = A[c * n + i];
+  }
+  __syncthreads();
+  const int kk = min(n, k1);
+  int j = 0, r = 1;
+  for (;; ++j) {
+    double part = 0.0;
+    for (int c = j + tid; c < k1; c += nt) {
+      T s = T(0);
+      for (int i = j; i < n; ++i) {
+        const T x = Mq[i * n + c];
+        s += x * x;
+      }
+      cn[c] = s;
+      part += (double)s;
+    }
+    const double trail = block_sum(part, redd);
+    const double tj = mu2 + s1 + trail;
+    if (tid == 0) info->tails[j] = tj;
+    if (fixed) {
+      if (j == rt || j >= kk) {
+        r = rt;
+        break;
+      }
+    } else {
+      if (j >= 1 && tj <= delta2) {
+        r = min(j, prm.r_cap);
+        break;
+      }
+      if (j >= kk || j >= prm.r_cap) {
+        r = max(1, min(j, prm.r_cap));
+        break;
+      }
+    }
+    // pivot: largest remaining column norm
+    T v = lowest_value<T>();
+    int idx = 0x7fffffff;
+    for (int c = j + tid; c < k1; c += nt) {
+      if (cn[c] > v) {
+        v = cn[c];
+        idx = c;
+      }
+    }
+    T cq;
+    int q;
+    block_argmax(v, idx, redt, redi, cq, q);
+    if (q != j) {
+      for (int i = tid; i < n; i += nt) swap_vals(Mq[i * n + j], Mq[i * n + q]);
+    }
+    __syncthreads();
+    const T alpha = sqrt(cq > T(0) ? cq : T(0));
+    const T x0 = Mq[j * n + j];
+    const T sg = x0 >= T(0) ? T(1) : T(-1);
+    const T vtv = T(2) * (alpha * alpha + sg * alpha * x0);
+    const T tj_ = vtv > T(0) ? T(2) / vtv : T(0);
+    __syncthreads();
+    if (tid == 0) {
+      Mq[j * n + j] = x0 + sg * alpha;
+      tau[j] = tj_;
+    }
+    __syncthreads();
+    for (int c = j + 1 + tid; c < k1; c += nt) {
+      T w = T(0);
+      for (int i = j; i < n; ++i) w += Mq[i * n + j] * Mq[i * n + c];
+      w *= tj_;
+      for (int i = j; i < n; ++i) Mq[i * n + c] -= w * Mq[i * n + j];
+    }
+    __syncthreads();
+  }
+  const int nref = j;  // reflectors 0..nref-1 were formed
+  // Z_1 = Pi_1 Q_2(:, 0:r): apply H_0 ... H_{nref-1} to the unit vectors.
+  for (int c = tid; c < r; c += nt) {
+    for (int i = 0; i < n; ++i) Qe[i * n + c] = (i == c) ? T(1) : T(0);
+    for (int h = min(nref - 1, c); h >= 0; --h) {
+      T w = T(0);
+      for (int i = h; i < n; ++i) w += Mq[i * n + h] * Qe[i * n + c];
+      w *= tau[h];
+      for (int i = h; i < n; ++i) Qe[i * n + c] -= w * Mq[i * n + h];
+    }
+  }
+  __syncthreads();
+  if (prm.Gw) {
+    // Z_1 = T^{-1} Pi_1 Q_2(:, 0:r) (Mq is free again: hold Pi_1 Q_2 there)
+    for (int e = tid; e < n * r; e += nt) {
+      const int i = e / r, c = e % r;
+      Mq[perm1[i] * n + c] = Qe[i * n + c];
+    }
+    __syncthreads();
+    for (int e = tid; e < n * r; e += nt) {
+      const int i = e / r, c = e % r;
+      T acc = T(0);
+      for (int k = i; k < n; ++k) acc += Ti[i * n + k] * Mq[k * n + c];
+      Z[(size_t)i * ldz + c] = (ZT)acc;
+    }
+  } else {
+    for (int e = tid; e < n * r; e += nt) {
+      const int i = e / r, c = e % r;
+      Z[(size_t)perm1[i] * ldz + c] = (ZT)Qe[i * n + c];
+    }
+  }
+  if (tid == 0) {
+    info->r = r;
+    info->k1 = k1;
+    info->nsteps = j;
+    info->s1 = s1;
+    info->tail = info->tails[min(r, j)];
+  }
+}
+
+template <typename T, typename ZT>
+cudaError_t launch_small(const double* G, SmallParams prm, void* Z, int ldz, void* ws,
+                         StepInfo* info, cudaStream_t st) {
+  const int n = prm.n;
+  T* work = (T*)ws;
+  size_t off = ((size_t)(4 * n * n + 2 * n) * sizeof(T) + 255) & ~(size_t)255;
+  int* iwork = (int*)((char*)ws + off);
+  small_kernel<T, ZT><<<1, NT, 0, st>>>(G, prm, work, iwork, (ZT*)Z, ldz, info);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t small_ws_bytes(int n, bool fp64) {
+  const size_t el = fp64 ? 8 : 4;
+  size_t off = ((size_t)(4 * n * n + 2 * n) * el + 255) & ~(size_t)255;
+  return off + (size_t)2 * n * sizeof(int) + 256;
+}
+
+cudaError_t small_factor(const double* G, SmallParams prm, bool fp64_math, void* Z, bool z_fp64,
+                         int ldz, void* ws, StepInfo* info, cudaStream_t st) {
+  if (prm.n < 1 || prm.n > kMaxSmall) return cudaErrorInvalidValue;
+  if (fp64_math)
+    return z_fp64 ? launch_small<double, double>(G, prm, Z, ldz, ws, info, st)
+                  : launch_small<double, float>(G, prm, Z, ldz, ws, info, st);
+  return z_fp64 ? launch_small<float, double>(G, prm, Z, ldz, ws, info, st)
+                : launch_small<float, float>(G, prm, Z, ldz, ws, info, st);
+}
+
+}  // namespace ttk

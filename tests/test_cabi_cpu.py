@@ -1,0 +1,86 @@
+"""The C-ABI library loads and exports every entry point include/ttutv.h
+declares; argument validation answers without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2501_07904_gb300 as tu
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ttutv.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(tt_[a-z_]+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(tu.LIB_PATH):
+        from paper_2501_07904_gb300 import build
+        build.build()
+    return tu.lib()
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(tu.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_version_and_defaults(L):
+    assert b"sm_103a" in L.tt_version()
+    o = tu.tt_opts()
+    L.tt_opts_default(ctypes.byref(o))
+    assert (o.precision, o.small_precision, o.oversample, o.l_full, o.seed) == (1, 0, 16, 256, 0)
+
+
+def _call(L, A=1, dtype=0, d=3, dims=(4, 5, 6), eps=0.1, fixed=None, variant=0, direction=0, opts=None):
+    res = tu.tt_result()
+    fr = tu._i64(fixed) if fixed is not None else None
+    return L.tt_utv(ctypes.c_void_p(A) if A else None, dtype, d, tu._i64(dims) if dims else None,
+                    eps, fr, variant, direction, opts, tu.ALLOC_FN(0), tu.FREE_FN(0), None, None,
+                    ctypes.byref(res))
+
+
+@pytest.mark.parametrize("kw, status", [
+    (dict(A=0), 1), (dict(dims=None), 1), (dict(d=1), 1), (dict(d=17, dims=[2] * 17), 1),
+    (dict(dims=(4, 0, 6)), 1), (dict(eps=0.0), 1), (dict(eps=-1.0), 1), (dict(eps=float("nan")), 1),
+    (dict(fixed=(2, 0)), 1), (dict(dtype=7), 1), (dict(variant=0, direction=1), 7),
+    (dict(variant=1, direction=0), 7), (dict(variant=5), 1),
+])
+def test_invalid_arguments_rejected(L, kw, status):
+    assert _call(L, **kw) == status
+    assert L.tt_last_error() != b""
+
+
+def test_invalid_options_rejected(L):
+    o = tu.tt_opts()
+    L.tt_opts_default(ctypes.byref(o))
+    o.l_full = 300
+    assert _call(L, opts=ctypes.byref(o)) == 1
+    L.tt_opts_default(ctypes.byref(o))
+    w = (ctypes.c_double * 2)(0.5, 0.5)          # sum w^2 != 1
+    o.weights = ctypes.cast(w, ctypes.POINTER(ctypes.c_double))
+    assert _call(L, opts=ctypes.byref(o)) == 1
+
+
+def test_eval_rejects_bad_ranks(L):
+    dims, ranks = tu._i64([3, 3]), tu._i64([1, 65, 1])
+    ptrs = (ctypes.c_void_p * 2)(1, 1)
+    assert L.tt_eval_at(2, dims, ranks, ptrs, ctypes.c_void_p(1), 4, ctypes.c_void_p(1), None) == 1
+    ranks = tu._i64([2, 3, 1])
+    assert L.tt_eval_at(2, dims, ranks, ptrs, ctypes.c_void_p(1), 4, ctypes.c_void_p(1), None) == 1
+
+
+def test_full_work_bytes(L):
+    n = L.tt_full_work_bytes(3, tu._i64([4, 5, 6]), tu._i64([1, 2, 3, 1]), 0)
+    assert n >= 2 * 4 * 5 * 3 * 4
+    assert L.tt_full_work_bytes(1, tu._i64([4]), tu._i64([1, 1]), 0) == 0
