@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark of the TT-UTV sweep on GB300.
+
+Workload (default "c5"): a 128^4 FP32 tensor (1 GiB) built from Gaussian TT
+cores of ranks (1,64,64,64,1) plus Gaussian noise at 1e-3 relative norm,
+decomposed by TT-URV right-to-left (Alg. 3 with the prescribed-accuracy rule
+of Sec. 3.1) at eps = 1e-2.  One step = one full sweep (all unfoldings, all
+kernels, the per-step rank reads included).  Metric: tensor GB/s = bytes of
+the input tensor / sweep time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|mixed]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+
+Under torchrun (N > 1) every rank decomposes its own copy of the workload
+(independent problems, no collective on the data path: weak scaling); rank 0
+prints the JSON line with the whole-job throughput over the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "TT-UTV sweep tensor GB/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz max clock / 1e3
+
+WORKLOADS = {
+    "c5": dict(dims=(128, 128, 128, 128), ranks=(1, 64, 64, 64, 1), rel_noise=1e-3, seed=0,
+               eps=1e-2, variant="URV",
+               desc="128^4 f32 tensor from Gaussian TT cores ranks (1,64,64,64,1) + 1e-3 relative "
+                    "Gaussian noise, eps=1e-2, TT-URV right-to-left"),
+    "c5-half": dict(dims=(64, 128, 128, 128), ranks=(1, 64, 64, 64, 1), rel_noise=1e-3, seed=0,
+                    eps=1e-2, variant="URV",
+                    desc="64x128^3 f32 (512 MiB) slab of the 128^4 workload's generator, for "
+                         "profiler captures"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def make_input(wl):
+    return synth.gaussian_tt(wl["dims"], wl["ranks"], wl["rel_noise"], wl["seed"], np.float32)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, enabled=True):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        self.enabled = enabled
+
+    def __enter__(self):
+        if not self.enabled:
+            return self
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------- roofline inputs
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path)), "measured"
+        except ValueError:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2501_07904_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it still matches the source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    ent = d.get("kernels", {}).get(f"{workload}:{kernel_key}")
+    return None if ent is None else ent.get("traffic_bytes")
+
+
+def phase_model(wl, ranks):
+    """Algorithmic bytes and flops of the dominant per-step kernels (first
+    unfolding of the right-to-left sweep: C is prod(I_1..I_{d-1}) x I_d)."""
+    dims = wl["dims"]
+    m = int(np.prod(dims[:-1]))
+    n = dims[-1]
+    r = ranks[-2]
+    return {
+        "gram": dict(bytes=4.0 * m * n, flops=float(m) * n * (n + 1)),
+        "carry": dict(bytes=4.0 * m * n + 4.0 * m * r, flops=2.0 * m * n * r),
+    }
+
+
+# --------------------------------------------------------------- our arm
+
+def run_ours(args, wl, rank, world):
+    import torch
+
+    import paper_2501_07904_gb300 as tu
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    A_np = make_input(wl)
+    nbytes = A_np.nbytes
+    A_host = torch.from_numpy(A_np).pin_memory()
+    A = A_host.to(dev)
+    st = torch.cuda.current_stream()
+    kw = dict(eps=wl["eps"], variant=wl["variant"], precision=args.precision)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        res = tu.tt_utv(A, **kw)
+    torch.cuda.synchronize()
+    ranks = res.ranks
+
+    # timed region: K sweeps, device-resident input (1 GiB >> 129 MB L2)
+    phase_sum = None
+    barrier()
+    torch.cuda.synchronize()
+    l0 = tu.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index, not args.no_clocks) as clk:
+        t0 = time.perf_counter()
+        ev0.record(st)
+        for _ in range(args.steps):
+            res = tu.tt_utv(A, timing=True, **kw)
+            ph = res.info["phase_ms"]
+            if phase_sum is None:
+                phase_sum = [dict(p) for p in ph]
+            else:
+                for a, b in zip(phase_sum, ph):
+                    for key in a:
+                        a[key] += b[key]
+        ev1.record(st)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier()
+    launches = tu.kernel_launches() - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nbytes / (ms * 1e-3) / 1e9
+    clocks = clk.summary()
+    phases = [{k: v / args.steps for k, v in p.items()} for p in phase_sum]
+
+    # roofline of the dominant kernel (largest per-sweep phase time)
+    model = phase_model(wl, ranks)
+    peaks, peak_src = measured_peaks()
+    dom_step, dom_phase = max(((s, k) for s, p in enumerate(phases) for k in p), key=lambda sk: phases[sk[0]][sk[1]])
+    dom_ms = phases[dom_step][dom_phase]
+    roof = None
+    if dom_step == 0 and dom_phase in model:
+        mm = model[dom_phase]
+        gbs = mm["bytes"] / (dom_ms * 1e-3) / 1e9
+        tfl = mm["flops"] / (dom_ms * 1e-3) / 1e12
+        f_hbm = gbs / peaks["hbm_gbs"]
+        f_alu = tfl / FP32_PEAK_TFLOPS
+        if f_alu > f_hbm:
+            roof = {"bound": "alu", "achieved": round(tfl, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
+                    "unit": "TFLOP/s", "frac": round(f_alu, 4),
+                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
+                    "hbm_frac": round(f_hbm, 4), "hbm_gbs": round(gbs, 1)}
+        else:
+            roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": round(f_hbm, 4), "peak_source": peak_src,
+                    "alu_frac": round(f_alu, 4)}
+        roof.update({"kernel": f"step0:{dom_phase}", "ms": round(dom_ms, 4),
+                     "algorithmic_bytes": mm["bytes"], "algorithmic_flops": mm["flops"],
+                     "traffic": ncu_traffic(dom_phase, args.workload)})
+
+    # accuracy of this run (untimed): error equality, RSE, sampled diff vs the oracle
+    acc = accuracy(tu, torch, A, res, args.workload)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        core_bytes = sum(c.numel() * c.element_size() for c in res.cores)
+        outs = [torch.empty(c.shape, dtype=c.dtype, pin_memory=True) for c in res.cores]
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            r2 = tu.tt_utv(A_host, **kw)
+            outs = [torch.empty(c.shape, dtype=c.dtype, pin_memory=True) for c in r2.cores] \
+                if [tuple(c.shape) for c in r2.cores] != [tuple(o.shape) for o in outs] else outs
+            for o, c in zip(outs, r2.cores):
+                o.copy_(c, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            t = torch.tensor([ms_e2e], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": round(world * nbytes / (ms_e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
+               "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": int(nbytes),
+               "d2h_bytes_per_step": int(core_bytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {wl['desc']}", "precision": args.precision,
+                   "l2": "inputs larger than L2 (1 GiB tensor, 512 MiB carry)",
+                   "parallelism": f"replicas x{world} (independent problems)", "ranks": ranks,
+                   "bytes_per_step": nbytes},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clocks, "accuracy": acc,
+        "phase_ms": [{k: round(v, 4) for k, v in p.items() if v > 0} for p in phases],
+        "wall_s": round(wall, 3),
+    }
+    return out
+
+
+def accuracy(tu, torch, A, res, workload):
+    out = {"ranks": res.ranks}
+    normA2 = float((A.double() ** 2).sum())
+    full = tu.tt_full(res.cores)
+    err2 = 0.0
+    for a, b in zip(A.reshape(-1).split(1 << 26), full.reshape(-1).split(1 << 26)):
+        err2 += float(((a.double() - b.double()) ** 2).sum())
+    del full
+    out["rse"] = (err2 / normA2) ** 0.5
+    out["tails_over_err2"] = sum(res.tail_sq) / err2 if err2 > 0 else None
+    gold = os.path.join(ROOT, "tests", "golden", f"{workload.split('-')[0]}_URV.npz")
+    if workload == "c5" and os.path.exists(gold):
+        g = np.load(gold)
+        vals = tu.tt_eval_at([c.float() for c in res.cores],
+                             torch.from_numpy(g["sample_idx"]).to(A.device)).double().cpu().numpy()
+        out["oracle_ranks"] = [int(x) for x in g["ranks"]]
+        out["oracle_rse"] = float(g["rse"])
+        out["rel_err_vs_oracle_sampled"] = float(
+            np.sqrt(np.sum((vals - g["sample_val"]) ** 2) / np.sum(g["sample_ref"] ** 2)))
+    return out
+
+
+# -------------------------------------------------------- CPU oracle arms
+
+def cpu_sample(wl):
+    """Bounded sample of the workload for the oracle: the first I1' slices of mode 1."""
+    dims = list(wl["dims"])
+    s = 4
+    return s, dims
+
+
+def cpu_baseline(wl, repeats=1):
+    from oracle import tt as otc  # the FP64 oracle: only this leg of bench.py runs it
+
+    s, dims = cpu_sample(wl)
+    A = make_input(wl)[:s].astype(np.float64)
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        otc.tt_utv(A, eps=wl["eps"], variant=wl["variant"])
+    dt = (time.perf_counter() - t0) / repeats
+    nbytes = A.size * 4
+    return {"value": round(nbytes / dt / 1e9, 4), "unit": "GB/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"first {s} of {dims[0]} mode-1 slices ({s}x{'x'.join(map(str, dims[1:]))} f32, "
+                      f"{nbytes / 1e6:.0f} MB), same eps and sweep; {dt:.2f} s per sweep",
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return None
+    s, dims = cpu_sample(wl)
+    from oracle import tt as otc
+
+    A = make_input(wl)[:s].astype(np.float64)
+    nbytes = A.size * 4
+    for _ in range(min(args.warmup, 1)):
+        otc.tt_utv(A, eps=wl["eps"], variant=wl["variant"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        otc.tt_utv(A, eps=wl["eps"], variant=wl["variant"])
+    dt = (time.perf_counter() - t0) / args.steps
+    value = nbytes / dt / 1e9
+    sample = (f"first {s} of {dims[0]} mode-1 slices ({s}x{'x'.join(map(str, dims[1:]))} f32, "
+              f"{nbytes / 1e6:.0f} MB), same eps and sweep")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}", "precision": "fp64 oracle",
+                       "l2": "n/a (CPU)", "parallelism": "1 process, host cores"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    wl = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, wl, rank, world)
+    else:
+        out = run_ours(args, wl, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,19 @@ typedef enum { TT_P_FP64 = 0, TT_P_FP32 = 1, TT_P_MIXED = 2 } tt_precision;
  *  FP64 otherwise; TT_SMALL_FP32 / TT_SMALL_FP64 force one. */
 typedef enum { TT_SMALL_AUTO = 0, TT_SMALL_FP32 = 1, TT_SMALL_FP64 = 2 } tt_small_precision;
 
+/* Phases timed when tt_opts.phase_ms is set (device time from CUDA events
+ * recorded on the sweep's stream). */
+typedef enum {
+  TT_PH_GRAM = 0,     /* exact path: Gram of the basis side */
+  TT_PH_SMALL = 1,    /* small factorization (QLP / Jacobi) */
+  TT_PH_CARRY = 2,    /* carry product (the next unfolding) */
+  TT_PH_CORE = 3,     /* core formation */
+  TT_PH_SKETCH = 4,   /* sketch matrix and Y = C^T Omega / C Omega */
+  TT_PH_ORTH = 5,     /* Cholesky-QR3 of Y */
+  TT_PH_PROJECT = 6,  /* B = C W / C^T W and its Gram */
+  TT_NPHASES = 8
+} tt_phase;
+
 typedef struct {
   int32_t precision;        /* tt_precision, default TT_P_FP32 */
   int32_t small_precision;  /* tt_small_precision, default TT_SMALL_AUTO */
@@ -72,6 +85,9 @@ typedef struct {
   int32_t l_full;           /* basis side <= l_full columns -> exact Gram path, default 256 (max 256) */
   uint64_t seed;            /* Philox key of the Rademacher sketch, default 0 */
   const double* weights;    /* host, d-1 error weights w_k with sum w_k^2 = 1; NULL = equal 1/sqrt(d-1) */
+  double* phase_ms;         /* host, TT_MAXD * TT_NPHASES doubles [sweep step][tt_phase], or NULL.
+                               Milliseconds of device time are ADDED to it; the sweep step index is
+                               0 for the first factored unfolding. */
 } tt_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -170,6 +186,10 @@ tt_status tt_eval_at_backward(int32_t d, const int64_t* dims, const int64_t* ran
  * sweep draws it. */
 tt_status tt_sketch_matrix(int64_t rows, int64_t cols, uint64_t seed, int32_t step, int32_t dtype,
                            void* out, void* stream);
+
+/* Number of kernels this library has launched in the process so far
+ * (all threads); a diagnostic for counting launches per call. */
+uint64_t tt_kernel_launches(void);
 
 /* Thread-local message of the last failure ("" if none). */
 const char* tt_last_error(void);

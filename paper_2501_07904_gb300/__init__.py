@@ -34,8 +34,10 @@ TT_RL, TT_LR = 0, 1
 
 # Every symbol include/ttutv.h declares.
 EXPORTS = ["tt_opts_default", "tt_utv", "tt_svd", "tt_result_free", "tt_full_work_bytes",
-           "tt_full", "tt_eval_at", "tt_eval_at_backward", "tt_sketch_matrix", "tt_last_error",
-           "tt_version"]
+           "tt_full", "tt_eval_at", "tt_eval_at_backward", "tt_sketch_matrix", "tt_kernel_launches",
+           "tt_last_error", "tt_version"]
+PHASES = ["gram", "small", "carry", "core", "sketch", "orth", "project"]
+TT_NPHASES = 8
 
 
 class TTError(RuntimeError):
@@ -47,7 +49,8 @@ class TTError(RuntimeError):
 class tt_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("small_precision", ctypes.c_int32),
                 ("oversample", ctypes.c_int32), ("l_full", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("weights", ctypes.POINTER(ctypes.c_double))]
+                ("seed", ctypes.c_uint64), ("weights", ctypes.POINTER(ctypes.c_double)),
+                ("phase_ms", ctypes.POINTER(ctypes.c_double))]
 
 
 class tt_result(ctypes.Structure):
@@ -97,6 +100,8 @@ def lib():
     L.tt_eval_at_backward.restype = I32
     L.tt_sketch_matrix.argtypes = [I64, I64, U64, I32, I32, P, P]
     L.tt_sketch_matrix.restype = I32
+    L.tt_kernel_launches.argtypes = []
+    L.tt_kernel_launches.restype = ctypes.c_uint64
     L.tt_last_error.argtypes = []
     L.tt_last_error.restype = ctypes.c_char_p
     L.tt_version.argtypes = []
@@ -162,7 +167,8 @@ class TTResult:
     info: dict = field(default_factory=dict)
 
 
-def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream):
+def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream,
+           timing=False):
     if not isinstance(A, torch.Tensor):
         raise TypeError("A must be a torch.Tensor")
     if A.dtype not in (torch.float32, torch.float64):
@@ -182,6 +188,10 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
     if weights is not None:
         wbuf = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
         opts.weights = ctypes.cast(wbuf, ctypes.POINTER(ctypes.c_double))
+    tbuf = None
+    if timing:
+        tbuf = (ctypes.c_double * (TT_MAXD * TT_NPHASES))()
+        opts.phase_ms = ctypes.cast(tbuf, ctypes.POINTER(ctypes.c_double))
     dims = _i64(A.shape)
     fr = _i64(ranks) if ranks is not None else None
     alloc = _TorchAllocator(dev)
@@ -200,16 +210,20 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
         cores = [alloc.take(res.cores[k], (rk[k], int(res.dims[k]), rk[k + 1]), out_dtype)
                  for k in range(d)]
     alloc.live.clear()
+    info = {}
+    if timing:
+        info["phase_ms"] = [{ph: tbuf[s * TT_NPHASES + i] for i, ph in enumerate(PHASES)}
+                            for s in range(d - 1)]
     return TTResult(cores=cores, ranks=rk, norm_sq=float(res.norm_sq),
                     tail_sq=[float(res.tail_sq[k]) for k in range(d - 1)],
                     delta_sq=[float(res.delta_sq[k]) for k in range(d - 1)],
                     sketch_l=[int(res.sketch_l[k]) for k in range(d - 1)],
                     small_fp64=[int(res.small_fp64[k]) for k in range(d - 1)],
-                    orth="right" if res.orth == 0 else "left")
+                    orth="right" if res.orth == 0 else "left", info=info)
 
 
 def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, oversample=16,
-           l_full=256, small="auto", weights=None, stream=None):
+           l_full=256, small="auto", weights=None, stream=None, timing=False):
     """TT-URV right-to-left (Alg. 3) or TT-ULV left-to-right (Alg. 1/2).
 
     Give ``eps`` (prescribed relative accuracy, Alg. 2) or ``ranks``
@@ -219,7 +233,7 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
         raise ValueError("give exactly one of eps or ranks")
     v = {"URV": (TT_URV, TT_RL), "ULV": (TT_ULV, TT_LR)}[variant]
     return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
-                  weights, stream)
+                  weights, stream, timing)
 
 
 def tt_svd(A, eps=None, ranks=None, direction="LR", precision="fp32", l_full=256, small="auto",
@@ -314,3 +328,8 @@ def sketch_matrix(rows, cols, seed=0, step=0, dtype=torch.float32, device="cuda"
 
 def version():
     return lib().tt_version().decode()
+
+
+def kernel_launches():
+    """Kernels this library has launched in the process so far."""
+    return int(lib().tt_kernel_launches())

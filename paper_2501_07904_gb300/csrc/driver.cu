@@ -132,6 +132,52 @@ int64_t sketch_size(int64_t nb, int64_t no, int64_t r_prev, int64_t p, int64_t r
   return std::min<int64_t>(l, ttk::kMaxSmall);
 }
 
+// CUDA-event timing of the sweep's phases (only when opts.phase_ms is set).
+struct PhaseTimer {
+  double* out = nullptr;
+  cudaStream_t st = nullptr;
+  struct Rec {
+    int step, phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  int open = -1;
+  void begin(int step, int phase) {
+    if (!out) return;
+    Rec r{step, phase, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaEventRecord(r.a, st);
+    recs.push_back(r);
+    open = (int)recs.size() - 1;
+  }
+  void end() {
+    if (!out || open < 0) return;
+    cudaEventRecord(recs[open].b, st);
+    open = -1;
+  }
+  // after a stream synchronization
+  void collect() {
+    for (auto& r : recs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && out)
+        out[r.step * TT_NPHASES + r.phase] += ms;
+      cudaGetLastError();
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    recs.clear();
+  }
+  ~PhaseTimer() {
+    for (auto& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+};
+
 struct SweepCfg {
   bool urv;   // basis on the column side, right-to-left
   bool svd;   // Jacobi small factor (TT-SVD)
@@ -207,6 +253,9 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     }
   } guard{cores, al};
 
+  PhaseTimer tm;
+  tm.out = o.phase_ms;
+  tm.st = st;
   std::vector<double> x2s(d, 0.0);
   const W* C = A;
   Buf cbuf(&al);
@@ -267,12 +316,14 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       TT_ALLOC(gb, (size_t)nb * nb * sizeof(double));
       TT_ALLOC(ws, std::max(ttk::gemm_ws_bytes<W>(nb, nb, no, true), ttk::small_ws_bytes((int)nb, true)));
       const bool acc = !W64 && tight(nb);
+      tm.begin(s, TT_PH_GRAM);
       if (cfg.urv)
         TT_CK(ttk::gemm<W>({C, n, false}, {C, n, true}, n, n, m, nullptr, 0, gb.as<double>(), true,
                            nullptr, ws.p, st, acc), "Gram C^T C");
       else
         TT_CK(ttk::gemm<W>({C, n, true}, {C, n, false}, m, m, n, nullptr, 0, gb.as<double>(), true,
                            nullptr, ws.p, st, acc), "Gram C C^T");
+      tm.end();
       small64 = choose_small64(nb);
       prm.n = (int)nb;
       if (first) {
@@ -283,10 +334,13 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       prm.piv_tol = small64 ? 1e-15 : 1e-6;
       TT_ALLOC(zb, (size_t)nb * nb * sizeof(W));
       ldz = nb;
+      tm.begin(s, TT_PH_SMALL);
       TT_CK(ttk::small_factor(gb.as<double>(), prm, small64, zb.p, W64, (int)ldz, ws.p,
                               dinfo.as<ttk::StepInfo>(), st), "small factor");
+      tm.end();
       TT_CK(cudaMemcpyAsync(hinfo, dinfo.p, sizeof(ttk::StepInfo), cudaMemcpyDeviceToHost, st), "info");
       TT_CK(cudaStreamSynchronize(st), "step sync");
+      tm.collect();
       if (hinfo->status & 1) return fail(TT_ENONFINITE, "input holds NaN or Inf");
       if (hinfo->status & 2) return fail(TT_ENOCONV, "Jacobi eigen-solver did not converge");
       r = hinfo->r;
@@ -306,6 +360,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         const bool identity = l >= no;
         small64 = choose_small64(l);
         TT_ALLOC(omega, (size_t)no * l * sizeof(W));
+        tm.begin(s, TT_PH_SKETCH);
         TT_CK(ttk::fill_sketch(omega.p, W64, no, l, o.seed, (uint32_t)k, identity, st), "sketch matrix");
         TT_ALLOC(yb, (size_t)nb * l * sizeof(W));
         size_t wsz = 0;
@@ -322,6 +377,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         else
           TT_CK(ttk::gemm<W>({C, n, true}, {omega.as<W>(), l, true}, m, l, n, yb.as<W>(), l,
                              nullptr, false, nullptr, ws.p, st), "sketch C Omega");
+        tm.end();
         omega.reset();
         // W = shifted Cholesky-QR3(Y): a shifted pass that cannot break
         // down, then two plain passes; span(W[:, :j]) = span(Y[:, :j]).
@@ -343,6 +399,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         const double u_c = orth64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
         const W* src_pass = yb.as<W>();
         W* dst_pass[3] = {w1b.as<W>(), wb.as<W>(), w1b.as<W>()};
+        tm.begin(s, TT_PH_ORTH);
         for (int pass = 0; pass < 3; ++pass) {
           po.shift_rel = pass == 0 ? 64.0 * (double)l * u_c : 0.0;
           po.piv_tol = pass == 0 ? 0.0 : 64.0 * (double)l * u_c * u_c;
@@ -355,8 +412,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
                              l, nullptr, false, nullptr, ws.p, st), "apply R^-1");
           src_pass = dst_pass[pass];
         }
+        tm.end();
         const W* Wm = w1b.as<W>();
         TT_ALLOC(bb, (size_t)no * l * sizeof(W));
+        tm.begin(s, TT_PH_PROJECT);
         if (cfg.urv)
           TT_CK(ttk::gemm<W>({C, n, true}, {Wm, l, true}, m, l, n, bb.as<W>(), l, nullptr, false,
                              nullptr, ws.p, st), "project C W");
@@ -375,16 +434,20 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
                              true, nullptr, ws.p, st, true), "Gram W^T W");
         }
         prm.Gw = whiten ? gwb.as<double>() : nullptr;
+        tm.end();
         prm.n = (int)l;
         prm.r_cap = (int)std::min<int64_t>(rcap, l);
         prm.x2_dev = x2_dev;
         prm.piv_tol = small64 ? 1e-15 : 1e-6;
         TT_ALLOC(zb, (size_t)l * l * sizeof(W));
         ldz = l;
+        tm.begin(s, TT_PH_SMALL);
         TT_CK(ttk::small_factor(gy.as<double>(), prm, small64, zb.p, W64, (int)ldz, ws2.p,
                                 dinfo.as<ttk::StepInfo>(), st), "small factor");
+        tm.end();
         TT_CK(cudaMemcpyAsync(hinfo, dinfo.p, sizeof(ttk::StepInfo), cudaMemcpyDeviceToHost, st), "info");
         TT_CK(cudaStreamSynchronize(st), "step sync");
+        tm.collect();
         if (hinfo->status & 1) return fail(TT_ENONFINITE, "input holds NaN or Inf");
         if (hinfo->status & 2) return fail(TT_ENOCONV, "Jacobi eigen-solver did not converge");
         r = hinfo->r;
@@ -432,29 +495,39 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       TT_ALLOC(ws, wsz);
     }
     if (exact) {
-      if (cfg.urv) {
+      tm.begin(s, TT_PH_CARRY);
+      if (cfg.urv)
         TT_CK(ttk::gemm<W>({C, n, true}, {Zp, ldz, true}, m, r, n, carry.as<W>(), r, nullptr, false,
                            d_carry2 + s, ws.p, st), "carry C Z1");
-        TT_CK(ttk::copy2d(Zp, ldz, true, core.p, n, r, n, W64, st), "core Z1^T");
-      } else {
+      else
         TT_CK(ttk::gemm<W>({Zp, ldz, false}, {C, n, true}, r, n, m, carry.as<W>(), n, nullptr, false,
                            d_carry2 + s, ws.p, st), "carry Z1^T C");
+      tm.end();
+      tm.begin(s, TT_PH_CORE);
+      if (cfg.urv)
+        TT_CK(ttk::copy2d(Zp, ldz, true, core.p, n, r, n, W64, st), "core Z1^T");
+      else
         TT_CK(ttk::copy2d(Zp, ldz, false, core.p, r, m, r, W64, st), "core Z1");
-      }
+      tm.end();
     } else {
       const W* Bm = bb.as<W>();
       const W* Wm = w1b.as<W>();
-      if (cfg.urv) {
+      tm.begin(s, TT_PH_CARRY);
+      if (cfg.urv)
         TT_CK(ttk::gemm<W>({Bm, l, true}, {Zp, ldz, true}, m, r, l, carry.as<W>(), r, nullptr, false,
                            d_carry2 + s, ws.p, st), "carry B Z1");
-        TT_CK(ttk::gemm<W>({Zp, ldz, false}, {Wm, l, false}, r, n, l, core.as<W>(), n, nullptr, false,
-                           nullptr, ws.p, st), "core (W Z1)^T");
-      } else {
+      else
         TT_CK(ttk::gemm<W>({Zp, ldz, false}, {Bm, l, false}, r, n, l, carry.as<W>(), n, nullptr, false,
                            d_carry2 + s, ws.p, st), "carry (B Z1)^T");
+      tm.end();
+      tm.begin(s, TT_PH_CORE);
+      if (cfg.urv)
+        TT_CK(ttk::gemm<W>({Zp, ldz, false}, {Wm, l, false}, r, n, l, core.as<W>(), n, nullptr, false,
+                           nullptr, ws.p, st), "core (W Z1)^T");
+      else
         TT_CK(ttk::gemm<W>({Wm, l, true}, {Zp, ldz, true}, m, r, l, core.as<W>(), r, nullptr, false,
                            nullptr, ws.p, st), "core W Z1");
-      }
+      tm.end();
     }
     cores[k - 1] = core.release();
     if (cfg.urv)
@@ -477,6 +550,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   double h_carry2[TT_MAXD];
   TT_CK(cudaMemcpyAsync(h_carry2, d_carry2, sizeof(double) * (d - 1), cudaMemcpyDeviceToHost, st), "tails");
   TT_CK(cudaStreamSynchronize(st), "final sync");
+  tm.collect();
   for (int s = 0; s < d - 1; ++s) {
     const int k = cfg.urv ? d - s : s + 1;
     const int u = cfg.urv ? k - 1 : k;
@@ -552,6 +626,7 @@ void tt_opts_default(tt_opts* o) {
   o->l_full = 256;
   o->seed = 0;
   o->weights = nullptr;
+  o->phase_ms = nullptr;
 }
 
 tt_status tt_utv(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
@@ -686,6 +761,8 @@ tt_status tt_sketch_matrix(int64_t rows, int64_t cols, uint64_t seed, int32_t st
   if (e != cudaSuccess) return cuda_fail(e, "tt_sketch_matrix");
   return TT_OK;
 }
+
+uint64_t tt_kernel_launches(void) { return ttk::launches(); }
 
 const char* tt_last_error(void) { return g_err.c_str(); }
 

@@ -283,6 +283,7 @@ cudaError_t gemm(Mat<T> A, Mat<T> B, int64_t M, int64_t N, int64_t K, T* out, in
     return cudaSuccess;
   }
   if (p.gn > 65535) return cudaErrorInvalidConfiguration;
+  count_launch(1 + (use_part ? 1 : 0) + (sumsq ? 1 : 0));
   dim3 grid((unsigned)p.gm, (unsigned)p.gn, (unsigned)p.S);
   double* sqp = (!use_part && sumsq) ? sq_part : nullptr;
 if (A.row && B.row)

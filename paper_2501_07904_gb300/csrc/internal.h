@@ -8,6 +8,10 @@
 
 namespace ttk {
 
+// Process-wide count of kernels launched by this library.
+void count_launch(int n = 1);
+uint64_t launches();
+
 // Matrix operand: element (i, j) is p[i*ld + j] (row) or p[i + j*ld] (!row).
 template <typename T>
 struct Mat {

@@ -1,8 +1,15 @@
 // Elementwise kernels of the sweep (sketch matrix, casts, core copies,
 // sums of squares) and the masked TT evaluation with its gradient.
+#include <atomic>
+
 #include "internal.h"
 
 namespace ttk {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+
 namespace {
 
 constexpr int kGrid = 152 * 8;
@@ -177,6 +184,7 @@ bool fill_eval_args(EvalArgs& a, int d, const int64_t* dims, const int64_t* rank
 
 cudaError_t fill_sketch(void* out, bool fp64, int64_t rows, int64_t cols, uint64_t seed,
                         uint32_t step, bool identity, cudaStream_t st) {
+  count_launch(1);
   const int g = grid_for(rows * cols, 256);
   if (fp64)
     fill_sketch_kernel<double><<<g, 256, 0, st>>>((double*)out, rows, cols, seed, step, identity);
@@ -188,6 +196,7 @@ cudaError_t fill_sketch(void* out, bool fp64, int64_t rows, int64_t cols, uint64
 cudaError_t cast_copy(const void* in, bool in64, void* out, bool out64, int64_t n,
                       cudaStream_t st) {
   const int g = grid_for(n, 256);
+  if (in64 != out64) count_launch();
   if (in64 && !out64)
     cast_kernel<double, float><<<g, 256, 0, st>>>((const double*)in, (float*)out, n);
   else if (!in64 && out64)
@@ -201,6 +210,7 @@ cudaError_t copy2d(const void* in, int64_t ldi, bool trans, void* out, int64_t l
                    int64_t cols, bool fp64, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return cudaSuccess;
   const int g = grid_for(rows * cols, 256);
+  count_launch();
   if (fp64)
     copy2d_kernel<double><<<g, 256, 0, st>>>((const double*)in, ldi, trans, (double*)out, ldo,
                                              rows, cols);
@@ -213,6 +223,7 @@ cudaError_t copy2d(const void* in, int64_t ldi, bool trans, void* out, int64_t l
 size_t sumsq_ws_bytes(int64_t) { return (size_t)kGrid * sizeof(double) + 256; }
 
 cudaError_t sumsq(const void* x, bool fp64, int64_t n, double* out, void* ws, cudaStream_t st) {
+  count_launch(2);
   const int g = grid_for(n, 256);
   double* part = (double*)ws;
   if (fp64)
@@ -228,6 +239,7 @@ cudaError_t eval_at(int d, const int64_t* dims, const int64_t* ranks, const floa
   EvalArgs a;
   if (!fill_eval_args(a, d, dims, ranks, cores, nullptr)) return cudaErrorInvalidValue;
   if (n <= 0) return cudaSuccess;
+  count_launch();
   eval_kernel<<<grid_for(n, 128), 128, 0, st>>>(a, idx, n, out);
   return cudaGetLastError();
 }
@@ -238,6 +250,7 @@ cudaError_t eval_at_backward(int d, const int64_t* dims, const int64_t* ranks,
   EvalArgs a;
   if (!fill_eval_args(a, d, dims, ranks, cores, grads)) return cudaErrorInvalidValue;
   if (n <= 0) return cudaSuccess;
+  count_launch();
   eval_backward_kernel<<<grid_for(n, 128), 128, 0, st>>>(a, idx, n, gout);
   return cudaGetLastError();
 }

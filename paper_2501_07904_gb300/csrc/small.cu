@@ -538,6 +538,7 @@ cudaError_t launch_small(const double* G, SmallParams prm, void* Z, int ldz, voi
   T* work = (T*)ws;
   size_t off = ((size_t)(4 * n * n + 2 * n) * sizeof(T) + 255) & ~(size_t)255;
   int* iwork = (int*)((char*)ws + off);
+  count_launch();
   small_kernel<T, ZT><<<1, NT, 0, st>>>(G, prm, work, iwork, (ZT*)Z, ldz, info);
   return cudaGetLastError();
 }
