@@ -85,6 +85,9 @@ typedef struct {
   int32_t l_full;           /* basis side <= l_full columns -> exact Gram path, default 256 (max 256) */
   uint64_t seed;            /* Philox key of the Rademacher sketch, default 0 */
   const double* weights;    /* host, d-1 error weights w_k with sum w_k^2 = 1; NULL = equal 1/sqrt(d-1) */
+  int32_t orth_precision;   /* tt_small_precision of the Cholesky-QR passes of a sketched step;
+                               default TT_SMALL_AUTO = FP64 for FP64 data or a tight step, else FP32 */
+  int32_t pad_;
   double* phase_ms;         /* host, TT_MAXD * TT_NPHASES doubles [sweep step][tt_phase], or NULL.
                                Milliseconds of device time are ADDED to it; the sweep step index is
                                0 for the first factored unfolding. */

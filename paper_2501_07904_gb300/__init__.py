@@ -50,6 +50,7 @@ class tt_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("small_precision", ctypes.c_int32),
                 ("oversample", ctypes.c_int32), ("l_full", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("weights", ctypes.POINTER(ctypes.c_double)),
+                ("orth_precision", ctypes.c_int32), ("pad_", ctypes.c_int32),
                 ("phase_ms", ctypes.POINTER(ctypes.c_double))]
 
 
@@ -168,7 +169,7 @@ class TTResult:
 
 
 def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream,
-           timing=False):
+           timing=False, orth="auto"):
     if not isinstance(A, torch.Tensor):
         raise TypeError("A must be a torch.Tensor")
     if A.dtype not in (torch.float32, torch.float64):
@@ -181,6 +182,7 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
     lib().tt_opts_default(ctypes.byref(opts))
     opts.precision = PRECISION[precision]
     opts.small_precision = SMALL[small]
+    opts.orth_precision = SMALL[orth]
     opts.oversample = int(oversample)
     opts.l_full = int(l_full)
     opts.seed = int(seed)
@@ -223,7 +225,7 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
 
 
 def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, oversample=16,
-           l_full=256, small="auto", weights=None, stream=None, timing=False):
+           l_full=256, small="auto", weights=None, stream=None, timing=False, orth="auto"):
     """TT-URV right-to-left (Alg. 3) or TT-ULV left-to-right (Alg. 1/2).
 
     Give ``eps`` (prescribed relative accuracy, Alg. 2) or ``ranks``
@@ -233,7 +235,7 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
         raise ValueError("give exactly one of eps or ranks")
     v = {"URV": (TT_URV, TT_RL), "ULV": (TT_ULV, TT_LR)}[variant]
     return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
-                  weights, stream, timing)
+                  weights, stream, timing, orth)
 
 
 def tt_svd(A, eps=None, ranks=None, direction="LR", precision="fp32", l_full=256, small="auto",

@@ -395,13 +395,17 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         // FP32 floor; W_1 is then too ill-conditioned for an FP32-summed
         // Gram to stay positive definite, so those Grams use exact products
         // and FP64 sums and the Cholesky runs in FP64.
-        const bool orth64 = small64 || W64;
+        const bool orth64 = o.orth_precision == TT_SMALL_FP64 ||
+                            (o.orth_precision == TT_SMALL_AUTO && (small64 || W64));
         const double u_c = orth64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
         const W* src_pass = yb.as<W>();
         W* dst_pass[3] = {w1b.as<W>(), wb.as<W>(), w1b.as<W>()};
         tm.begin(s, TT_PH_ORTH);
         for (int pass = 0; pass < 3; ++pass) {
-          po.shift_rel = pass == 0 ? 64.0 * (double)l * u_c : 0.0;
+          // the smallest shift that keeps the first Cholesky positive definite
+          // (a few l u of the Gram's scale): a larger one squashes the sketch's
+          // weak directions, and the later passes then amplify rounding in them
+          po.shift_rel = pass == 0 ? 4.0 * (double)l * u_c : 0.0;
           po.piv_tol = pass == 0 ? 0.0 : 64.0 * (double)l * u_c * u_c;
           TT_CK(ttk::gemm<W>({src_pass, l, false}, {src_pass, l, true}, l, l, nb, nullptr, 0,
                              gy.as<double>(), true, nullptr, ws.p, st, !W64 && small64),
@@ -585,6 +589,8 @@ tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims,
   if (o.precision < TT_P_FP64 || o.precision > TT_P_MIXED) return fail(TT_EINVAL, "bad precision");
   if (o.small_precision < TT_SMALL_AUTO || o.small_precision > TT_SMALL_FP64)
     return fail(TT_EINVAL, "bad small_precision");
+  if (o.orth_precision < TT_SMALL_AUTO || o.orth_precision > TT_SMALL_FP64)
+    return fail(TT_EINVAL, "bad orth_precision");
   if (o.weights) {
     double s = 0.0;
     for (int k = 0; k < d - 1; ++k) {
@@ -626,6 +632,7 @@ void tt_opts_default(tt_opts* o) {
   o->l_full = 256;
   o->seed = 0;
   o->weights = nullptr;
+  o->orth_precision = TT_SMALL_AUTO;
   o->phase_ms = nullptr;
 }
 

@@ -475,8 +475,18 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
     const T alpha = sqrt(cq > T(0) ? cq : T(0));
     const T x0 = Mq[j * n + j];
     const T sg = x0 >= T(0) ? T(1) : T(-1);
-    const T vtv = T(2) * (alpha * alpha + sg * alpha * x0);
-    const T tj_ = vtv > T(0) ? T(2) / vtv : T(0);
+    // tau = 2 / ||v||^2 from the stored v itself (FP64 sum): the reflector is
+    // then orthogonal to working precision even when the column norm used for
+    // alpha carries FP32 summation error.
+    double rest = 0.0;
+    for (int i = j + 1 + tid; i < n; i += nt) {
+      const double x = (double)Mq[i * n + j];
+      rest += x * x;
+    }
+    rest = block_sum(rest, redd);
+    const double v0 = (double)(x0 + sg * alpha);
+    const double vtv = v0 * v0 + rest;
+    const T tj_ = vtv > 0.0 ? (T)(2.0 / vtv) : T(0);
     __syncthreads();
     if (tid == 0) {
       Mq[j * n + j] = x0 + sg * alpha;

@@ -39,7 +39,8 @@ def test_version_and_defaults(L):
     assert b"sm_103a" in L.tt_version()
     o = tu.tt_opts()
     L.tt_opts_default(ctypes.byref(o))
-    assert (o.precision, o.small_precision, o.oversample, o.l_full, o.seed) == (1, 0, 16, 256, 0)
+    assert (o.precision, o.small_precision, o.oversample, o.l_full, o.seed, o.orth_precision) == \
+        (1, 0, 16, 256, 0, 0)
 
 
 def _call(L, A=1, dtype=0, d=3, dims=(4, 5, 6), eps=0.1, fixed=None, variant=0, direction=0, opts=None):
