@@ -167,6 +167,24 @@ size_t tt_full_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks, 
 tt_status tt_full(int32_t d, const int64_t* dims, const int64_t* ranks, const void* const* cores,
                   int32_t dtype, void* out, void* work, void* stream);
 
+/* tt_full without any device allocation, for callers that cannot allocate
+ * device memory during the call: code running with every byte of device
+ * memory already owned by another allocator's pool, or a latency-critical
+ * loop that must not hit cudaMalloc's implicit device synchronization.  (The
+ * paper has no counterpart; this is a service of the library.)
+ * Same arguments and result as tt_full, without `work`: the scratch is a
+ * fixed array of tt_full_noalloc_max_work_bytes() = 32 MiB of static device
+ * memory, which every GPU that loads this library holds until the process
+ * exits.  A contraction needing more (tt_full_work_bytes) returns TT_EINVAL.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture on the device.  All calls share the one array and nothing in it
+ * needs to start at zero, but two calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it: serialize them. */
+size_t tt_full_noalloc_max_work_bytes(void);
+tt_status tt_full_noalloc(int32_t d, const int64_t* dims, const int64_t* ranks,
+                          const void* const* cores, int32_t dtype, void* out, void* stream);
+
 /* Masked TT evaluation x_e = G_1[i_1] G_2[:, i_2, :] ... G_d[:, i_d] at n
  * row-major linear indices idx[e] (device int64, 0 <= idx < prod(dims)).
  * FP32 only.  out: device float[n]. */

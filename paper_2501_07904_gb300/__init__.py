@@ -34,8 +34,9 @@ TT_RL, TT_LR = 0, 1
 
 # Every symbol include/ttutv.h declares.
 EXPORTS = ["tt_opts_default", "tt_utv", "tt_svd", "tt_result_free", "tt_full_work_bytes",
-           "tt_full", "tt_eval_at", "tt_eval_at_backward", "tt_sketch_matrix", "tt_kernel_launches",
-           "tt_last_error", "tt_version"]
+           "tt_full", "tt_full_noalloc", "tt_full_noalloc_max_work_bytes", "tt_eval_at",
+           "tt_eval_at_backward", "tt_sketch_matrix", "tt_kernel_launches", "tt_last_error",
+           "tt_version"]
 PHASES = ["gram", "small", "carry", "core", "sketch", "orth", "project"]
 TT_NPHASES = 8
 
@@ -94,6 +95,10 @@ def lib():
     L.tt_full_work_bytes.restype = SZ
     L.tt_full.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), I32, P, P, P]
     L.tt_full.restype = I32
+    L.tt_full_noalloc.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), I32, P, P]
+    L.tt_full_noalloc.restype = I32
+    L.tt_full_noalloc_max_work_bytes.argtypes = []
+    L.tt_full_noalloc_max_work_bytes.restype = SZ
     L.tt_eval_at.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P, P]
     L.tt_eval_at.restype = I32
     L.tt_eval_at_backward.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P,

@@ -621,6 +621,10 @@ tt_status sweep_entry(const void* A, int32_t dtype, int32_t d, const int64_t* di
 
 }  // namespace
 
+namespace ttk {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace ttk
+
 extern "C" {
 
 void tt_opts_default(tt_opts* o) {

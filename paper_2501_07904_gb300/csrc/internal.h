@@ -8,6 +8,9 @@
 
 namespace ttk {
 
+// Set the thread-local message returned by tt_last_error().
+void set_last_error(const char* msg);
+
 // Process-wide count of kernels launched by this library.
 void count_launch(int n = 1);
 uint64_t launches();
