@@ -61,6 +61,11 @@ struct SmallParams {
   const double* Gw;       // QLP/Jacobi on a sketch: W^T W of the range basis, or null
 };
 size_t small_ws_bytes(int n, bool fp64);
+// Register-resident fast path (small_fast.cu) for SM_QLP / SM_ORTH with
+// n <= 128 (FP32) or n <= 64 (FP64); small_factor() dispatches to it.
+bool small_fast_eligible(const SmallParams& prm, bool fp64);
+cudaError_t small_factor_fast(const double* G, SmallParams prm, bool fp64_math, void* Z,
+                              bool z_fp64, int ldz, void* ws, StepInfo* info, cudaStream_t st);
 // Z (n x ldz, written as T_out = float/double per zfp64) receives the basis Z_1
 // (QLP/Jacobi) or the orthonormalizing factor S (ORTH).
 cudaError_t small_factor(const double* G, SmallParams prm, bool fp64_math, void* Z, bool z_fp64,

@@ -557,13 +557,16 @@ cudaError_t launch_small(const double* G, SmallParams prm, void* Z, int ldz, voi
 
 size_t small_ws_bytes(int n, bool fp64) {
   const size_t el = fp64 ? 8 : 4;
-  size_t off = ((size_t)(4 * n * n + 2 * n) * el + 255) & ~(size_t)255;
-  return off + (size_t)2 * n * sizeof(int) + 256;
+  const size_t nn = ((size_t)n + 31) / 32 * 32;
+  size_t off = ((4 * nn * (nn + 1) + 2 * nn) * el + 255) & ~(size_t)255;
+  return off + (size_t)2 * nn * sizeof(int) + 256;
 }
 
 cudaError_t small_factor(const double* G, SmallParams prm, bool fp64_math, void* Z, bool z_fp64,
                          int ldz, void* ws, StepInfo* info, cudaStream_t st) {
   if (prm.n < 1 || prm.n > kMaxSmall) return cudaErrorInvalidValue;
+  if (small_fast_eligible(prm, fp64_math))
+    return small_factor_fast(G, prm, fp64_math, Z, z_fp64, ldz, ws, info, st);
   if (fp64_math)
     return z_fp64 ? launch_small<double, double>(G, prm, Z, ldz, ws, info, st)
                   : launch_small<double, float>(G, prm, Z, ldz, ws, info, st);
