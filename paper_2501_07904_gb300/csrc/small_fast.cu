@@ -3,12 +3,13 @@
 // Cholesky-QR (SM_ORTH), for n <= 128 in FP32 and n <= 64 in FP64.
 //
 // The symmetric n x n matrix is held in registers, a 4 x 8 tile per thread
-// (512 threads cover 128 x 128).  One Cholesky step is: one warp picks the
-// pivot p (largest remaining diagonal, lowest index on ties), the owners of
-// row p publish it to shared memory, every thread applies the rank-one update
-// to its own entries -- two barriers per step.  Pivoting is virtual (nothing
-// is swapped): the factor's rows come out in pivot order and its columns keep
-// the original coordinates.
+// (512 threads cover 128 x 128).  One Cholesky step is: every warp picks the
+// same pivot p (largest remaining diagonal, lowest index on ties), the owners
+// of row p publish it to shared memory, every thread applies the rank-one
+// update to its own entries -- one barrier per step, the diagonal, pivot row
+// and eliminated flags being double-buffered by step parity.  Pivoting is
+// virtual (nothing is swapped): the factor's rows come out in pivot order and
+// its columns keep the original coordinates.
 //
 // Pivoted QLP (Stewart's rank-revealing UTV, cited in Sec. 2.2):
 //   1. pivoted Cholesky of G = X^T X gives R_1 (the R of column-pivoted QR of X);
@@ -31,9 +32,15 @@ constexpr int FT = 512;  // threads
 constexpr int NP = 128;  // the register tiles cover NP x NP
 
 struct Scal {
-  int p, stop, drop;
+  int p, stop;
   double dp, trace;
 };
+
+// Register tile of a thread: rows r = ty + 32 i (i < 4), columns c = tx + 16 jj
+// (jj < 8) with ty = tid / 16, tx = tid % 16.  The strided columns make the
+// column-side shared-memory reads of a warp hit 16 distinct banks.
+__device__ __forceinline__ int tile_r(int i) { return (int)(threadIdx.x / 16) + 32 * i; }
+__device__ __forceinline__ int tile_c(int jj) { return (int)(threadIdx.x % 16) + 16 * jj; }
 
 template <typename T>
 __device__ __forceinline__ T sel4(const T (&a)[4][8], int i, int jj) {
@@ -42,136 +49,192 @@ __device__ __forceinline__ T sel4(const T (&a)[4][8], int i, int jj) {
 
 template <typename T>
 __device__ void load_regs(T (&a)[4][8], const double* G, int n) {
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) {
-      const int r = 4 * ty + i, c = 8 * tx + jj;
+      const int r = tile_r(i), c = tile_c(jj);
       a[i][jj] = (r < n && c < n) ? (T)G[r * n + c] : T(0);
     }
 }
 
-// Cholesky of the symmetric matrix in registers (see file comment).
-//   pivot      largest remaining diagonal first; else column order, a column
-//              whose remaining diagonal is not above tol * (largest initial
-//              diagonal) being dropped (zero row of R);
+// a[r][c] = sum_{q < qn} A(r, q) B(c, q) over the thread's tile (r < mr, c < mc).
+template <typename T, typename FA, typename FB>
+__device__ __forceinline__ void tile_product(T (&a)[4][8], int mr, int mc, int qn, FA fa, FB fb) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) a[i][jj] = T(0);
+  for (int q = 0; q < qn; ++q) {
+    T ra[4], cb[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ra[i] = tile_r(i) < mr ? fa(tile_r(i), q) : T(0);
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) cb[jj] = tile_c(jj) < mc ? fb(tile_c(jj), q) : T(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) a[i][jj] = fma(ra[i], cb[jj], a[i][jj]);
+  }
+}
+
+// Warp argmax of non-negative candidates, lowest index on ties; 'has' marks
+// a lane's candidate.  Returns (index or -1, value).
+__device__ __forceinline__ int warp_argmax(bool has, float v, int idx, float& best) {
+  const unsigned key = has ? __float_as_uint(v > 0.f ? v : 0.f) : 0u;
+  const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+  const bool any = __any_sync(0xffffffffu, has);
+  const unsigned cand = (has && key == mx) ? (unsigned)idx : 0xffffffffu;
+  const unsigned pi = __reduce_min_sync(0xffffffffu, cand);
+  best = __uint_as_float(mx);
+  return any ? (int)pi : -1;
+}
+__device__ __forceinline__ int warp_argmax(bool has, double v, int idx, double& best) {
+  double b = has ? v : -1.0;
+  int bi = has ? idx : 0x7fffffff;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, b, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > b || (ob == b && oi < bi)) {
+      b = ob;
+      bi = oi;
+    }
+  }
+  best = b;
+  return bi == 0x7fffffff ? -1 : bi;
+}
+
+// Cholesky of the symmetric matrix in registers, one barrier per step.
+//   pivot      largest remaining diagonal first (every warp computes the same
+//              choice); else column order, a column whose remaining diagonal
+//              is not above tol * (largest initial diagonal) being dropped
+//              (zero row of R, no elimination);
 //   stop_mode  0: tolerance (pivoted) or all columns (column order);
 //              1: first j >= 1 with base + trace <= delta2;
 //              2: j == r_stop;
 //   kmax       at most this many steps.
-// Rows of R (ld ldr) in step order, perm[j] = column eliminated at step j;
-// tails[j] = base + remaining trace before step j (if tails != null).
-// Returns the number of steps; sc.trace = remaining Schur trace (>= 0, FP64).
+// Rows of R (ld ldr) in step order with original-coordinate columns;
+// perm[j] = column eliminated at step j; tails[j] = base + remaining trace
+// before step j (if tails != null).  Returns the number of steps; sc.trace =
+// the remaining Schur trace (>= 0).
+// Shared buffers (double-buffered by step parity): dbuf[2][NP] remaining
+// diagonal, Lbuf[2][NP] pivot row, dn[2][NP] eliminated flags.
 template <typename T>
 __device__ int pchol(T (&a)[4][8], int n, bool pivot, double tol, int stop_mode, double base,
-                     double delta2, int r_stop, int kmax, T* R, int ldr, int* perm, T* d, T* Lraw,
-                     int* done, double* tails, Scal& sc) {
+                     double delta2, int r_stop, int kmax, T* R, int ldr, int* perm, T* dbuf, T* Lbuf,
+                     int* dn, double* tails, Scal& sc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ty = tid / 16, tx = tid % 16;
-  for (int i = tid; i < NP; i += FT) done[i] = (i >= n) ? 1 : 0;
+  const int ty = tid / 16;
+  for (int i = tid; i < NP; i += FT) {
+    dn[i] = (i >= n) ? 1 : 0;
+    dn[NP + i] = dn[i];
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj)
-      if (4 * ty + i == 8 * tx + jj) d[4 * ty + i] = a[i][jj];
+      if (tile_r(i) == tile_c(jj)) {
+        dbuf[tile_r(i)] = a[i][jj];   // D_0 lives in buffer 1 ("step -1")
+        dbuf[NP + tile_r(i)] = a[i][jj];
+      }
+  for (int i = tid; i < NP; i += FT) Lbuf[NP + i] = T(0);  // L_{-1} = 0
   __syncthreads();
   double d0 = 0.0;
-  if (warp == 0) {
+  {
     double m = 0.0;
-    for (int i = lane; i < n; i += 32) m = fmax(m, (double)d[i]);
+    for (int i = lane; i < n; i += 32) m = fmax(m, (double)dbuf[i]);
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     d0 = m;
   }
+  T inv_prev = T(0);
   int j = 0;
   for (;; ++j) {
+    const int cur = j & 1, prv = cur ^ 1;
+    // D_j = D_{j-1} - L_{j-1}^2 / dp_{j-1}, computed by every warp; warp 0 stores it
+    T best_v = T(-1);
+    int best_i = -1;
+    T tr = T(0);
+#pragma unroll
+    for (int k = 0; k < NP / 32; ++k) {
+      const int i = lane + 32 * k;
+      const T l = Lbuf[prv * NP + i];
+      const T dj = dbuf[prv * NP + i] - l * l * inv_prev;
+      if (warp == 0) dbuf[cur * NP + i] = dj;
+      if (!dn[prv * NP + i]) {
+        tr += dj;
+        if (best_i < 0 || dj > best_v) {
+          best_v = dj;
+          best_i = i;
+        }
+      }
+    }
+    int p;
+    double dp;
+    if (pivot) {
+      T bv;
+      p = warp_argmax(best_i >= 0, best_v, best_i, bv);
+      dp = (double)bv;
+    } else {
+      // column order: D_j[j], recomputed exactly as its owning lane did above
+      p = j;
+      dp = 0.0;
+      if (j < n) {
+        const T l = Lbuf[prv * NP + j];
+        dp = (double)(dbuf[prv * NP + j] - l * l * inv_prev);
+      }
+    }
+    double trd = 0.0;
+    if (stop_mode == 1 || tails) {
+      T t = tr;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      trd = fmax((double)t, 0.0);
+    }
+    int stop = 0;
+    bool drop = false;
+    if (j >= kmax || p < 0) stop = 1;
+    if (!stop && stop_mode == 1 && j >= 1 && base + trd <= delta2) stop = 1;
+    if (!stop && stop_mode == 2 && j == r_stop) stop = 1;
+    if (!stop) {
+      const bool ok = (dp > 0.0) && (dp > tol * d0);
+      if (pivot && !ok) stop = 1;
+      if (!pivot && !ok) drop = true;
+    }
+    if (tid == 0) {
+      if (tails) tails[j] = base + trd;
+      sc.trace = trd;
+    }
+    if (stop) break;
+    // eliminated flags after this step
     if (warp == 0) {
-      double tr = 0.0;
-      T best = lowest_value<T>();
-      int bi = 0x7fffffff;
-      for (int i = lane; i < NP; i += 32) {
-        if (done[i]) continue;
-        tr += (double)d[i];
-        if (d[i] > best || (d[i] == best && i < bi)) {
-          best = d[i];
-          bi = i;
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        tr += __shfl_xor_sync(0xffffffffu, tr, o);
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (lane == 0) {
-        tr = fmax(tr, 0.0);
-        if (tails) tails[j] = base + tr;
-        int stop = 0, drop = 0, p = bi;
-        double dp = (double)best;
-        if (!pivot) {
-          p = j;
-          dp = (j < n) ? (double)d[j] : 0.0;
-        }
-        if (j >= kmax) stop = 1;
-        if (!stop && stop_mode == 1 && j >= 1 && base + tr <= delta2) stop = 1;
-        if (!stop && stop_mode == 2 && j == r_stop) stop = 1;
-        if (!stop) {
-          const bool ok = (dp > 0.0) && (dp > tol * d0);
-          if (pivot && !ok) stop = 1;
-          if (!pivot && !ok) drop = 1;
-        }
-        sc.p = p;
-        sc.dp = dp;
-        sc.stop = stop;
-        sc.drop = drop;
-        sc.trace = tr;
+#pragma unroll
+      for (int k = 0; k < NP / 32; ++k) {
+        const int i = lane + 32 * k;
+        dn[cur * NP + i] = dn[prv * NP + i] | (i == p ? 1 : 0);
       }
     }
-    __syncthreads();
-    if (sc.stop) break;
-    const int p = sc.p;
-    if (sc.drop) {
-      for (int c = tid; c < ldr; c += FT) R[j * ldr + c] = T(0);
-      if (tid == 0) {
-        done[p] = 1;
-        perm[j] = p;
-      }
-      continue;
-    }
-    if (ty == p / 4) {
-      const int pi = p % 4;
+    // pivot row: owners publish row p (zero for a dropped column)
+    if (ty == (p & 31)) {
+      const int pi = p >> 5;
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj) {
-        const int c = 8 * tx + jj;
-        Lraw[c] = done[c] ? T(0) : sel4(a, pi, jj);
+        const int c = tile_c(jj);
+        Lbuf[cur * NP + c] = (drop || dn[prv * NP + c]) ? T(0) : sel4(a, pi, jj);
       }
     }
     __syncthreads();
-    const T dp = (T)sc.dp;
-    const T inv = T(1) / dp;
+    const T inv = drop ? T(0) : T(1) / (T)dp;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const T lr = Lraw[4 * ty + i] * inv;
+      const T lr = Lbuf[cur * NP + tile_r(i)] * inv;
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) a[i][jj] -= lr * Lraw[8 * tx + jj];
+      for (int jj = 0; jj < 8; ++jj) a[i][jj] -= lr * Lbuf[cur * NP + tile_c(jj)];
     }
-    if (warp == 0) {
-      const T s = sqrt(dp);
-      for (int c = lane; c < ldr; c += 32) {
-        const T l = (c < NP) ? Lraw[c] : T(0);
-        R[j * ldr + c] = l / s;
-        if (c < NP && !done[c]) d[c] -= l * l * inv;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        done[p] = 1;
-        perm[j] = p;
-        d[p] = T(0);
-      }
+    if (warp == 1) {
+      const T rs = drop ? T(0) : T(1) / sqrt((T)dp);
+      for (int c = lane; c < ldr; c += 32) R[j * ldr + c] = (c < NP) ? Lbuf[cur * NP + c] * rs : T(0);
+      if (lane == 0) perm[j] = p;
     }
+    inv_prev = inv;
   }
   __syncthreads();
   return j;
@@ -244,16 +307,15 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
                                                            T* __restrict__ gws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = prm.n, tid = threadIdx.x;
-  const int ty = tid / 16, tx = tid % 16;
   const int nn = ((n + 31) / 32) * 32, ld = nn + 1;
   T* R1 = (T*)smem_raw;            // nn x ld
   T* R2 = R1 + nn * ld;            // nn x ld
   T* X = R2 + nn * ld;             // nn x ld
   T* tmp = X + nn * ld;            // (nn/32) * 1024
-  T* d = tmp + (nn / 32) * 1024;   // NP
-  T* Lraw = d + NP;                // NP
-  int* done = (int*)(Lraw + NP);   // NP
-  int* perm1 = done + NP;          // NP
+  T* dbuf = tmp + (nn / 32) * 1024;  // 2 NP
+  T* Lbuf = dbuf + 2 * NP;         // 2 NP
+  int* dn = (int*)(Lbuf + 2 * NP); // 2 NP
+  int* perm1 = dn + 2 * NP;        // NP
   int* perm2 = perm1 + NP;         // NP
   __shared__ Scal sc;
   __shared__ double redd[32];
@@ -297,18 +359,17 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj)
-          if (4 * ty + i == 8 * tx + jj && 4 * ty + i < n) a[i][jj] += sh;
+          if (tile_r(i) == tile_c(jj) && tile_r(i) < n) a[i][jj] += sh;
     }
-    pchol(a, n, false, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, ld, perm1, d, Lraw, done, nullptr, sc);
+    pchol(a, n, false, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, ld, perm1, dbuf, Lbuf, dn, nullptr, sc);
     tri_inverse(R1, n, ld, X, tmp);
-    int kept = 0;
-    if (tid == 0)
-      for (int i = 0; i < n; ++i) kept += (R1[i * ld + i] != T(0));
     for (int e = tid; e < n * ldz; e += FT) {
       const int i = e / ldz, c = e % ldz;
       Z[e] = (c < n) ? (ZT)X[i * ld + c] : ZT(0);
     }
     if (tid == 0) {
+      int kept = 0;
+      for (int i = 0; i < n; ++i) kept += (R1[i * ld + i] != T(0));
       info->r = kept;
       info->k1 = kept;
       info->nsteps = n;
@@ -324,7 +385,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   if (prm.Gw) {
     // W^T W = T^T T; factor A = T^{-T} G T^{-1}, the Gram of X Q for Q = W T^{-1}
     load_regs(a, prm.Gw, n);
-    pchol(a, n, false, 0.0, 0, 0.0, 0.0, 0, n, R1, ld, perm1, d, Lraw, done, nullptr, sc);
+    pchol(a, n, false, 0.0, 0, 0.0, 0.0, 0, n, R1, ld, perm1, dbuf, Lbuf, dn, nullptr, sc);
     tri_inverse(R1, n, ld, X, tmp);
     for (int e = tid; e < nn * ld; e += FT) Tw[e] = X[e];
     for (int e = tid; e < n * n; e += FT) {  // R2 = G T^{-1}
@@ -334,18 +395,15 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
       R2[i * ld + c] = (T)s;
     }
     __syncthreads();
+    // a = T^{-T} (G T^{-1}): a[r][c] = sum_k X[k][r] R2[k][c]
+    tile_product(a, n, n, n, [&](int r, int k) { return X[k * ld + r]; },
+                 [&](int c, int k) { return R2[k * ld + c]; });
     double t2 = 0.0;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int r = 4 * ty + i, c = 8 * tx + jj;
-        T s = T(0);
-        if (r < n && c < n)
-          for (int k = 0; k <= r; ++k) s += X[k * ld + r] * R2[k * ld + c];
-        a[i][jj] = s;
-        if (r == c) t2 += (double)s;
-      }
+      for (int jj = 0; jj < 8; ++jj)
+        if (tile_r(i) == tile_c(jj)) t2 += (double)a[i][jj];
     tr = block_sum(t2, redd);
   } else {
     load_regs(a, G, n);
@@ -353,24 +411,16 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   const double mu2 = prm.x2_dev ? fmax(0.0, x2 - tr) : 0.0;
 
   // phase 1: pivoted Cholesky of G
-  const int k1 = pchol(a, n, true, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, ld, perm1, d, Lraw, done,
+  const int k1 = pchol(a, n, true, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, ld, perm1, dbuf, Lbuf, dn,
                        nullptr, sc);
   const double s1 = sc.trace;
   // phase 2: pivoted Cholesky of M = R_1 R_1^T
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) {
-      const int r = 4 * ty + i, c = 8 * tx + jj;
-      T s = T(0);
-      if (r < k1 && c < k1)
-        for (int q = 0; q < n; ++q) s += R1[r * ld + q] * R1[c * ld + q];
-      a[i][jj] = s;
-    }
+  tile_product(a, k1, k1, n, [&](int r, int q) { return R1[r * ld + q]; },
+               [&](int c, int q) { return R1[c * ld + q]; });
   const bool fixed = prm.r_fixed >= 1;
   const int rt = fixed ? min(prm.r_fixed, prm.r_cap) : -1;
   const int r2 = pchol(a, k1, true, 0.0, fixed ? 2 : 1, mu2 + s1, delta2, rt, min(k1, prm.r_cap),
-                       R2, ld, perm2, d, Lraw, done, info->tails, sc);
+                       R2, ld, perm2, dbuf, Lbuf, dn, info->tails, sc);
   const int r = fixed ? rt : max(1, r2);
   const int rz = min(r, r2);  // columns produced by the factorization
 
@@ -383,57 +433,56 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   for (int e = tid; e < rz * rz; e += FT) R2[(e / rz) * ld + e % rz] = X[(e / rz) * ld + e % rz];
   __syncthreads();
   tri_inverse(R2, rz, ld, X, tmp);
-  // Zs = R_1^T(:, perm2) R2_11^{-1}  (n x rz) into R2
-  for (int e = tid; e < n * rz; e += FT) {
-    const int i = e / rz, c = e % rz;
-    T s = T(0);
-    for (int aa = 0; aa <= c; ++aa) s += R1[perm2[aa] * ld + i] * X[aa * ld + c];
-    R2[i * ld + c] = s;
-  }
+  // Zs = R_1^T(:, perm2) R2_11^{-1} (n x rz), into R2
+  tile_product(a, n, rz, rz, [&](int i, int q) { return R1[perm2[q] * ld + i]; },
+               [&](int c, int q) { return q <= c ? X[q * ld + c] : T(0); });
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj)
+      if (tile_r(i) < n && tile_c(jj) < rz) R2[tile_r(i) * ld + tile_c(jj)] = a[i][jj];
   __syncthreads();
   if (sizeof(T) == 4 && rz > 0) {
     // one more Cholesky-QR pass: Zs <- Zs chol(Zs^T Zs)^{-1}
+    tile_product(a, rz, rz, n, [&](int rr, int q) { return R2[q * ld + rr]; },
+                 [&](int c, int q) { return R2[q * ld + c]; });
+    pchol(a, rz, false, 0.0, 0, 0.0, 0.0, 0, rz, R1, ld, perm1, dbuf, Lbuf, dn, nullptr, sc);
+    tri_inverse(R1, rz, ld, X, tmp);
+    tile_product(a, n, rz, rz, [&](int i, int q) { return R2[i * ld + q]; },
+                 [&](int c, int q) { return q <= c ? X[q * ld + c] : T(0); });
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int rr = 4 * ty + i, c = 8 * tx + jj;
-        T s = T(0);
-        if (rr < rz && c < rz)
-          for (int q = 0; q < n; ++q) s += R2[q * ld + rr] * R2[q * ld + c];
-        a[i][jj] = s;
-      }
-    pchol(a, rz, false, 0.0, 0, 0.0, 0.0, 0, rz, R1, ld, perm1, d, Lraw, done, nullptr, sc);
-    tri_inverse(R1, rz, ld, X, tmp);
-    mul_upper(R2, ld, X, ld, n, rz, R1, ld);  // R1 = Zs X
-    for (int e = tid; e < n * rz; e += FT) R2[(e / rz) * ld + e % rz] = R1[(e / rz) * ld + e % rz];
+      for (int jj = 0; jj < 8; ++jj)
+        if (tile_r(i) < n && tile_c(jj) < rz) R2[tile_r(i) * ld + tile_c(jj)] = a[i][jj];
     __syncthreads();
   }
   // fixed rank above the numerical rank: complete with unit vectors
   // orthogonalized (twice) against the columns already formed
   if (r > rz && tid < 32) {
     const int lane = tid;
+    T* v = Lbuf;
     int cand = 0;
     for (int c = rz; c < r; ++c) {
       for (; cand < n; ++cand) {
-        // v = e_cand - Z Z^T e_cand, twice
-        for (int i = lane; i < n; i += 32) Lraw[i] = (i == cand) ? T(1) : T(0);
+        for (int i = lane; i < n; i += 32) v[i] = (i == cand) ? T(1) : T(0);
         __syncwarp();
         for (int pass = 0; pass < 2; ++pass) {
           for (int b = 0; b < c; ++b) {
             T dot = T(0);
-            for (int i = lane; i < n; i += 32) dot += R2[i * ld + b] * Lraw[i];
+            for (int i = lane; i < n; i += 32) dot += R2[i * ld + b] * v[i];
             for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-            for (int i = lane; i < n; i += 32) Lraw[i] -= dot * R2[i * ld + b];
+            for (int i = lane; i < n; i += 32) v[i] -= dot * R2[i * ld + b];
             __syncwarp();
           }
         }
         T nv = T(0);
-        for (int i = lane; i < n; i += 32) nv += Lraw[i] * Lraw[i];
+        for (int i = lane; i < n; i += 32) nv += v[i] * v[i];
         for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
         if (nv > T(0.25)) {
           const T s = T(1) / sqrt(nv);
-          for (int i = lane; i < n; i += 32) R2[i * ld + c] = Lraw[i] * s;
+          for (int i = lane; i < n; i += 32) R2[i * ld + c] = v[i] * s;
           __syncwarp();
           ++cand;
           break;
@@ -467,7 +516,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
 template <typename T>
 size_t fast_smem_bytes(int n) {
   const int nn = ((n + 31) / 32) * 32, ld = nn + 1;
-  return (size_t)(3 * nn * ld + (nn / 32) * 1024 + 2 * NP) * sizeof(T) + 3 * NP * sizeof(int);
+  return (size_t)(3 * nn * ld + (nn / 32) * 1024 + 4 * NP) * sizeof(T) + 4 * NP * sizeof(int);
 }
 
 template <typename T, typename ZT>
