@@ -44,7 +44,8 @@ typedef enum {
   TT_ENOMEM = 3,        /* the allocator returned NULL */
   TT_ECUDA = 4,         /* a CUDA runtime call failed (message has the CUDA error) */
   TT_ENOCONV = 5,       /* Jacobi (TT-SVD) did not converge within its sweep cap */
-  TT_ETIMEOUT = 6,      /* reserved: a bounded device-side wait ran out */
+  TT_ETIMEOUT = 6,      /* a bounded wait inside a tensor-core kernel ran out (2 s); the
+                           kernel unwound and released its resources, the context stays usable */
   TT_EUNSUPPORTED = 7   /* valid request outside what this build implements */
 } tt_status;
 
@@ -56,7 +57,15 @@ typedef enum { TT_RL = 0, TT_LR = 1 } tt_direction;
  *  TT_P_FP64 : everything in FP64 (an FP32 input is widened first).
  *  TT_P_FP32 : FP32 data and FFMA products; FP64 for every cross-block sum,
  *              Gram matrix, norm and truncation-error accumulation.
- *  TT_P_MIXED: like TT_P_FP32 (reserved for tensor-core range finding). */
+ *  TT_P_MIXED: FP32 data, products on the tcgen05 tensor cores with FP32
+ *              accumulation.  The Gram matrix of an exact step (the one
+ *              product that only ranks directions) rounds its operands to
+ *              TF32; every other product carries each FP32 operand as two
+ *              TF32 terms (~2^-22 relative), so the sketch, Cholesky-QR,
+ *              projection, carry and core match the FP32 form to within a
+ *              few 1e-6.  Tight steps (see TT_SMALL_AUTO) run on the FP32
+ *              SIMT path, as do products whose leading dimensions are not
+ *              multiples of 4. */
 typedef enum { TT_P_FP64 = 0, TT_P_FP32 = 1, TT_P_MIXED = 2 } tt_precision;
 
 /* Arithmetic of the small (<= 256 x 256) factorizations:

@@ -113,6 +113,19 @@ ttk::StepInfo* pinned_info() {
   return h;
 }
 
+// Pinned copy of the device error word of the tensor-core kernels.
+int* pinned_err() {
+  thread_local int* h = nullptr;
+  thread_local int fallback = 0;
+  if (!h) {
+    if (cudaMallocHost((void**)&h, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      h = &fallback;
+    }
+  }
+  return h;
+}
+
 int64_t roundup(int64_t x, int64_t m) { return ((x + m - 1) / m) * m; }
 
 // TTUTV_DEBUG=1 prints one line per sweep step to stderr.
@@ -178,6 +191,46 @@ struct PhaseTimer {
   }
 };
 
+// Product routing.  With TT_P_MIXED, FP32 products run on the tensor cores
+// (tc_gemm: TF32 operands, split hi + lo where the product is part of the
+// kept factor) when their operands are eligible; Gram matrices that must
+// resolve errors below FP32 rounding (accurate) and everything else run on
+// the SIMT kernels (gemm<W>).
+struct MM {
+  bool tc;
+  int* err;
+  cudaStream_t st;
+};
+
+template <typename W>
+size_t mm_ws(const MM& mm, int64_t M, int64_t N, int64_t K, bool sym_or_out64) {
+  size_t b = ttk::gemm_ws_bytes<W>(M, N, K, sym_or_out64);
+  if constexpr (std::is_same<W, float>::value) {
+    if (mm.tc)
+      b = std::max(b, ttk::tc_gemm_ws_bytes(M, N, K, sym_or_out64, sym_or_out64, true, true));
+  }
+  return b;
+}
+
+template <typename W>
+cudaError_t mm_run(const MM& mm, ttk::Mat<W> A, ttk::Mat<W> B, int64_t M, int64_t N, int64_t K,
+                   W* out, int64_t ldo, double* out64, bool sym, double* sumsq, void* ws,
+                   bool accurate, bool a_split, bool b_split, bool round_out) {
+  if constexpr (std::is_same<W, float>::value) {
+    if (mm.tc && !accurate) {
+      ttk::TcOpts o;
+      o.a_split = a_split;
+      o.b_split = b_split;
+      o.round_out = round_out;
+      o.err = mm.err;
+      cudaError_t e = ttk::tc_gemm(A, B, M, N, K, out, ldo, out64, sym, sumsq, ws, mm.st, o);
+      if (e != cudaErrorNotSupported) return e;
+      cudaGetLastError();
+    }
+  }
+  return ttk::gemm<W>(A, B, M, N, K, out, ldo, out64, sym, sumsq, ws, mm.st, accurate);
+}
+
 struct SweepCfg {
   bool urv;   // basis on the column side, right-to-left
   bool svd;   // Jacobi small factor (TT-SVD)
@@ -230,7 +283,11 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   double* d_scal = scal.as<double>();
   double* d_x2first = d_scal;            // ||A||^2 when the first step is sketched
   double* d_carry2 = d_scal + 4;         // per step: ||carry||^2 (sum of squares of stored values)
+  int* d_err = (int*)(d_scal + 1);       // set by a tensor-core kernel whose bounded wait ran out
   TT_CK(cudaMemsetAsync(d_scal, 0, sizeof(double) * (4 + 2 * TT_MAXD), st), "memset");
+  int* herr = pinned_err();
+  const bool mixed = !W64 && o.precision == TT_P_MIXED;
+  const MM mm_all{mixed, d_err, st};
   Buf dinfo(&al);
   TT_ALLOC(dinfo, sizeof(ttk::StepInfo));
   ttk::StepInfo* hinfo = pinned_info();
@@ -310,19 +367,24 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     int64_t r = 1, l = 0;
     bool small64 = false;
     const W* Zp = nullptr;
+    const W* Wfin = nullptr;  // final sketch basis (sketch path)
     int64_t ldz = 0;
 
+    // Tight steps run entirely on the SIMT path: their tail estimates must be
+    // unbiased below FP32 rounding, which the tensor cores' accumulation is not.
+    MM mm = mm_all;
     if (exact) {
+      mm.tc = mm_all.tc && !tight(nb);
       TT_ALLOC(gb, (size_t)nb * nb * sizeof(double));
-      TT_ALLOC(ws, std::max(ttk::gemm_ws_bytes<W>(nb, nb, no, true), ttk::small_ws_bytes((int)nb, true)));
+      TT_ALLOC(ws, std::max(mm_ws<W>(mm, nb, nb, no, true), ttk::small_ws_bytes((int)nb, true)));
       const bool acc = !W64 && tight(nb);
       tm.begin(s, TT_PH_GRAM);
       if (cfg.urv)
-        TT_CK(ttk::gemm<W>({C, n, false}, {C, n, true}, n, n, m, nullptr, 0, gb.as<double>(), true,
-                           nullptr, ws.p, st, acc), "Gram C^T C");
+        TT_CK(mm_run<W>(mm, {C, n, false}, {C, n, true}, n, n, m, nullptr, 0, gb.as<double>(), true,
+                        nullptr, ws.p, acc, false, false, false), "Gram C^T C");
       else
-        TT_CK(ttk::gemm<W>({C, n, true}, {C, n, false}, m, m, n, nullptr, 0, gb.as<double>(), true,
-                           nullptr, ws.p, st, acc), "Gram C C^T");
+        TT_CK(mm_run<W>(mm, {C, n, true}, {C, n, false}, m, m, n, nullptr, 0, gb.as<double>(), true,
+                        nullptr, ws.p, acc, false, false, false), "Gram C C^T");
       tm.end();
       small64 = choose_small64(nb);
       prm.n = (int)nb;
@@ -339,8 +401,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
                               dinfo.as<ttk::StepInfo>(), st), "small factor");
       tm.end();
       TT_CK(cudaMemcpyAsync(hinfo, dinfo.p, sizeof(ttk::StepInfo), cudaMemcpyDeviceToHost, st), "info");
+      TT_CK(cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error word");
       TT_CK(cudaStreamSynchronize(st), "step sync");
       tm.collect();
+      if (*herr) return fail(TT_ETIMEOUT, "a bounded wait in a tensor-core kernel ran out");
       if (hinfo->status & 1) return fail(TT_ENONFINITE, "input holds NaN or Inf");
       if (hinfo->status & 2) return fail(TT_ENOCONV, "Jacobi eigen-solver did not converge");
       r = hinfo->r;
@@ -359,24 +423,34 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       while (true) {
         const bool identity = l >= no;
         small64 = choose_small64(l);
-        TT_ALLOC(omega, (size_t)no * l * sizeof(W));
+        mm.tc = mm_all.tc && !tight(l);
+        if (!identity) TT_ALLOC(omega, (size_t)no * l * sizeof(W));
         tm.begin(s, TT_PH_SKETCH);
-        TT_CK(ttk::fill_sketch(omega.p, W64, no, l, o.seed, (uint32_t)k, identity, st), "sketch matrix");
+        if (!identity)
+          TT_CK(ttk::fill_sketch(omega.p, W64, no, l, o.seed, (uint32_t)k, false, st), "sketch matrix");
         TT_ALLOC(yb, (size_t)nb * l * sizeof(W));
         size_t wsz = 0;
-        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(nb, l, no, false));
-        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(l, l, nb, true));
-        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(nb, l, l, false));
-        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(no, l, nb, false));
-        wsz = std::max(wsz, ttk::gemm_ws_bytes<W>(l, l, no, true));
+        wsz = std::max(wsz, mm_ws<W>(mm, nb, l, no, false));
+        wsz = std::max(wsz, mm_ws<W>(mm, l, l, nb, true));
+        wsz = std::max(wsz, mm_ws<W>(mm, nb, l, l, false));
+        wsz = std::max(wsz, mm_ws<W>(mm, no, l, nb, false));
+        wsz = std::max(wsz, mm_ws<W>(mm, l, l, no, true));
         TT_ALLOC(ws, wsz);
         TT_ALLOC(ws2, ttk::small_ws_bytes((int)l, true));
-        if (cfg.urv)
-          TT_CK(ttk::gemm<W>({C, n, false}, {omega.as<W>(), l, true}, n, l, m, yb.as<W>(), l,
-                             nullptr, false, nullptr, ws.p, st), "sketch C^T Omega");
+        // Omega = I (l = N_o): Y is C^T / C itself, copied exactly.  On the
+        // tensor cores C is split into two TF32 terms (Omega = +-1 is exact):
+        // TF32 rounding noise in Y would enter every sketch column at ~2^-12
+        // of its norm, outside the row space of C, and tilt the basis.
+        if (identity && cfg.urv)
+          TT_CK(ttk::copy2d(C, n, true, yb.p, l, nb, l, W64, st), "sketch C^T");
+        else if (identity)
+          TT_CK(ttk::copy2d(C, n, false, yb.p, l, nb, l, W64, st), "sketch C");
+        else if (cfg.urv)
+          TT_CK(mm_run<W>(mm, {C, n, false}, {omega.as<W>(), l, true}, n, l, m, yb.as<W>(), l,
+                          nullptr, false, nullptr, ws.p, false, true, false, false), "sketch C^T Omega");
         else
-          TT_CK(ttk::gemm<W>({C, n, true}, {omega.as<W>(), l, true}, m, l, n, yb.as<W>(), l,
-                             nullptr, false, nullptr, ws.p, st), "sketch C Omega");
+          TT_CK(mm_run<W>(mm, {C, n, true}, {omega.as<W>(), l, true}, m, l, n, yb.as<W>(), l,
+                          nullptr, false, nullptr, ws.p, false, true, false, false), "sketch C Omega");
         tm.end();
         omega.reset();
         // W = shifted Cholesky-QR3(Y): a shifted pass that cannot break
@@ -407,35 +481,37 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
           // weak directions, and the later passes then amplify rounding in them
           po.shift_rel = pass == 0 ? 4.0 * (double)l * u_c : 0.0;
           po.piv_tol = pass == 0 ? 0.0 : 64.0 * (double)l * u_c * u_c;
-          TT_CK(ttk::gemm<W>({src_pass, l, false}, {src_pass, l, true}, l, l, nb, nullptr, 0,
-                             gy.as<double>(), true, nullptr, ws.p, st, !W64 && small64),
+          TT_CK(mm_run<W>(mm, {src_pass, l, false}, {src_pass, l, true}, l, l, nb, nullptr, 0,
+                          gy.as<double>(), true, nullptr, ws.p, !W64 && small64, true, true, false),
                 "Gram of sketch");
           TT_CK(ttk::small_factor(gy.as<double>(), po, orth64, s1b.p, W64, (int)l, ws2.p,
                                   dinfo.as<ttk::StepInfo>(), st), "orthonormalize");
-          TT_CK(ttk::gemm<W>({src_pass, l, true}, {s1b.as<W>(), l, true}, nb, l, l, dst_pass[pass],
-                             l, nullptr, false, nullptr, ws.p, st), "apply R^-1");
+          TT_CK(mm_run<W>(mm, {src_pass, l, true}, {s1b.as<W>(), l, true}, nb, l, l, dst_pass[pass],
+                          l, nullptr, false, nullptr, ws.p, false, true, true, false), "apply R^-1");
           src_pass = dst_pass[pass];
         }
         tm.end();
-        const W* Wm = w1b.as<W>();
+        const W* Wm = src_pass;
+        Wfin = Wm;
         TT_ALLOC(bb, (size_t)no * l * sizeof(W));
         tm.begin(s, TT_PH_PROJECT);
         if (cfg.urv)
-          TT_CK(ttk::gemm<W>({C, n, true}, {Wm, l, true}, m, l, n, bb.as<W>(), l, nullptr, false,
-                             nullptr, ws.p, st), "project C W");
+          TT_CK(mm_run<W>(mm, {C, n, true}, {Wm, l, true}, m, l, n, bb.as<W>(), l, nullptr, false,
+                          nullptr, ws.p, false, true, true, false), "project C W");
         else
-          TT_CK(ttk::gemm<W>({C, n, false}, {Wm, l, true}, n, l, m, bb.as<W>(), l, nullptr, false,
-                             nullptr, ws.p, st), "project C^T W");
-        TT_CK(ttk::gemm<W>({bb.as<W>(), l, false}, {bb.as<W>(), l, true}, l, l, no, nullptr, 0,
-                           gy.as<double>(), true, nullptr, ws.p, st, !W64 && tight(l)), "Gram B^T B");
+          TT_CK(mm_run<W>(mm, {C, n, false}, {Wm, l, true}, n, l, m, bb.as<W>(), l, nullptr, false,
+                          nullptr, ws.p, false, true, true, false), "project C^T W");
+        TT_CK(mm_run<W>(mm, {bb.as<W>(), l, false}, {bb.as<W>(), l, true}, l, l, no, nullptr, 0,
+                        gy.as<double>(), true, nullptr, ws.p, !W64 && tight(l), true, true, false),
+              "Gram B^T B");
         // FP32 W is orthonormal only to ~1e-7, which biases ||X W||^2 and so
         // the range miss mu^2; with a tight tolerance the small factor
         // whitens by W^T W (exact products, FP64 sums).
         const bool whiten = !W64 && small64;
         if (whiten) {
           TT_ALLOC(gwb, (size_t)l * l * sizeof(double));
-          TT_CK(ttk::gemm<W>({Wm, l, false}, {Wm, l, true}, l, l, nb, nullptr, 0, gwb.as<double>(),
-                             true, nullptr, ws.p, st, true), "Gram W^T W");
+          TT_CK(mm_run<W>(mm, {Wm, l, false}, {Wm, l, true}, l, l, nb, nullptr, 0, gwb.as<double>(),
+                          true, nullptr, ws.p, true, false, false, false), "Gram W^T W");
         }
         prm.Gw = whiten ? gwb.as<double>() : nullptr;
         tm.end();
@@ -450,8 +526,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
                                 dinfo.as<ttk::StepInfo>(), st), "small factor");
         tm.end();
         TT_CK(cudaMemcpyAsync(hinfo, dinfo.p, sizeof(ttk::StepInfo), cudaMemcpyDeviceToHost, st), "info");
+        TT_CK(cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error word");
         TT_CK(cudaStreamSynchronize(st), "step sync");
         tm.collect();
+        if (*herr) return fail(TT_ETIMEOUT, "a bounded wait in a tensor-core kernel ran out");
         if (hinfo->status & 1) return fail(TT_ENONFINITE, "input holds NaN or Inf");
         if (hinfo->status & 2) return fail(TT_ENOCONV, "Jacobi eigen-solver did not converge");
         r = hinfo->r;
@@ -491,21 +569,21 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     {
       size_t wsz = 0;
       if (exact) {
-        wsz = cfg.urv ? ttk::gemm_ws_bytes<W>(m, r, n, false) : ttk::gemm_ws_bytes<W>(r, n, m, false);
+        wsz = cfg.urv ? mm_ws<W>(mm, m, r, n, false) : mm_ws<W>(mm, r, n, m, false);
       } else {
-        wsz = std::max(cfg.urv ? ttk::gemm_ws_bytes<W>(m, r, l, false) : ttk::gemm_ws_bytes<W>(r, n, l, false),
-                       cfg.urv ? ttk::gemm_ws_bytes<W>(r, n, l, false) : ttk::gemm_ws_bytes<W>(m, r, l, false));
+        wsz = std::max(cfg.urv ? mm_ws<W>(mm, m, r, l, false) : mm_ws<W>(mm, r, n, l, false),
+                       cfg.urv ? mm_ws<W>(mm, r, n, l, false) : mm_ws<W>(mm, m, r, l, false));
       }
       TT_ALLOC(ws, wsz);
     }
     if (exact) {
       tm.begin(s, TT_PH_CARRY);
       if (cfg.urv)
-        TT_CK(ttk::gemm<W>({C, n, true}, {Zp, ldz, true}, m, r, n, carry.as<W>(), r, nullptr, false,
-                           d_carry2 + s, ws.p, st), "carry C Z1");
+        TT_CK(mm_run<W>(mm, {C, n, true}, {Zp, ldz, true}, m, r, n, carry.as<W>(), r, nullptr, false,
+                        d_carry2 + s, ws.p, false, true, true, false), "carry C Z1");
       else
-        TT_CK(ttk::gemm<W>({Zp, ldz, false}, {C, n, true}, r, n, m, carry.as<W>(), n, nullptr, false,
-                           d_carry2 + s, ws.p, st), "carry Z1^T C");
+        TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {C, n, true}, r, n, m, carry.as<W>(), n, nullptr, false,
+                        d_carry2 + s, ws.p, false, true, true, false), "carry Z1^T C");
       tm.end();
       tm.begin(s, TT_PH_CORE);
       if (cfg.urv)
@@ -515,22 +593,22 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       tm.end();
     } else {
       const W* Bm = bb.as<W>();
-      const W* Wm = w1b.as<W>();
+      const W* Wm = Wfin;
       tm.begin(s, TT_PH_CARRY);
       if (cfg.urv)
-        TT_CK(ttk::gemm<W>({Bm, l, true}, {Zp, ldz, true}, m, r, l, carry.as<W>(), r, nullptr, false,
-                           d_carry2 + s, ws.p, st), "carry B Z1");
+        TT_CK(mm_run<W>(mm, {Bm, l, true}, {Zp, ldz, true}, m, r, l, carry.as<W>(), r, nullptr, false,
+                        d_carry2 + s, ws.p, false, true, true, false), "carry B Z1");
       else
-        TT_CK(ttk::gemm<W>({Zp, ldz, false}, {Bm, l, false}, r, n, l, carry.as<W>(), n, nullptr, false,
-                           d_carry2 + s, ws.p, st), "carry (B Z1)^T");
+        TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {Bm, l, false}, r, n, l, carry.as<W>(), n, nullptr, false,
+                        d_carry2 + s, ws.p, false, true, true, false), "carry (B Z1)^T");
       tm.end();
       tm.begin(s, TT_PH_CORE);
       if (cfg.urv)
-        TT_CK(ttk::gemm<W>({Zp, ldz, false}, {Wm, l, false}, r, n, l, core.as<W>(), n, nullptr, false,
-                           nullptr, ws.p, st), "core (W Z1)^T");
+        TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {Wm, l, false}, r, n, l, core.as<W>(), n, nullptr, false,
+                        nullptr, ws.p, false, true, true, false), "core (W Z1)^T");
       else
-        TT_CK(ttk::gemm<W>({Wm, l, true}, {Zp, ldz, true}, m, r, l, core.as<W>(), r, nullptr, false,
-                           nullptr, ws.p, st), "core W Z1");
+        TT_CK(mm_run<W>(mm, {Wm, l, true}, {Zp, ldz, true}, m, r, l, core.as<W>(), r, nullptr, false,
+                        nullptr, ws.p, false, true, true, false), "core W Z1");
       tm.end();
     }
     cores[k - 1] = core.release();
@@ -553,8 +631,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   cores[cfg.urv ? 0 : d - 1] = cbuf.release();
   double h_carry2[TT_MAXD];
   TT_CK(cudaMemcpyAsync(h_carry2, d_carry2, sizeof(double) * (d - 1), cudaMemcpyDeviceToHost, st), "tails");
+  TT_CK(cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error word");
   TT_CK(cudaStreamSynchronize(st), "final sync");
   tm.collect();
+  if (*herr) return fail(TT_ETIMEOUT, "a bounded wait in a tensor-core kernel ran out");
   for (int s = 0; s < d - 1; ++s) {
     const int k = cfg.urv ? d - s : s + 1;
     const int u = cfg.urv ? k - 1 : k;

@@ -44,6 +44,28 @@ cudaError_t gemm(Mat<T> A, Mat<T> B, int64_t M, int64_t N, int64_t K, T* out, in
                  double* out64, bool sym, double* sumsq, void* ws, cudaStream_t st,
                  bool accurate = false);
 
+// Tensor-core product (tc_gemm.cu): same contract as gemm<float> for FP32
+// data, computed with tcgen05 MMAs on TF32 operands rounded to nearest and
+// FP32 accumulation.  A split operand is carried as hi + lo (both TF32),
+// which makes its products accurate to ~2^-22 relative; round_out rounds the
+// FP32 result to TF32 (so it is exact as a later TF32 operand).  err is a
+// device int set to 1 when a bounded wait in the kernel ran out.
+// tc_gemm returns cudaErrorNotSupported for shapes or layouts it does not
+// take (leading dimensions not a multiple of 4, unaligned pointers, too many
+// Gram tiles); callers then use gemm<float>.
+struct TcOpts {
+  bool a_split = false;
+  bool b_split = false;
+  bool round_out = false;
+  int* err = nullptr;
+};
+bool tc_gemm_eligible(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K);
+size_t tc_gemm_ws_bytes(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_split,
+                        bool b_split);
+cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K, float* out,
+                    int64_t ldo, double* out64, bool sym, double* sumsq, void* ws, cudaStream_t st,
+                    TcOpts o);
+
 // Small single-CTA factorizations of an n x n FP64 Gram matrix (n <= 256).
 enum SmallMode { SM_QLP = 0, SM_JACOBI = 1, SM_ORTH = 2 };
 struct SmallParams {

@@ -388,15 +388,20 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
     pchol(a, n, false, 0.0, 0, 0.0, 0.0, 0, n, R1, ld, perm1, dbuf, Lbuf, dn, nullptr, sc);
     tri_inverse(R1, n, ld, X, tmp);
     for (int e = tid; e < nn * ld; e += FT) Tw[e] = X[e];
-    for (int e = tid; e < n * n; e += FT) {  // R2 = G T^{-1}
-      const int i = e / n, c = e % n;
-      double s = 0.0;
-      for (int k = 0; k <= c; ++k) s += G[i * n + k] * (double)X[k * ld + c];
-      R2[i * ld + c] = (T)s;
-    }
+    for (int e = tid; e < n * n; e += FT) R2[(e / n) * ld + e % n] = (T)G[e];
     __syncthreads();
-    // a = T^{-T} (G T^{-1}): a[r][c] = sum_k X[k][r] R2[k][c]
-    tile_product(a, n, n, n, [&](int r, int k) { return X[k * ld + r]; },
+    // G T^{-1} (T^{-1} upper triangular), back into R2
+    tile_product(a, n, n, n, [&](int r, int k) { return R2[r * ld + k]; },
+                 [&](int c, int k) { return k <= c ? X[k * ld + c] : T(0); });
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        if (tile_r(i) < n && tile_c(jj) < n) R2[tile_r(i) * ld + tile_c(jj)] = a[i][jj];
+    __syncthreads();
+    // a = T^{-T} (G T^{-1})
+    tile_product(a, n, n, n, [&](int r, int k) { return k <= r ? X[k * ld + r] : T(0); },
                  [&](int c, int k) { return R2[k * ld + c]; });
     double t2 = 0.0;
 #pragma unroll
@@ -491,17 +496,22 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
     }
   }
   __syncthreads();
-  // output (whitened: Z_1 = T^{-1} Zs)
-  for (int e = tid; e < n * r; e += FT) {
-    const int i = e / r, c = e % r;
-    T z;
-    if (prm.Gw) {
-      z = T(0);
-      for (int k = i; k < n; ++k) z += Tw[i * ld + k] * R2[k * ld + c];
-    } else {
-      z = R2[i * ld + c];
+  // output (whitened: Z_1 = T^{-1} Zs, T^{-1} brought back into X)
+  if (prm.Gw) {
+    for (int e = tid; e < nn * ld; e += FT) X[e] = Tw[e];
+    __syncthreads();
+    tile_product(a, n, r, n, [&](int i, int k) { return k >= i ? X[i * ld + k] : T(0); },
+                 [&](int c, int k) { return R2[k * ld + c]; });
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        if (tile_r(i) < n && tile_c(jj) < r) Z[(size_t)tile_r(i) * ldz + tile_c(jj)] = (ZT)a[i][jj];
+  } else {
+    for (int e = tid; e < n * r; e += FT) {
+      const int i = e / r, c = e % r;
+      Z[(size_t)i * ldz + c] = (ZT)R2[i * ld + c];
     }
-    Z[(size_t)i * ldz + c] = (ZT)z;
   }
   if (tid == 0) {
     info->r = r;

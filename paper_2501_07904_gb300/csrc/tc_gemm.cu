@@ -1,0 +1,764 @@
+// Tensor-core (tcgen05) products for the mixed-precision sweep: D = A B with
+// FP32 data, TF32 operands rounded to nearest, FP32 accumulation.
+//
+// One persistent CTA per SM, ten warps with fixed roles:
+//   warp 0     TMA producer: 2-D tensor-map copies of the FP32 operand
+//              slabs (128 rows x 32 k of A, n_mma rows x 32 k of B) into a
+//              staging ring;
+//   warp 1     allocates tensor memory; one lane issues tcgen05.mma;
+//   warps 2-5  converters: round the staged FP32 values to TF32 (and, for a
+//              split operand, the TF32 rounding of the remainder), writing
+//              K-major 128-byte-swizzled operand tiles;
+//   warps 6-9  epilogue: after every k-block (one TMEM chunk) the
+//              accumulator is read back and added into a running FP32 sum
+//              kept in spare TMEM columns, which bounds the rounding drift of
+//              the tensor-core accumulation; at the end of a work segment the
+//              sum goes to the output or to a partial.
+// Work is scheduled stream-K: the (tile, k-block) sequence is cut into one
+// contiguous range per CTA, so a few output tiles over a long K (Gram
+// matrices, sketches) still occupy every SM.  Tiles covered by several CTAs
+// are finished by a fix-up kernel that adds the partials in CTA order
+// (deterministic).  A split operand x = hi + lo (both TF32) makes the
+// product accurate to ~2^-22 relative (three MMAs per k-step when both are
+// split: hi*hi + hi*lo + lo*hi).
+//
+// Every mbarrier wait is bounded (tc_common.cuh): a stall sets the error
+// word, the roles unwind, in-flight copies and MMAs are drained and the
+// tensor memory is released before the kernel returns.
+#include <cuda.h>
+
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace ttk {
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 320;
+constexpr int kBM = 128;       // rows of an output tile (MMA M)
+constexpr int kBK = 32;        // k per staged slab (one 128-byte swizzle row of TF32)
+// k-blocks accumulated in TMEM before the epilogue drains them into the
+// running sum: the tensor-core accumulation drifts toward zero by up to about
+// one FP32 ulp per accumulate step, so chunks are kept to one k-block (at
+// most 12 MMAs) and the long sums are carried in round-to-nearest FP32 adds.
+constexpr int kChunkKB = 1;
+constexpr int kMaxStages = 8;
+constexpr int kSmemBudget = 225 * 1024;
+
+struct TcArgs {
+  int64_t M, N, K;
+  int kb;            // k-blocks per tile
+  int ntm, ntn;      // tile grid (rows, cols of tiles)
+  int ntiles;
+  int64_t total;     // ntiles * kb
+  int G;             // CTAs
+  int n_mma;         // MMA N (multiple of 16, <= NREG)
+  int a_kmajor, b_kmajor;  // source layouts (1: contiguous along k)
+  int a_split, b_split;
+  int sym;           // Gram: upper tiles only, diagonal tiles use A for B
+  int all_partial;   // every segment writes a partial (FP64 output / mirroring)
+  int round_out;     // round FP32 outputs to TF32
+  int S_st, S_op;    // ring depths
+  uint32_t stage_bytes, a_box_bytes, b_box_bytes, op_bytes;
+  float* out;
+  int64_t ldo;
+  float* part;       // [G][2][128][NREG]
+  double* sq_part;   // [G] (sum of squares of directly written outputs) or null
+  int* err;
+};
+
+__device__ __forceinline__ int64_t seg_beg(const TcArgs& a, int c) {
+  return (int64_t)c * a.total / a.G;
+}
+
+// Tile t -> (row tile, col tile); a Gram enumerates the upper triangle row by row.
+__host__ __device__ __forceinline__ void tile_coords(int t, int ntm, int ntn, int sym, int& mt,
+                                                     int& nt) {
+  if (!sym) {
+    mt = t / ntn;
+    nt = t % ntn;
+    return;
+  }
+  mt = 0;
+  int row_len = ntn;
+  while (t >= row_len) {
+    t -= row_len;
+    ++mt;
+    --row_len;
+  }
+  nt = mt + t;
+}
+
+// Position in the (tile, k-block) sequence, advanced without divisions.
+struct Cursor {
+  int t, kbi, mt, nt;
+  __device__ __forceinline__ void init(const TcArgs& a, int64_t pos) {
+    t = (int)(pos / a.kb);
+    kbi = (int)(pos % a.kb);
+    tile_coords(t, a.ntm, a.ntn, a.sym, mt, nt);
+  }
+  __device__ __forceinline__ void next_tile(const TcArgs& a) {
+    kbi = 0;
+    ++t;
+    if (++nt == a.ntn) {
+      ++mt;
+      nt = a.sym ? mt : 0;
+    }
+  }
+  __device__ __forceinline__ void next(const TcArgs& a) {
+    if (++kbi == a.kb) next_tile(a);
+  }
+};
+
+// Convert one staged FP32 slab into a K-major SW128 TF32 tile of R rows
+// (R a multiple of 16, at most 128); hi/lo are shared addresses, lo = 0 for
+// an unsplit operand.  A thread owns the 16-byte chunks idx = ct + 128 j of a
+// K-major source (row idx / 8, chunk idx % 8), or row ct of an MN-major one;
+// all of its loads are issued before the first conversion.
+//   K-major source:  staging [R][32]  (one float4 per chunk)
+//   MN-major source: staging [32][R]  (four floats, stride R, per chunk)
+__device__ __forceinline__ void store_chunk(uint32_t hi, uint32_t lo, uint32_t off, float4 v) {
+  const uint32_t h0 = to_tf32(v.x), h1 = to_tf32(v.y), h2 = to_tf32(v.z), h3 = to_tf32(v.w);
+  sts128(hi + off, h0, h1, h2, h3);
+  if (lo)
+    sts128(lo + off, to_tf32(v.x - __uint_as_float(h0)), to_tf32(v.y - __uint_as_float(h1)),
+           to_tf32(v.z - __uint_as_float(h2)), to_tf32(v.w - __uint_as_float(h3)));
+}
+
+__device__ __forceinline__ void convert_slab(uint32_t stg, int kmajor, int R, uint32_t hi,
+                                             uint32_t lo, int ct) {
+  const int nchunks = R * 8;  // <= 1024: at most 8 per thread
+  float4 v[8];
+  if (kmajor) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int idx = ct + 128 * j;
+      if (idx < nchunks) v[j] = lds128(stg + (uint32_t)idx * 16u);  // row idx/8, chunk idx%8
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int idx = ct + 128 * j;
+      if (idx < nchunks) store_chunk(hi, lo, sw128_off((uint32_t)(idx >> 3), (uint32_t)(idx & 7) * 4u), v[j]);
+    }
+  } else if (ct < R) {
+    // thread ct owns row ct: chunks q = 0..7 (k = 4q..4q+3)
+    const uint32_t p0 = stg + (uint32_t)ct * 4u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t p = p0 + (uint32_t)(q * 4 * R) * 4u;
+      v[q].x = lds32(p);
+      v[q].y = lds32(p + 4u * R);
+      v[q].z = lds32(p + 8u * R);
+      v[q].w = lds32(p + 12u * R);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) store_chunk(hi, lo, sw128_off((uint32_t)ct, (uint32_t)q * 4u), v[q]);
+  }
+}
+
+__device__ __forceinline__ float round_tf32(float x) { return __uint_as_float(to_tf32(x)); }
+
+template <int NREG>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte alignment of the tiles (SW128 atoms) is established by hand.
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)smem;  // 64 barriers
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kMaxStages;
+  uint64_t* opfull = bars + 2 * kMaxStages;
+  uint64_t* opempty = bars + 3 * kMaxStages;
+  uint64_t* accfull = bars + 4 * kMaxStages;
+  uint64_t* accempty = accfull + 2;
+  uint64_t* finalbar = accfull + 4;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 48);
+  double* red = (double*)(bars + 56);  // 4 doubles
+  uint8_t* stage_base = smem + 1024;
+  uint8_t* op_base = stage_base + (size_t)a.S_st * a.stage_bytes;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = blockIdx.x;
+
+  if (tid == 0) {
+    for (int s = 0; s < a.S_st; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 128);
+    }
+    for (int t = 0; t < a.S_op; ++t) {
+      mbar_init(&opfull[t], 128);
+      mbar_init(&opempty[t], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 128);
+    }
+    mbar_init(finalbar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, 4 * NREG);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int64_t beg = seg_beg(a, c), end = seg_beg(a, c + 1);
+  const int first_tile = (int)(beg / a.kb);
+
+  if (warp == 0) {
+    // ---------------- TMA producer (warp-wide loop, one elected issuer) ----------------
+    int s = 0;
+    uint32_t ph = 0;
+    uint32_t issued = 0u, issued_ph = 0u;  // per-stage bits
+    bool ok = true;
+    Cursor cur;
+    cur.init(a, beg);
+    for (int64_t pos = beg; pos < end; ++pos, cur.next(a)) {
+      const bool same = a.sym && cur.mt == cur.nt;
+      ok = __all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1u, a.err));
+      if (!ok) break;
+      if (elect_one()) {
+        uint8_t* st = stage_base + (size_t)s * a.stage_bytes;
+        mbar_arrive_expect_tx(&full[s], a.a_box_bytes + (same ? 0u : a.b_box_bytes));
+        const int k0 = cur.kbi * kBK;
+        if (a.a_kmajor)
+          tma_load_2d(st, &mapA, k0, cur.mt * kBM, &full[s]);
+        else
+          tma_load_2d(st, &mapA, cur.mt * kBM, k0, &full[s]);
+        if (!same) {
+          const int n0 = cur.nt * NREG;
+          if (a.b_kmajor)
+            tma_load_2d(st + a.a_box_bytes, &mapB, k0, n0, &full[s]);
+          else
+            tma_load_2d(st + a.a_box_bytes, &mapB, n0, k0, &full[s]);
+        }
+      }
+      __syncwarp();
+      issued |= 1u << s;
+      issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
+      if (++s == a.S_st) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+    if (!ok) {
+      // drain copies still in flight before the CTA's shared memory goes away
+      for (int i = 0; i < a.S_st; ++i) {
+        if (!((issued >> i) & 1u)) continue;
+        const uint64_t t0 = globaltimer_ns();
+        while (!mbar_try_wait(&full[i], (issued_ph >> i) & 1u) &&
+               globaltimer_ns() - t0 < kWaitLimitNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (warp-wide loop, one elected issuer) ----------------
+    const uint32_t idesc = idesc_tf32(kBM, a.n_mma);
+    const uint32_t op0 = smem_u32(op_base);
+    int t_op = 0;
+    uint32_t ph_op = 0;
+    uint32_t fills[2] = {0u, 0u};
+    int buf = 0;
+    bool ok = true;
+    int64_t pos = beg;
+    Cursor cur;
+    cur.init(a, beg);
+    while (pos < end && ok) {
+      const int kstart = cur.kbi;
+      const int kend = (int)std::min<int64_t>((int64_t)a.kb, kstart + (end - pos));
+      const bool same = a.sym && cur.mt == cur.nt;
+      for (int kbi = kstart; kbi < kend; ++kbi) {
+        const int local = kbi - kstart;
+        const bool chunk_start = (local % kChunkKB) == 0;
+        if (chunk_start) {
+          ok = __all_sync(0xffffffffu, mbar_wait(&accempty[buf], (fills[buf] & 1u) ^ 1u, a.err));
+          if (!ok) break;
+        }
+        ok = __all_sync(0xffffffffu, mbar_wait(&opfull[t_op], ph_op, a.err));
+        if (!ok) break;
+        const uint32_t a_hi = op0 + (uint32_t)t_op * a.op_bytes;
+        const uint32_t a_lo = a_hi + 16384u;
+        const uint32_t b_hi = same ? a_hi : a_hi + (a.a_split ? 32768u : 16384u);
+        const uint32_t b_lo = same ? a_lo : b_hi + (uint32_t)a.n_mma * 128u;
+        const uint32_t d = tmem + (uint32_t)(buf * NREG);
+        const bool chunk_end = (local % kChunkKB == kChunkKB - 1) || (kbi == kend - 1);
+        if (elect_one()) {
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t acc = (chunk_start && kk == 0) ? 0u : 1u;
+            const uint64_t dah = make_sw128_desc(a_hi + kk * 32);
+            const uint64_t dbh = make_sw128_desc(b_hi + kk * 32);
+            mma_tf32(d, dah, dbh, idesc, acc);
+            if (a.b_split) mma_tf32(d, dah, make_sw128_desc(b_lo + kk * 32), idesc, 1u);
+            if (a.a_split) mma_tf32(d, make_sw128_desc(a_lo + kk * 32), dbh, idesc, 1u);
+          }
+          mma_commit(&opempty[t_op]);
+          if (chunk_end) mma_commit(&accfull[buf]);
+        }
+        __syncwarp();
+        if (++t_op == a.S_op) {
+          t_op = 0;
+          ph_op ^= 1u;
+        }
+        if (chunk_end) {
+          ++fills[buf];
+          buf ^= 1;
+        }
+      }
+      pos += kend - kstart;
+      cur.next_tile(a);
+    }
+    // every MMA issued so far has completed once this barrier flips
+    if (elect_one()) mma_commit(finalbar);
+    __syncwarp();
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(finalbar, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
+    }
+  } else if (warp < 6) {
+    // ---------------- converters ----------------
+    const int ct = tid - 64;
+    int s = 0, t_op = 0;
+    uint32_t ph = 0, ph_op = 0;
+    Cursor cur;
+    cur.init(a, beg);
+    for (int64_t pos = beg; pos < end; ++pos, cur.next(a)) {
+      const bool same = a.sym && cur.mt == cur.nt;
+      bool ok = mbar_wait(&full[s], ph, a.err);
+      ok = ok && mbar_wait(&opempty[t_op], ph_op ^ 1u, a.err);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      const uint32_t st = smem_u32(stage_base) + (uint32_t)s * a.stage_bytes;
+      const uint32_t op = smem_u32(op_base) + (uint32_t)t_op * a.op_bytes;
+      convert_slab(st, a.a_kmajor, kBM, op, a.a_split ? op + 16384u : 0u, ct);
+      if (!same) {
+        const uint32_t bh = op + (a.a_split ? 32768u : 16384u);
+        convert_slab(st + a.a_box_bytes, a.b_kmajor, a.n_mma, bh,
+                     a.b_split ? bh + (uint32_t)a.n_mma * 128u : 0u, ct);
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&opfull[t_op]);
+      mbar_arrive(&empty[s]);
+      if (++s == a.S_st) {
+        s = 0;
+        ph ^= 1u;
+      }
+      if (++t_op == a.S_op) {
+        t_op = 0;
+        ph_op ^= 1u;
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    // TMEM columns [0, 2 NREG) are the two MMA buffers, [2 NREG, 3 NREG) the
+    // running FP32 sum of the current segment's drained chunks.
+    const int q = warp & 3;               // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;        // tile row owned by this thread
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    const uint32_t sum_addr = lane_addr + 2u * NREG;
+    double sq = 0.0;
+    int buf = 0;
+    uint32_t drains[2] = {0u, 0u};
+    bool ok = true;
+    int64_t pos = beg;
+    Cursor cur;
+    cur.init(a, beg);
+    while (pos < end && ok) {
+      const int t = cur.t, kstart = cur.kbi, mt = cur.mt, nt = cur.nt;
+      const int kend = (int)std::min<int64_t>((int64_t)a.kb, kstart + (end - pos));
+      const int nchunks = (kend - kstart + kChunkKB - 1) / kChunkKB;
+      const bool direct = (kstart == 0 && kend == a.kb) && !a.all_partial;
+      const int64_t m = (int64_t)mt * kBM + row;
+      const int64_t n0 = (int64_t)nt * NREG;
+      const int ncols = (int)std::min<int64_t>((int64_t)NREG, a.N - n0);
+      float* o = a.out + m * a.ldo + n0;
+      const bool vec = ((a.ldo & 3) == 0) && ((((uintptr_t)a.out) & 15) == 0);
+      float* pp = a.part + (((size_t)c * 2 + ((t == first_tile) ? 0 : 1)) * kBM + row) * NREG;
+      float rs = 0.f;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        bool w = mbar_wait(&accfull[buf], drains[buf] & 1u, a.err);
+        if (!__all_sync(0xffffffffu, w)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const bool last = (ch == nchunks - 1);
+#pragma unroll 1
+        for (int c32 = 0; c32 < NREG / 32; ++c32) {
+          float v[32];
+          tmem_ld32(lane_addr + (uint32_t)(buf * NREG + c32 * 32), v);
+          if (ch > 0) {
+            float u[32];
+            tmem_ld32(sum_addr + (uint32_t)(c32 * 32), u);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] += u[j];
+          }
+          if (!last) {
+            tmem_st32(sum_addr + (uint32_t)(c32 * 32), v);
+            continue;
+          }
+          if (direct) {
+            if (m < a.M) {
+              const int jb = c32 * 32;
+#pragma unroll
+              for (int j = 0; j < 32; j += 4) {
+                float v0 = v[j], v1 = v[j + 1], v2 = v[j + 2], v3 = v[j + 3];
+                if (a.round_out) {
+                  v0 = round_tf32(v0);
+                  v1 = round_tf32(v1);
+                  v2 = round_tf32(v2);
+                  v3 = round_tf32(v3);
+                }
+                const int jj = jb + j;
+                if (jj + 3 < ncols) {
+                  if (vec) {
+                    *reinterpret_cast<float4*>(o + jj) = make_float4(v0, v1, v2, v3);
+                  } else {
+                    o[jj] = v0;
+                    o[jj + 1] = v1;
+                    o[jj + 2] = v2;
+                    o[jj + 3] = v3;
+                  }
+                  rs += v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
+                } else {
+                  if (jj < ncols) { o[jj] = v0; rs += v0 * v0; }
+                  if (jj + 1 < ncols) { o[jj + 1] = v1; rs += v1 * v1; }
+                  if (jj + 2 < ncols) { o[jj + 2] = v2; rs += v2 * v2; }
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(pp + c32 * 32 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&accempty[buf]);
+        ++drains[buf];
+        buf ^= 1;
+      }
+      sq += (double)rs;
+      pos += kend - kstart;
+      cur.next_tile(a);
+    }
+    if (a.sq_part) {
+      for (int o2 = 16; o2 > 0; o2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o2);
+      if (lane == 0) red[q] = sq;
+      named_barrier(1, 128);
+      if (tid == 192) a.sq_part[c] = red[0] + red[1] + red[2] + red[3];
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 4 * NREG);
+}
+
+// Finish tiles covered by more than one CTA (or every tile when all_partial):
+// partials added in CTA order in FP64, mirrored for a Gram.  blockIdx.y
+// selects kFixRows rows of the tile.
+constexpr int kFixRows = 4;
+
+template <int NREG>
+__global__ void tc_fixup_kernel(TcArgs a, double* __restrict__ out64, double* __restrict__ fix_sq) {
+  __shared__ double red[32];
+  int t;
+  if (a.all_partial) {
+    t = blockIdx.x;
+  } else {
+    // block b finishes the tile in which CTA b's range starts, when that
+    // start lies strictly inside a tile and no earlier CTA start does
+    const int b = blockIdx.x;
+    t = -1;
+    if (b >= 1 && b < a.G) {
+      const int64_t pb = seg_beg(a, b);
+      const int tt = (int)(pb / a.kb);
+      if (pb % a.kb != 0 && seg_beg(a, b - 1) <= (int64_t)tt * a.kb) t = tt;
+    }
+  }
+  double sq = 0.0;
+  if (t >= 0) {
+    int mt, nt;
+    tile_coords(t, a.ntm, a.ntn, a.sym, mt, nt);
+    const int64_t p_lo = (int64_t)t * a.kb, p_hi = p_lo + a.kb - 1;
+    const int c_lo = (int)(((p_lo + 1) * a.G - 1) / a.total);
+    const int c_hi = (int)(((p_hi + 1) * a.G - 1) / a.total);
+    const int64_t m0 = (int64_t)mt * kBM, n0 = (int64_t)nt * NREG;
+    const int i0 = blockIdx.y * kFixRows;
+    for (int e = threadIdx.x; e < kFixRows * NREG; e += blockDim.x) {
+      const int i = i0 + e / NREG, j = e % NREG;
+      const int64_t m = m0 + i, n = n0 + j;
+      if (m >= a.M || n >= a.N) continue;
+      double s = 0.0;
+      for (int cc = c_lo; cc <= c_hi; ++cc) {
+        const int slot = (seg_beg(a, cc) / a.kb == t) ? 0 : 1;
+        s += (double)a.part[(((size_t)cc * 2 + slot) * kBM + i) * NREG + j];
+      }
+      const bool mirror = a.sym && mt != nt;
+      if (out64) {
+        out64[m * a.N + n] = s;
+        if (mirror) out64[n * a.N + m] = s;
+      }
+      if (a.out) {
+        float v = (float)s;
+        if (a.round_out) v = round_tf32(v);
+        a.out[m * a.ldo + n] = v;
+        sq += (double)v * (double)v;
+        if (mirror) {
+          a.out[n * a.ldo + m] = v;
+          sq += (double)v * (double)v;
+        }
+      }
+    }
+  }
+  if (fix_sq) {
+    sq = block_sum(sq, red);
+    if (threadIdx.x == 0) fix_sq[(size_t)blockIdx.x * gridDim.y + blockIdx.y] = sq;
+  }
+}
+
+__global__ void tc_sumsq_kernel(const double* __restrict__ a, int na, const double* __restrict__ b,
+                                int nb, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < na; i += blockDim.x) s += a[i];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += b[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct DevInfo {
+  int sms = 0;
+  bool attr_set[3] = {false, false, false};
+};
+
+std::mutex g_mu;
+EncodeTiledFn g_encode = nullptr;
+std::vector<DevInfo> g_dev;
+
+cudaError_t dev_info(DevInfo** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return cudaErrorNotSupported;
+    }
+    g_encode = (EncodeTiledFn)fn;
+  }
+  if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+  DevInfo& d = g_dev[dev];
+  if (d.sms == 0) {
+    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  *out = &d;
+  return cudaSuccess;
+}
+
+struct Plan {
+  TcArgs a;
+  int nreg;
+  size_t smem;
+  size_t part_bytes, sq_bytes, fix_bytes;
+  int fix_blocks;
+};
+
+int64_t ceil_div(int64_t x, int64_t y) { return (x + y - 1) / y; }
+
+bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_split, bool b_split,
+               int sms, Plan& p) {
+  memset(&p, 0, sizeof(p));
+  TcArgs& a = p.a;
+  const int64_t nw = std::min<int64_t>(N, 128);
+  p.nreg = nw <= 32 ? 32 : (nw <= 64 ? 64 : 128);
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.n_mma = (int)std::min<int64_t>(p.nreg, ceil_div(nw, 16) * 16);
+  a.kb = (int)ceil_div(K, kBK);
+  a.ntm = (int)ceil_div(M, kBM);
+  a.ntn = (int)ceil_div(N, p.nreg);
+  if (sym) {
+    if (M != N || p.nreg != 128 && a.ntm != 1) return false;
+    if (a.ntm != a.ntn) return false;
+    a.ntiles = a.ntm * (a.ntm + 1) / 2;
+  } else {
+    a.ntiles = a.ntm * a.ntn;
+  }
+  a.sym = sym ? 1 : 0;
+  a.total = (int64_t)a.ntiles * a.kb;
+  a.all_partial = (sym || out64) ? 1 : 0;
+  int64_t G = std::min<int64_t>((int64_t)sms, std::max<int64_t>(1, ceil_div(a.total, 4)));
+  if (a.all_partial) {
+    // each CTA range no longer than a tile: at most two tiles (partial slots) per CTA
+    G = std::max<int64_t>(G, a.ntiles);
+    if (G > sms) return false;
+    G = std::min<int64_t>(G, a.total);
+  }
+  a.G = (int)G;
+  a.a_split = a_split ? 1 : 0;
+  a.b_split = b_split ? 1 : 0;
+  a.a_box_bytes = kBM * kBK * 4;
+  a.b_box_bytes = (uint32_t)a.n_mma * kBK * 4;
+  // a Gram's off-diagonal tiles load B; diagonal ones reuse A
+  const bool any_b = !sym || a.ntm > 1;
+  a.stage_bytes = a.a_box_bytes + (any_b ? a.b_box_bytes : 0u);
+  a.stage_bytes = (a.stage_bytes + 1023u) & ~1023u;
+  a.op_bytes = 16384u * (a_split ? 2u : 1u) + (any_b ? (uint32_t)a.n_mma * 128u * (b_split ? 2u : 1u) : 0u);
+  a.op_bytes = (a.op_bytes + 1023u) & ~1023u;
+  const size_t fixed = 2048 + 1024;  // barriers + alignment slack
+  a.S_op = 2;
+  if (fixed + 4 * (size_t)a.stage_bytes + 3 * (size_t)a.op_bytes <= (size_t)kSmemBudget) a.S_op = 3;
+  const size_t left = kSmemBudget - fixed - (size_t)a.S_op * a.op_bytes;
+  a.S_st = (int)std::min<size_t>(kMaxStages, left / a.stage_bytes);
+  if (a.S_st < 2) return false;
+  p.smem = fixed + (size_t)a.S_st * a.stage_bytes + (size_t)a.S_op * a.op_bytes;
+  p.part_bytes = ((size_t)G * 2 * kBM * p.nreg * sizeof(float) + 255) & ~(size_t)255;
+  p.sq_bytes = ((size_t)G * sizeof(double) + 255) & ~(size_t)255;
+  p.fix_blocks = a.all_partial ? a.ntiles : (int)G;
+  p.fix_bytes = ((size_t)p.fix_blocks * (kBM / kFixRows) * sizeof(double) + 255) & ~(size_t)255;
+  return true;
+}
+
+// Tensor map of an FP32 operand: rows R (the M or N side) by K.
+bool encode(CUtensorMap* map, const float* p, int64_t ld, bool kmajor, int64_t R, int64_t K,
+            int box_rows) {
+  cuuint64_t dims[2], strides[1];
+  cuuint32_t box[2], estr[2] = {1, 1};
+  if (kmajor) {
+    dims[0] = (cuuint64_t)K;
+    dims[1] = (cuuint64_t)R;
+    box[0] = kBK;
+    box[1] = (cuuint32_t)box_rows;
+  } else {
+    dims[0] = (cuuint64_t)R;
+    dims[1] = (cuuint64_t)K;
+    box[0] = (cuuint32_t)box_rows;
+    box[1] = kBK;
+  }
+  strides[0] = (cuuint64_t)ld * sizeof(float);
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)p, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int NREG>
+cudaError_t launch(const Plan& p, const CUtensorMap& ma, const CUtensorMap& mb, DevInfo* d,
+                   int slot, cudaStream_t st) {
+  if (!d->attr_set[slot]) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<NREG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBudget);
+    if (e != cudaSuccess) return e;
+    d->attr_set[slot] = true;
+  }
+  tc_gemm_kernel<NREG><<<p.a.G, kThreads, p.smem, st>>>(ma, mb, p.a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_gemm_eligible(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K) {
+  if (M <= 0 || N <= 0 || K <= 0) return false;
+  if ((A.ld & 3) || (B.ld & 3) || (((uintptr_t)A.p) & 15) || (((uintptr_t)B.p) & 15)) return false;
+  if (K > INT32_MAX - 64 || M > INT32_MAX - 256 || N > INT32_MAX - 256) return false;
+  // TMA strides below 2^40 bytes
+  if ((uint64_t)A.ld * 4 >= (1ull << 40) || (uint64_t)B.ld * 4 >= (1ull << 40)) return false;
+  return true;
+}
+
+size_t tc_gemm_ws_bytes(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_split,
+                        bool b_split) {
+  DevInfo* d = nullptr;
+  int sms = 152;
+  if (dev_info(&d) == cudaSuccess) sms = d->sms;
+  Plan p;
+  if (!make_plan(M, N, K, sym, out64, a_split, b_split, sms, p)) return 0;
+  return p.part_bytes + p.sq_bytes + p.fix_bytes + 256;
+}
+
+cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K, float* out,
+                    int64_t ldo, double* out64, bool sym, double* sumsq, void* ws, cudaStream_t st,
+                    TcOpts o) {
+  if (!tc_gemm_eligible(A, B, M, N, K)) return cudaErrorNotSupported;
+  if (!out && !out64) return cudaErrorInvalidValue;
+  if (sumsq && !out) return cudaErrorInvalidValue;
+  if (!o.err) return cudaErrorInvalidValue;
+  DevInfo* d = nullptr;
+  cudaError_t e = dev_info(&d);
+  if (e != cudaSuccess) return e;
+  Plan p;
+  if (!make_plan(M, N, K, sym, out64 != nullptr, o.a_split, o.b_split, d->sms, p))
+    return cudaErrorNotSupported;
+  TcArgs& a = p.a;
+  a.a_kmajor = A.row ? 1 : 0;   // A(i,k) = p[i*ld + k]
+  a.b_kmajor = B.row ? 0 : 1;   // B(k,j) = p[k + j*ld]
+  a.round_out = o.round_out ? 1 : 0;
+  a.out = out;
+  a.ldo = ldo;
+  a.err = o.err;
+  char* w = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  a.part = (float*)w;
+  double* sq_part = (double*)(w + p.part_bytes);
+  double* fix_sq = (double*)(w + p.part_bytes + p.sq_bytes);
+  a.sq_part = sumsq ? sq_part : nullptr;
+
+  CUtensorMap ma, mb;
+  if (!encode(&ma, A.p, A.ld, a.a_kmajor != 0, M, K, kBM)) return cudaErrorInvalidValue;
+  if (!encode(&mb, B.p, B.ld, a.b_kmajor != 0, N, K, a.n_mma)) return cudaErrorInvalidValue;
+
+  const int slot = p.nreg == 32 ? 0 : (p.nreg == 64 ? 1 : 2);
+  int nl = 1;
+  if (p.nreg == 32)
+    e = launch<32>(p, ma, mb, d, slot, st);
+  else if (p.nreg == 64)
+    e = launch<64>(p, ma, mb, d, slot, st);
+  else
+    e = launch<128>(p, ma, mb, d, slot, st);
+  if (e != cudaSuccess) return e;
+  const bool need_fix = a.all_partial || a.G > 1;
+  if (need_fix) {
+    ++nl;
+    const dim3 fg((unsigned)p.fix_blocks, kBM / kFixRows);
+    if (p.nreg == 32)
+      tc_fixup_kernel<32><<<fg, 256, 0, st>>>(a, out64, sumsq ? fix_sq : nullptr);
+    else if (p.nreg == 64)
+      tc_fixup_kernel<64><<<fg, 256, 0, st>>>(a, out64, sumsq ? fix_sq : nullptr);
+    else
+      tc_fixup_kernel<128><<<fg, 256, 0, st>>>(a, out64, sumsq ? fix_sq : nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (sumsq) {
+    ++nl;
+    tc_sumsq_kernel<<<1, 256, 0, st>>>(sq_part, a.G, fix_sq,
+                                       need_fix ? p.fix_blocks * (kBM / kFixRows) : 0, sumsq);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  count_launch(nl);
+  return cudaSuccess;
+}
+
+}  // namespace ttk
