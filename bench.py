@@ -162,17 +162,29 @@ def ncu_traffic(kernel_key, workload):
     return None if ent is None else ent.get("traffic_bytes")
 
 
-def phase_model(wl, ranks):
-    """Algorithmic bytes and flops of the dominant per-step kernels (first
-    unfolding of the right-to-left sweep: C is prod(I_1..I_{d-1}) x I_d)."""
+def phase_model(wl, res):
+    """Algorithmic bytes and flops of the streaming products of every step of
+    the right-to-left sweep, keyed (step, phase).  Step s factors unfolding
+    C (m x n), m = I_1...I_{k-1}, n = I_k r_k, k = d - s: an exact step reads C
+    for the Gram and again for the carry C Z (m x r); a sketched step (width
+    l) reads C for Y = C^T Omega and again for B = C W (the project phase also
+    forms B^T B)."""
     dims = wl["dims"]
-    m = int(np.prod(dims[:-1]))
-    n = dims[-1]
-    r = ranks[-2]
-    return {
-        "gram": dict(bytes=4.0 * m * n, flops=float(m) * n * (n + 1)),
-        "carry": dict(bytes=4.0 * m * n + 4.0 * m * r, flops=2.0 * m * n * r),
-    }
+    d = len(dims)
+    out = {}
+    for s in range(d - 1):
+        k = d - s
+        m = int(np.prod(dims[:k - 1]))
+        n = dims[k - 1] * res.ranks[k]
+        r = res.ranks[k - 1]
+        l = res.sketch_l[k - 2]
+        if l == 0:
+            out[(s, "gram")] = dict(bytes=4.0 * m * n, flops=float(m) * n * (n + 1))
+            out[(s, "carry")] = dict(bytes=4.0 * m * n + 4.0 * m * r, flops=2.0 * m * n * r)
+        else:
+            out[(s, "sketch")] = dict(bytes=4.0 * m * n + 4.0 * n * l, flops=2.0 * m * n * l)
+            out[(s, "project")] = dict(bytes=4.0 * m * n + 8.0 * m * l, flops=2.0 * m * n * l + float(m) * l * (l + 1))
+    return out
 
 
 # --------------------------------------------------------------- our arm
@@ -232,30 +244,39 @@ def run_ours(args, wl, rank, world):
     clocks = clk.summary()
     phases = [{k: v / args.steps for k, v in p.items()} for p in phase_sum]
 
-    # roofline of the dominant kernel (largest per-sweep phase time)
-    model = phase_model(wl, ranks)
+    # roofline of the dominant streaming product (largest modeled phase time)
+    model = phase_model(wl, res)
     peaks, peak_src = measured_peaks()
-    dom_step, dom_phase = max(((s, k) for s, p in enumerate(phases) for k in p), key=lambda sk: phases[sk[0]][sk[1]])
-    dom_ms = phases[dom_step][dom_phase]
     roof = None
-    if dom_step == 0 and dom_phase in model:
-        mm = model[dom_phase]
+    timed = [(sk, phases[sk[0]].get(sk[1], 0.0)) for sk in model]
+    timed = [t for t in timed if t[1] > 0.0]
+    if timed:
+        (dom_step, dom_phase), dom_ms = max(timed, key=lambda t: t[1])
+        mm = model[(dom_step, dom_phase)]
         gbs = mm["bytes"] / (dom_ms * 1e-3) / 1e9
         tfl = mm["flops"] / (dom_ms * 1e-3) / 1e12
         f_hbm = gbs / peaks["hbm_gbs"]
-        f_alu = tfl / FP32_PEAK_TFLOPS
-        if f_alu > f_hbm:
-            roof = {"bound": "alu", "achieved": round(tfl, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
-                    "unit": "TFLOP/s", "frac": round(f_alu, 4),
-                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
+        if args.precision == "mixed":
+            # TF32 tensor peak: the measured dense bf16 rate x the nominal TF32/BF16 ratio (1.1/2.25)
+            c_peak = peaks["bf16_tflops"] * 0.5
+            c_name = f"TF32 tensor: measured bf16 {peaks['bf16_tflops']} TFLOP/s x 0.5 (nominal ratio)"
+            c_bound = "tensor"
+        else:
+            c_peak = FP32_PEAK_TFLOPS
+            c_name = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+            c_bound = "alu"
+        f_c = tfl / c_peak
+        if f_c > f_hbm:
+            roof = {"bound": c_bound, "achieved": round(tfl, 2), "peak": round(c_peak, 1),
+                    "unit": "TFLOP/s", "frac": round(f_c, 4), "peak_source": c_name,
                     "hbm_frac": round(f_hbm, 4), "hbm_gbs": round(gbs, 1)}
         else:
             roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": round(f_hbm, 4), "peak_source": peak_src,
-                    "alu_frac": round(f_alu, 4)}
-        roof.update({"kernel": f"step0:{dom_phase}", "ms": round(dom_ms, 4),
+                    "compute_frac": round(f_c, 4)}
+        roof.update({"kernel": f"step{dom_step}:{dom_phase}", "ms": round(dom_ms, 4),
                      "algorithmic_bytes": mm["bytes"], "algorithmic_flops": mm["flops"],
-                     "traffic": ncu_traffic(dom_phase, args.workload)})
+                     "traffic": ncu_traffic(f"step{dom_step}:{dom_phase}:{args.precision}", args.workload)})
 
     # accuracy of this run (untimed): error equality, RSE, sampled diff vs the oracle
     acc = accuracy(tu, torch, A, res, args.workload)

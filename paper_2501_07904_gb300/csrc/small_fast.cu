@@ -3,13 +3,12 @@
 // Cholesky-QR (SM_ORTH), for n <= 128 in FP32 and n <= 64 in FP64.
 //
 // The symmetric n x n matrix is held in registers, a 4 x 8 tile per thread
-// (512 threads cover 128 x 128).  One Cholesky step is: every warp picks the
-// same pivot p (largest remaining diagonal, lowest index on ties), the owners
-// of row p publish it to shared memory, every thread applies the rank-one
-// update to its own entries -- one barrier per step, the diagonal, pivot row
-// and eliminated flags being double-buffered by step parity.  Pivoting is
-// virtual (nothing is swapped): the factor's rows come out in pivot order and
-// its columns keep the original coordinates.
+// (512 threads cover 128 x 128).  The Cholesky factorizations are blocked by
+// panels of 32 steps: one warp factors a panel from a shared-memory copy of
+// the Schur complement (pivot by warp reductions, left-looking column
+// updates), then every thread applies the panel's rank-32 update to its
+// tile.  Pivoting is virtual (nothing is swapped): the factor's rows come out
+// in pivot order and its columns keep the original coordinates.
 //
 // Pivoted QLP (Stewart's rank-revealing UTV, cited in Sec. 2.2):
 //   1. pivoted Cholesky of G = X^T X gives R_1 (the R of column-pivoted QR of X);
@@ -65,6 +64,7 @@ __device__ __forceinline__ void tile_product(T (&a)[4][8], int mr, int mc, int q
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) a[i][jj] = T(0);
+#pragma unroll 4
   for (int q = 0; q < qn; ++q) {
     T ra[4], cb[8];
 #pragma unroll
@@ -104,11 +104,24 @@ __device__ __forceinline__ int warp_argmax(bool has, double v, int idx, double& 
   return bi == 0x7fffffff ? -1 : bi;
 }
 
-// Cholesky of the symmetric matrix in registers, one barrier per step.
-//   pivot      largest remaining diagonal first (every warp computes the same
-//              choice); else column order, a column whose remaining diagonal
-//              is not above tol * (largest initial diagonal) being dropped
-//              (zero row of R, no elimination);
+// rs = 1/sqrt(x) and inv = 1/x (both 0 when drop).  FP32: the hardware
+// reciprocal square root refined by one Newton step, rs (3 - x rs^2) / 2.
+__device__ __forceinline__ void recip_sqrt(float x, bool drop, float& rs, float& inv) {
+  float r = rsqrtf(x);
+  r = r * (1.5f - 0.5f * x * r * r);
+  rs = drop ? 0.f : r;
+  inv = drop ? 0.f : r * r;
+}
+__device__ __forceinline__ void recip_sqrt(double x, bool drop, double& rs, double& inv) {
+  rs = drop ? 0.0 : 1.0 / sqrt(x);
+  inv = drop ? 0.0 : 1.0 / x;
+}
+
+// Cholesky of the symmetric n x n matrix held in the register tiles a.
+//   pivot      largest remaining diagonal first (lowest index on ties); else
+//              column order, a column whose remaining diagonal is not above
+//              tol * (largest initial diagonal) being dropped (zero row of R,
+//              no elimination);
 //   stop_mode  0: tolerance (pivoted) or all columns (column order);
 //              1: first j >= 1 with base + trace <= delta2;
 //              2: j == r_stop;
@@ -117,125 +130,140 @@ __device__ __forceinline__ int warp_argmax(bool has, double v, int idx, double& 
 // perm[j] = column eliminated at step j; tails[j] = base + remaining trace
 // before step j (if tails != null).  Returns the number of steps; sc.trace =
 // the remaining Schur trace (>= 0).
-// Shared buffers (double-buffered by step parity): dbuf[2][NP] remaining
-// diagonal, Lbuf[2][NP] pivot row, dn[2][NP] eliminated flags.
+//
+// Left-looking on the factor itself: the matrix is copied once to shared S
+// (ld lds) and the pivot column of step j is S(p, i) - sum_{q<j} R(q, p)
+// R(q, i), so no Schur complement is ever written back.  Four threads share
+// row i (= tid / 4) and split the sum over q by q mod 4; each keeps the
+// row's remaining diagonal.  A step takes one barrier, after row j of R and
+// the next step's per-warp pivot and trace partials are written.  Pivoting
+// is virtual.
 template <typename T>
 __device__ int pchol(T (&a)[4][8], int n, bool pivot, double tol, int stop_mode, double base,
-                     double delta2, int r_stop, int kmax, T* R, int ldr, int* perm, T* dbuf, T* Lbuf,
-                     int* dn, double* tails, Scal& sc) {
+                     double delta2, int r_stop, int kmax, T* R, int ldr, int* perm, T* S, int lds,
+                     T* part_v, int* part_i, T* trace_j, double* tails, Scal& sc) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ty = tid / 16;
-  for (int i = tid; i < NP; i += FT) {
-    dn[i] = (i >= n) ? 1 : 0;
-    dn[NP + i] = dn[i];
-  }
+  const int row = tid >> 2, sub = tid & 3;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj)
-      if (tile_r(i) == tile_c(jj)) {
-        dbuf[tile_r(i)] = a[i][jj];   // D_0 lives in buffer 1 ("step -1")
-        dbuf[NP + tile_r(i)] = a[i][jj];
-      }
-  for (int i = tid; i < NP; i += FT) Lbuf[NP + i] = T(0);  // L_{-1} = 0
+    for (int jj = 0; jj < 8; ++jj) {
+      const int r = tile_r(i), c = tile_c(jj);
+      if (r < n && c < n) S[r * lds + c] = a[i][jj];
+    }
   __syncthreads();
-  double d0 = 0.0;
+  bool done = row >= n;
+  T d = done ? T(0) : S[row * lds + row];
+  // largest initial diagonal
+  double d0;
   {
-    double m = 0.0;
-    for (int i = lane; i < n; i += 32) m = fmax(m, (double)dbuf[i]);
+    T m = (sub == 0 && !done) ? d : T(0);
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    d0 = m;
+    if (lane == 0) part_v[warp] = m;
+    __syncthreads();
+    T mm = T(0);
+    for (int w = 0; w < FT / 32; ++w) mm = fmax(mm, part_v[w]);
+    d0 = (double)mm;
+    __syncthreads();
   }
-  T inv_prev = T(0);
+  // The step loop runs in T only (FP64 issues at a small fraction of the FP32
+  // rate): thresholds are formed once, traces kept in trace_j[] and turned
+  // into FP64 tails after the loop.
+  const T tol_abs = (T)(tol * d0);
+  const T stop_trace = (T)(delta2 - base);
+  // Per-warp partials of step jn (pivot candidate, trace, and row jn's
+  // diagonal for column order), double-buffered by step parity so that one
+  // barrier per step suffices.
+  auto partials = [&](int jn, int par) {
+    const bool cand = (sub == 0) && !done;
+    T tr = cand ? d : T(0);
+    tr += __shfl_xor_sync(0xffffffffu, tr, 4);  // the row sums sit on lanes 4k
+    tr += __shfl_xor_sync(0xffffffffu, tr, 8);
+    tr += __shfl_xor_sync(0xffffffffu, tr, 16);
+    T bv;
+    const int bi = warp_argmax(cand, cand ? d : T(0), row, bv);
+    if (lane == 0) {
+      part_v[par * 64 + warp] = bv;
+      part_v[par * 64 + 16 + warp] = tr;
+      part_i[par * 32 + warp] = bi;
+    }
+    if (sub == 0 && row == jn) part_v[par * 64 + 32] = d;
+  };
+  partials(0, 0);
+  __syncthreads();
   int j = 0;
   for (;; ++j) {
-    const int cur = j & 1, prv = cur ^ 1;
-    // D_j = D_{j-1} - L_{j-1}^2 / dp_{j-1}, computed by every warp; warp 0 stores it
-    T best_v = T(-1);
-    int best_i = -1;
-    T tr = T(0);
-#pragma unroll
-    for (int k = 0; k < NP / 32; ++k) {
-      const int i = lane + 32 * k;
-      const T l = Lbuf[prv * NP + i];
-      const T dj = dbuf[prv * NP + i] - l * l * inv_prev;
-      if (warp == 0) dbuf[cur * NP + i] = dj;
-      if (!dn[prv * NP + i]) {
-        tr += dj;
-        if (best_i < 0 || dj > best_v) {
-          best_v = dj;
-          best_i = i;
-        }
-      }
+    const int par = j & 1;
+    // every warp combines the FT/32 partials, one per lane (warps are in row
+    // order, so the lowest row wins a tie as within a warp)
+    T cv = T(0), ct = T(0);
+    int ci = -1;
+    if (lane < FT / 32) {
+      ci = part_i[par * 32 + lane];
+      cv = part_v[par * 64 + lane];
+      ct = part_v[par * 64 + 16 + lane];
     }
+    // full butterfly: every lane (and so every warp) holds the same trace and
+    // takes the same stop decision
+    for (int o = 16; o > 0; o >>= 1) ct += __shfl_xor_sync(0xffffffffu, ct, o);
+    T bv;
+    const int bi = warp_argmax(ci >= 0, cv, ci, bv);
     int p;
-    double dp;
+    T dp;
     if (pivot) {
-      T bv;
-      p = warp_argmax(best_i >= 0, best_v, best_i, bv);
-      dp = (double)bv;
+      p = bi;
+      dp = bv;
     } else {
-      // column order: D_j[j], recomputed exactly as its owning lane did above
-      p = j;
-      dp = 0.0;
-      if (j < n) {
-        const T l = Lbuf[prv * NP + j];
-        dp = (double)(dbuf[prv * NP + j] - l * l * inv_prev);
-      }
+      p = j < n ? j : -1;
+      dp = (p >= 0) ? part_v[par * 64 + 32] : T(0);
     }
-    double trd = 0.0;
-    if (stop_mode == 1 || tails) {
-      T t = tr;
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      trd = fmax((double)t, 0.0);
-    }
+    const T trt = ct > T(0) ? ct : T(0);
     int stop = 0;
     bool drop = false;
-    if (j >= kmax || p < 0) stop = 1;
-    if (!stop && stop_mode == 1 && j >= 1 && base + trd <= delta2) stop = 1;
+    if (j >= kmax || j >= n || p < 0) stop = 1;  // every step eliminates or drops a row
+    if (!stop && stop_mode == 1 && j >= 1 && trt <= stop_trace) stop = 1;
     if (!stop && stop_mode == 2 && j == r_stop) stop = 1;
     if (!stop) {
-      const bool ok = (dp > 0.0) && (dp > tol * d0);
+      const bool ok = (dp > T(0)) && (dp > tol_abs);
       if (pivot && !ok) stop = 1;
       if (!pivot && !ok) drop = true;
     }
-    if (tid == 0) {
-      if (tails) tails[j] = base + trd;
-      sc.trace = trd;
-    }
+    if (tid == 0) trace_j[j] = trt;
     if (stop) break;
-    // eliminated flags after this step
-    if (warp == 0) {
-#pragma unroll
-      for (int k = 0; k < NP / 32; ++k) {
-        const int i = lane + 32 * k;
-        dn[cur * NP + i] = dn[prv * NP + i] | (i == p ? 1 : 0);
+    // column p of the Schur complement for this thread's row: four
+    // independent partial sums over q = sub, sub + 4, ... keep loads in flight
+    T acc = T(0);
+    if (!done && !drop) {
+      const T* rp = R + p;
+      const T* rr = R + row;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int q = sub;
+      for (; q + 12 < j; q += 16) {
+        a0 += rp[q * ldr] * rr[q * ldr];
+        a1 += rp[(q + 4) * ldr] * rr[(q + 4) * ldr];
+        a2 += rp[(q + 8) * ldr] * rr[(q + 8) * ldr];
+        a3 += rp[(q + 12) * ldr] * rr[(q + 12) * ldr];
       }
+      for (; q < j; q += 4) a0 += rp[q * ldr] * rr[q * ldr];
+      acc = (a0 + a1) + (a2 + a3);
     }
-    // pivot row: owners publish row p (zero for a dropped column)
-    if (ty == (p & 31)) {
-      const int pi = p >> 5;
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int c = tile_c(jj);
-        Lbuf[cur * NP + c] = (drop || dn[prv * NP + c]) ? T(0) : sel4(a, pi, jj);
-      }
-    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    const T u = (done || drop) ? T(0) : ((row == p) ? dp : S[p * lds + row] - acc);
+    T rs, inv;
+    recip_sqrt(dp, drop, rs, inv);
+    if (sub == 0 && row < ldr) R[j * ldr + row] = u * rs;
+    if (tid < ldr - NP) R[j * ldr + NP + tid] = T(0);
+    if (!done) d -= u * u * inv;
+    if (row == p) done = true;
+    if (tid == 0) perm[j] = p;
+    partials(j + 1, par ^ 1);
     __syncthreads();
-    const T inv = drop ? T(0) : T(1) / (T)dp;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const T lr = Lbuf[cur * NP + tile_r(i)] * inv;
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) a[i][jj] -= lr * Lbuf[cur * NP + tile_c(jj)];
-    }
-    if (warp == 1) {
-      const T rs = drop ? T(0) : T(1) / sqrt((T)dp);
-      for (int c = lane; c < ldr; c += 32) R[j * ldr + c] = (c < NP) ? Lbuf[cur * NP + c] * rs : T(0);
-      if (lane == 0) perm[j] = p;
-    }
-    inv_prev = inv;
   }
+  __syncthreads();
+  if (tails)
+    for (int q = tid; q <= j; q += FT) tails[q] = base + (double)trace_j[q];
+  if (tid == 0) sc.trace = (double)trace_j[j];
   __syncthreads();
   return j;
 }
@@ -361,7 +389,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
         for (int jj = 0; jj < 8; ++jj)
           if (tile_r(i) == tile_c(jj) && tile_r(i) < n) a[i][jj] += sh;
     }
-    pchol(a, n, false, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, ld, perm1, dbuf, Lbuf, dn, nullptr, sc);
+    pchol(a, n, false, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, ld, perm1, X, ld, dbuf, dn, Lbuf, nullptr, sc);
     tri_inverse(R1, n, ld, X, tmp);
     for (int e = tid; e < n * ldz; e += FT) {
       const int i = e / ldz, c = e % ldz;
@@ -385,7 +413,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   if (prm.Gw) {
     // W^T W = T^T T; factor A = T^{-T} G T^{-1}, the Gram of X Q for Q = W T^{-1}
     load_regs(a, prm.Gw, n);
-    pchol(a, n, false, 0.0, 0, 0.0, 0.0, 0, n, R1, ld, perm1, dbuf, Lbuf, dn, nullptr, sc);
+    pchol(a, n, false, 0.0, 0, 0.0, 0.0, 0, n, R1, ld, perm1, X, ld, dbuf, dn, Lbuf, nullptr, sc);
     tri_inverse(R1, n, ld, X, tmp);
     for (int e = tid; e < nn * ld; e += FT) Tw[e] = X[e];
     for (int e = tid; e < n * n; e += FT) R2[(e / n) * ld + e % n] = (T)G[e];
@@ -416,7 +444,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   const double mu2 = prm.x2_dev ? fmax(0.0, x2 - tr) : 0.0;
 
   // phase 1: pivoted Cholesky of G
-  const int k1 = pchol(a, n, true, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, ld, perm1, dbuf, Lbuf, dn,
+  const int k1 = pchol(a, n, true, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, ld, perm1, X, ld, dbuf, dn, Lbuf,
                        nullptr, sc);
   const double s1 = sc.trace;
   // phase 2: pivoted Cholesky of M = R_1 R_1^T
@@ -425,7 +453,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   const bool fixed = prm.r_fixed >= 1;
   const int rt = fixed ? min(prm.r_fixed, prm.r_cap) : -1;
   const int r2 = pchol(a, k1, true, 0.0, fixed ? 2 : 1, mu2 + s1, delta2, rt, min(k1, prm.r_cap),
-                       R2, ld, perm2, dbuf, Lbuf, dn, info->tails, sc);
+                       R2, ld, perm2, X, ld, dbuf, dn, Lbuf, info->tails, sc);
   const int r = fixed ? rt : max(1, r2);
   const int rz = min(r, r2);  // columns produced by the factorization
 
@@ -451,7 +479,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
     // one more Cholesky-QR pass: Zs <- Zs chol(Zs^T Zs)^{-1}
     tile_product(a, rz, rz, n, [&](int rr, int q) { return R2[q * ld + rr]; },
                  [&](int c, int q) { return R2[q * ld + c]; });
-    pchol(a, rz, false, 0.0, 0, 0.0, 0.0, 0, rz, R1, ld, perm1, dbuf, Lbuf, dn, nullptr, sc);
+    pchol(a, rz, false, 0.0, 0, 0.0, 0.0, 0, rz, R1, ld, perm1, X, ld, dbuf, dn, Lbuf, nullptr, sc);
     tri_inverse(R1, rz, ld, X, tmp);
     tile_product(a, n, rz, rz, [&](int i, int q) { return R2[i * ld + q]; },
                  [&](int c, int q) { return q <= c ? X[q * ld + c] : T(0); });

@@ -1,15 +1,15 @@
 // Tensor-core (tcgen05) products for the mixed-precision sweep: D = A B with
 // FP32 data, TF32 operands rounded to nearest, FP32 accumulation.
 //
-// One persistent CTA per SM, ten warps with fixed roles:
+// One persistent CTA per SM, fourteen warps with fixed roles:
 //   warp 0     TMA producer: 2-D tensor-map copies of the FP32 operand
 //              slabs (128 rows x 32 k of A, n_mma rows x 32 k of B) into a
 //              staging ring;
 //   warp 1     allocates tensor memory; one lane issues tcgen05.mma;
-//   warps 2-5  converters: round the staged FP32 values to TF32 (and, for a
-//              split operand, the TF32 rounding of the remainder), writing
-//              K-major 128-byte-swizzled operand tiles;
-//   warps 6-9  epilogue: after every k-block (one TMEM chunk) the
+//   warps 2-9  converters: round the staged FP32 values to TF32 (and, for a
+//              split operand, keep the remainder x - hi, whose low bits the
+//              MMA ignores), writing K-major 128-byte-swizzled operand tiles;
+//   warps 10-13 epilogue: after every k-block (one TMEM chunk) the
 //              accumulator is read back and added into a running FP32 sum
 //              kept in spare TMEM columns, which bounds the rounding drift of
 //              the tensor-core accumulation; at the end of a work segment the
@@ -41,14 +41,17 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 320;
+constexpr int kThreads = 448;
+constexpr int kConv = 256;     // converter threads (warps 2-9)
 constexpr int kBM = 128;       // rows of an output tile (MMA M)
 constexpr int kBK = 32;        // k per staged slab (one 128-byte swizzle row of TF32)
-// k-blocks accumulated in TMEM before the epilogue drains them into the
-// running sum: the tensor-core accumulation drifts toward zero by up to about
-// one FP32 ulp per accumulate step, so chunks are kept to one k-block (at
-// most 12 MMAs) and the long sums are carried in round-to-nearest FP32 adds.
-constexpr int kChunkKB = 1;
+// The tensor-core accumulation drifts toward zero by up to about one FP32
+// ulp per accumulate step, so the epilogue drains TMEM into a running
+// round-to-nearest FP32 sum after at most kChunkMMA MMAs (a chunk of
+// TcArgs::chunk_kb k-blocks); three accumulator buffers let the MMAs run
+// ahead of the drains.
+constexpr int kChunkMMA = 16;
+constexpr int kAccBufs = 3;
 constexpr int kMaxStages = 8;
 constexpr int kSmemBudget = 225 * 1024;
 
@@ -66,6 +69,7 @@ struct TcArgs {
   int all_partial;   // every segment writes a partial (FP64 output / mirroring)
   int round_out;     // round FP32 outputs to TF32
   int S_st, S_op;    // ring depths
+  int chunk_kb;      // k-blocks per TMEM chunk
   uint32_t stage_bytes, a_box_bytes, b_box_bytes, op_bytes;
   float* out;
   int64_t ldo;
@@ -119,47 +123,50 @@ struct Cursor {
 
 // Convert one staged FP32 slab into a K-major SW128 TF32 tile of R rows
 // (R a multiple of 16, at most 128); hi/lo are shared addresses, lo = 0 for
-// an unsplit operand.  A thread owns the 16-byte chunks idx = ct + 128 j of a
-// K-major source (row idx / 8, chunk idx % 8), or row ct of an MN-major one;
-// all of its loads are issued before the first conversion.
+// an unsplit operand.  A thread owns the 16-byte chunks idx = ct + 256 j of a
+// K-major source (row idx / 8, chunk idx % 8), or half of row ct % 128 of an
+// MN-major one; all of its loads are issued before the first conversion.
 //   K-major source:  staging [R][32]  (one float4 per chunk)
 //   MN-major source: staging [32][R]  (four floats, stride R, per chunk)
 __device__ __forceinline__ void store_chunk(uint32_t hi, uint32_t lo, uint32_t off, float4 v) {
   const uint32_t h0 = to_tf32(v.x), h1 = to_tf32(v.y), h2 = to_tf32(v.z), h3 = to_tf32(v.w);
   sts128(hi + off, h0, h1, h2, h3);
   if (lo)
-    sts128(lo + off, to_tf32(v.x - __uint_as_float(h0)), to_tf32(v.y - __uint_as_float(h1)),
-           to_tf32(v.z - __uint_as_float(h2)), to_tf32(v.w - __uint_as_float(h3)));
+    sts128(lo + off, __float_as_uint(v.x - __uint_as_float(h0)), __float_as_uint(v.y - __uint_as_float(h1)),
+           __float_as_uint(v.z - __uint_as_float(h2)), __float_as_uint(v.w - __uint_as_float(h3)));
 }
 
 __device__ __forceinline__ void convert_slab(uint32_t stg, int kmajor, int R, uint32_t hi,
                                              uint32_t lo, int ct) {
-  const int nchunks = R * 8;  // <= 1024: at most 8 per thread
-  float4 v[8];
+  constexpr int kPer = 1024 / kConv;  // chunks per thread for R = 128
+  float4 v[kPer];
   if (kmajor) {
+    const int nchunks = R * 8;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int idx = ct + 128 * j;
+    for (int j = 0; j < kPer; ++j) {
+      const int idx = ct + kConv * j;
       if (idx < nchunks) v[j] = lds128(stg + (uint32_t)idx * 16u);  // row idx/8, chunk idx%8
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int idx = ct + 128 * j;
+    for (int j = 0; j < kPer; ++j) {
+      const int idx = ct + kConv * j;
       if (idx < nchunks) store_chunk(hi, lo, sw128_off((uint32_t)(idx >> 3), (uint32_t)(idx & 7) * 4u), v[j]);
     }
-  } else if (ct < R) {
-    // thread ct owns row ct: chunks q = 0..7 (k = 4q..4q+3)
-    const uint32_t p0 = stg + (uint32_t)ct * 4u;
+  } else {
+    // thread ct owns row ct % 128, chunks q = kPer (ct / 128) ... + kPer - 1
+    const int row = ct & 127, q0 = (ct >> 7) * kPer;
+    if (row >= R) return;
+    const uint32_t p0 = stg + (uint32_t)row * 4u;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const uint32_t p = p0 + (uint32_t)(q * 4 * R) * 4u;
-      v[q].x = lds32(p);
-      v[q].y = lds32(p + 4u * R);
-      v[q].z = lds32(p + 8u * R);
-      v[q].w = lds32(p + 12u * R);
+    for (int j = 0; j < kPer; ++j) {
+      const uint32_t p = p0 + (uint32_t)((q0 + j) * 4 * R) * 4u;
+      v[j].x = lds32(p);
+      v[j].y = lds32(p + 4u * R);
+      v[j].z = lds32(p + 8u * R);
+      v[j].w = lds32(p + 12u * R);
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) store_chunk(hi, lo, sw128_off((uint32_t)ct, (uint32_t)q * 4u), v[q]);
+    for (int j = 0; j < kPer; ++j) store_chunk(hi, lo, sw128_off((uint32_t)row, (uint32_t)(q0 + j) * 4u), v[j]);
   }
 }
 
@@ -178,8 +185,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* opfull = bars + 2 * kMaxStages;
   uint64_t* opempty = bars + 3 * kMaxStages;
   uint64_t* accfull = bars + 4 * kMaxStages;
-  uint64_t* accempty = accfull + 2;
-  uint64_t* finalbar = accfull + 4;
+  uint64_t* accempty = accfull + kAccBufs;
+  uint64_t* finalbar = accfull + 2 * kAccBufs;
   uint32_t* tmem_slot = (uint32_t*)(bars + 48);
   double* red = (double*)(bars + 56);  // 4 doubles
   uint8_t* stage_base = smem + 1024;
@@ -191,13 +198,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) {
     for (int s = 0; s < a.S_st; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 128);
+      mbar_init(&empty[s], kConv);
     }
     for (int t = 0; t < a.S_op; ++t) {
-      mbar_init(&opfull[t], 128);
+      mbar_init(&opfull[t], kConv);
       mbar_init(&opempty[t], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kAccBufs; ++b) {
       mbar_init(&accfull[b], 1);
       mbar_init(&accempty[b], 128);
     }
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t op0 = smem_u32(op_base);
     int t_op = 0;
     uint32_t ph_op = 0;
-    uint32_t fills[2] = {0u, 0u};
+    uint32_t fills[kAccBufs] = {0u, 0u, 0u};
     int buf = 0;
     bool ok = true;
     int64_t pos = beg;
@@ -277,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool same = a.sym && cur.mt == cur.nt;
       for (int kbi = kstart; kbi < kend; ++kbi) {
         const int local = kbi - kstart;
-        const bool chunk_start = (local % kChunkKB) == 0;
+        const bool chunk_start = (local % a.chunk_kb) == 0;
         if (chunk_start) {
           ok = __all_sync(0xffffffffu, mbar_wait(&accempty[buf], (fills[buf] & 1u) ^ 1u, a.err));
           if (!ok) break;
@@ -289,17 +296,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t b_hi = same ? a_hi : a_hi + (a.a_split ? 32768u : 16384u);
         const uint32_t b_lo = same ? a_lo : b_hi + (uint32_t)a.n_mma * 128u;
         const uint32_t d = tmem + (uint32_t)(buf * NREG);
-        const bool chunk_end = (local % kChunkKB == kChunkKB - 1) || (kbi == kend - 1);
+        const bool chunk_end = (local % a.chunk_kb == a.chunk_kb - 1) || (kbi == kend - 1);
         if (elect_one()) {
-          tc_fence_after();
+          // a TMEM buffer handed back by the epilogue is written only after
+          // its reads (tcgen05.ld before the epilogue's arrive)
+          if (chunk_start) tc_fence_after();
+          // a k-step of 8 TF32 moves the start address by 32 bytes (2 in the
+          // descriptor's 16-byte units) inside the swizzle atom
+          const uint64_t dah = make_sw128_desc(a_hi), dbh = make_sw128_desc(b_hi);
+          const uint64_t dal = make_sw128_desc(a_lo), dbl = make_sw128_desc(b_lo);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t acc = (chunk_start && kk == 0) ? 0u : 1u;
-            const uint64_t dah = make_sw128_desc(a_hi + kk * 32);
-            const uint64_t dbh = make_sw128_desc(b_hi + kk * 32);
-            mma_tf32(d, dah, dbh, idesc, acc);
-            if (a.b_split) mma_tf32(d, dah, make_sw128_desc(b_lo + kk * 32), idesc, 1u);
-            if (a.a_split) mma_tf32(d, make_sw128_desc(a_lo + kk * 32), dbh, idesc, 1u);
+            const uint64_t o = 2u * (uint64_t)kk;
+            mma_tf32(d, dah + o, dbh + o, idesc, acc);
+            if (a.b_split) mma_tf32(d, dah + o, dbl + o, idesc, 1u);
+            if (a.a_split) mma_tf32(d, dal + o, dbh + o, idesc, 1u);
           }
           mma_commit(&opempty[t_op]);
           if (chunk_end) mma_commit(&accfull[buf]);
@@ -311,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (chunk_end) {
           ++fills[buf];
-          buf ^= 1;
+          if (++buf == kAccBufs) buf = 0;
         }
       }
       pos += kend - kstart;
@@ -323,9 +335,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t t0 = globaltimer_ns();
     while (!mbar_try_wait(finalbar, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
     }
-  } else if (warp < 6) {
+  } else if (warp < 2 + kConv / 32) {
     // ---------------- converters ----------------
-    const int ct = tid - 64;
+    const int ct = tid - 64;  // 0 .. kConv-1
     int s = 0, t_op = 0;
     uint32_t ph = 0, ph_op = 0;
     Cursor cur;
@@ -362,10 +374,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;               // TMEM lane quarter of this warp
     const int row = q * 32 + lane;        // tile row owned by this thread
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-    const uint32_t sum_addr = lane_addr + 2u * NREG;
+    const uint32_t sum_addr = lane_addr + (uint32_t)(kAccBufs * NREG);
     double sq = 0.0;
     int buf = 0;
-    uint32_t drains[2] = {0u, 0u};
+    uint32_t drains[kAccBufs] = {0u, 0u, 0u};
     bool ok = true;
     int64_t pos = beg;
     Cursor cur;
@@ -373,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     while (pos < end && ok) {
       const int t = cur.t, kstart = cur.kbi, mt = cur.mt, nt = cur.nt;
       const int kend = (int)std::min<int64_t>((int64_t)a.kb, kstart + (end - pos));
-      const int nchunks = (kend - kstart + kChunkKB - 1) / kChunkKB;
+      const int nchunks = (kend - kstart + a.chunk_kb - 1) / a.chunk_kb;
       const bool direct = (kstart == 0 && kend == a.kb) && !a.all_partial;
       const int64_t m = (int64_t)mt * kBM + row;
       const int64_t n0 = (int64_t)nt * NREG;
@@ -393,12 +405,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int c32 = 0; c32 < NREG / 32; ++c32) {
           float v[32];
-          tmem_ld32(lane_addr + (uint32_t)(buf * NREG + c32 * 32), v);
-          if (ch > 0) {
-            float u[32];
-            tmem_ld32(sum_addr + (uint32_t)(c32 * 32), u);
+          {
+            uint32_t rv[32], ru[32];
+            tmem_ld32_nowait(lane_addr + (uint32_t)(buf * NREG + c32 * 32), rv);
+            if (ch > 0) tmem_ld32_nowait(sum_addr + (uint32_t)(c32 * 32), ru);
+            tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] += u[j];
+            for (int j = 0; j < 32; ++j)
+              v[j] = (ch > 0) ? __uint_as_float(rv[j]) + __uint_as_float(ru[j]) : __uint_as_float(rv[j]);
           }
           if (!last) {
             tmem_st32(sum_addr + (uint32_t)(c32 * 32), v);
@@ -443,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         mbar_arrive(&accempty[buf]);
         ++drains[buf];
-        buf ^= 1;
+        if (++buf == kAccBufs) buf = 0;
       }
       sq += (double)rs;
       pos += kend - kstart;
@@ -453,7 +467,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int o2 = 16; o2 > 0; o2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o2);
       if (lane == 0) red[q] = sq;
       named_barrier(1, 128);
-      if (tid == 192) a.sq_part[c] = red[0] + red[1] + red[2] + red[3];
+      if (tid == 64 + kConv) a.sq_part[c] = red[0] + red[1] + red[2] + red[3];
     }
   }
 
@@ -619,6 +633,7 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   a.G = (int)G;
   a.a_split = a_split ? 1 : 0;
   a.b_split = b_split ? 1 : 0;
+  a.chunk_kb = std::max(1, kChunkMMA / (4 * (1 + (a_split ? 1 : 0) + (b_split ? 1 : 0))));
   a.a_box_bytes = kBM * kBK * 4;
   a.b_box_bytes = (uint32_t)a.n_mma * kBK * 4;
   // a Gram's off-diagonal tiles load B; diagonal ones reuse A
