@@ -268,6 +268,120 @@ __device__ int pchol(T (&a)[4][8], int n, bool pivot, double tol, int stop_mode,
   return j;
 }
 
+// Column-order Cholesky (no pivoting, stop_mode 0, kmax = n) of the
+// symmetric n x n matrix in the register tiles a, blocked right-looking by
+// 32 columns in shared S (ld lds, lower triangle overwritten by L):
+//   1. warp 0 factors the 32 x 32 diagonal block (one row per lane, __syncwarp
+//      between columns); a column whose remaining diagonal is not above
+//      tol * (largest initial diagonal) is dropped (zero column of L);
+//   2. one thread per row below solves its panel row against that block;
+//   3. every thread applies the rank-32 update to 4 x 4 blocks of the
+//      trailing lower triangle.
+// Three barriers per block of 32 columns.  R = L^T (ld ldr) and perm[j] = j
+// as pchol() gives them for this mode; returns n.  rsb: 32 scratch entries.
+template <typename T>
+__device__ int chol_blocked(const T (&a)[4][8], int n, double tol, T* R, int ldr, int* perm, T* S,
+                            int lds, T* rsb, Scal& sc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      const int r = tile_r(i), c = tile_c(jj);
+      if (r < n && c < n) S[r * lds + c] = a[i][jj];
+    }
+  __syncthreads();
+  T tol_abs;
+  {
+    T m = T(0);
+    for (int i = lane; i < n; i += 32) m = fmax(m, S[i * lds + i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    tol_abs = (T)(tol * (double)m);
+  }
+  for (int kb = 0; kb < n; kb += 32) {
+    const int nb = min(32, n - kb);
+    // 1. diagonal block
+    if (warp == 0) {
+      for (int k = 0; k < nb; ++k) {
+        const T piv = S[(kb + k) * lds + kb + k];
+        const bool drop = !(piv > tol_abs);
+        T rs, inv;
+        recip_sqrt(piv, drop, rs, inv);
+        if (lane == k) {
+          S[(kb + k) * lds + kb + k] = drop ? T(0) : piv * rs;
+          rsb[k] = rs;
+        }
+        T lik = T(0);
+        if (lane > k && lane < nb) {
+          lik = S[(kb + lane) * lds + kb + k] * rs;
+          S[(kb + lane) * lds + kb + k] = lik;
+        }
+        __syncwarp();
+        if (lane > k && lane < nb)
+          for (int jx = k + 1; jx <= lane; ++jx)
+            S[(kb + lane) * lds + kb + jx] -= lik * S[(kb + jx) * lds + kb + k];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // 2. panel rows below the block: L(r, kb+c) = (S(r, kb+c) - sum_{c'<c} L(r, kb+c') L(kb+c, kb+c')) / L(kb+c, kb+c)
+    const int r0 = kb + nb;
+    if (tid < n - r0) {
+      const int r = r0 + tid;
+      T* Sr = S + r * lds + kb;
+      for (int c = 0; c < nb; ++c) {
+        T x = Sr[c];
+        const T* Lc = S + (kb + c) * lds + kb;
+        for (int cp = 0; cp < c; ++cp) x -= Sr[cp] * Lc[cp];
+        Sr[c] = x * rsb[c];
+      }
+    }
+    __syncthreads();
+    // 3. trailing update of the lower triangle, 4 x 4 blocks per thread
+    const int m2 = n - r0;
+    if (m2 > 0) {
+      const int nt = (m2 + 3) / 4;
+      for (int blk = tid; blk < nt * nt; blk += FT) {
+        const int bi = blk / nt, bj = blk % nt;
+        if (bj > bi) continue;
+        T acc[4][4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+        const int i0 = r0 + 4 * bi, j0 = r0 + 4 * bj;
+        for (int c = 0; c < nb; ++c) {
+          T li[4], lj[4];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            li[x] = (i0 + x < n) ? S[(i0 + x) * lds + kb + c] : T(0);
+            lj[x] = (j0 + x < n) ? S[(j0 + x) * lds + kb + c] : T(0);
+          }
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] += li[x] * lj[y];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y)
+            if (i0 + x < n && j0 + y <= i0 + x) S[(i0 + x) * lds + j0 + y] -= acc[x][y];
+      }
+    }
+    __syncthreads();
+  }
+  // R = L^T, zero below the diagonal and beyond n
+  for (int e = tid; e < n * ldr; e += FT) {
+    const int j = e / ldr, c = e % ldr;
+    R[e] = (c < n && c >= j) ? S[c * lds + j] : T(0);
+  }
+  for (int j = tid; j < n; j += FT) perm[j] = j;
+  if (tid == 0) sc.trace = 0.0;
+  __syncthreads();
+  return n;
+}
+
 // X = U^{-1} for the upper-triangular m x m U (ld ld); a row/column with
 // U_kk == 0 is treated as dropped (zero in X).  Blocked by 32: one warp per
 // diagonal block (a thread per column), then X_IJ = -X_II sum_K U_IK X_KJ by
@@ -389,7 +503,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
         for (int jj = 0; jj < 8; ++jj)
           if (tile_r(i) == tile_c(jj) && tile_r(i) < n) a[i][jj] += sh;
     }
-    pchol(a, n, false, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, ld, perm1, X, ld, dbuf, dn, Lbuf, nullptr, sc);
+    chol_blocked(a, n, prm.piv_tol, R1, ld, perm1, X, ld, dbuf, sc);
     tri_inverse(R1, n, ld, X, tmp);
     for (int e = tid; e < n * ldz; e += FT) {
       const int i = e / ldz, c = e % ldz;
@@ -413,7 +527,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   if (prm.Gw) {
     // W^T W = T^T T; factor A = T^{-T} G T^{-1}, the Gram of X Q for Q = W T^{-1}
     load_regs(a, prm.Gw, n);
-    pchol(a, n, false, 0.0, 0, 0.0, 0.0, 0, n, R1, ld, perm1, X, ld, dbuf, dn, Lbuf, nullptr, sc);
+    chol_blocked(a, n, 0.0, R1, ld, perm1, X, ld, dbuf, sc);
     tri_inverse(R1, n, ld, X, tmp);
     for (int e = tid; e < nn * ld; e += FT) Tw[e] = X[e];
     for (int e = tid; e < n * n; e += FT) R2[(e / n) * ld + e % n] = (T)G[e];
@@ -479,7 +593,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
     // one more Cholesky-QR pass: Zs <- Zs chol(Zs^T Zs)^{-1}
     tile_product(a, rz, rz, n, [&](int rr, int q) { return R2[q * ld + rr]; },
                  [&](int c, int q) { return R2[q * ld + c]; });
-    pchol(a, rz, false, 0.0, 0, 0.0, 0.0, 0, rz, R1, ld, perm1, X, ld, dbuf, dn, Lbuf, nullptr, sc);
+    chol_blocked(a, rz, 0.0, R1, ld, perm1, X, ld, dbuf, sc);
     tri_inverse(R1, rz, ld, X, tmp);
     tile_product(a, n, rz, rz, [&](int i, int q) { return R2[i * ld + q]; },
                  [&](int c, int q) { return q <= c ? X[q * ld + c] : T(0); });

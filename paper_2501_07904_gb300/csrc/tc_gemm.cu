@@ -478,9 +478,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // Finish tiles covered by more than one CTA (or every tile when all_partial):
-// partials added in CTA order in FP64, mirrored for a Gram.  blockIdx.y
-// selects kFixRows rows of the tile.
-constexpr int kFixRows = 4;
+// the FP32 partials are added in CTA order with compensated (Kahan) FP32
+// sums -- accurate to about one ulp of the result, without FP64 adds, which
+// GB300 issues at a small fraction of the FP32 rate -- and mirrored for a
+// Gram.  blockIdx.y selects kBM / gridDim.y rows of the tile (one row per
+// block for the few tiles of a Gram, more where most blocks find no split
+// tile).
 
 template <int NREG>
 __global__ void tc_fixup_kernel(TcArgs a, double* __restrict__ out64, double* __restrict__ fix_sq) {
@@ -499,7 +502,7 @@ __global__ void tc_fixup_kernel(TcArgs a, double* __restrict__ out64, double* __
       if (pb % a.kb != 0 && seg_beg(a, b - 1) <= (int64_t)tt * a.kb) t = tt;
     }
   }
-  double sq = 0.0;
+  float sqf = 0.f;
   if (t >= 0) {
     int mt, nt;
     tile_coords(t, a.ntm, a.ntn, a.sym, mt, nt);
@@ -507,35 +510,40 @@ __global__ void tc_fixup_kernel(TcArgs a, double* __restrict__ out64, double* __
     const int c_lo = (int)(((p_lo + 1) * a.G - 1) / a.total);
     const int c_hi = (int)(((p_hi + 1) * a.G - 1) / a.total);
     const int64_t m0 = (int64_t)mt * kBM, n0 = (int64_t)nt * NREG;
-    const int i0 = blockIdx.y * kFixRows;
-    for (int e = threadIdx.x; e < kFixRows * NREG; e += blockDim.x) {
+    const int rows = kBM / gridDim.y;
+    const int i0 = blockIdx.y * rows;
+    for (int e = threadIdx.x; e < rows * NREG; e += blockDim.x) {
       const int i = i0 + e / NREG, j = e % NREG;
       const int64_t m = m0 + i, n = n0 + j;
       if (m >= a.M || n >= a.N) continue;
-      double s = 0.0;
+      float sum = 0.f, comp = 0.f;
       for (int cc = c_lo; cc <= c_hi; ++cc) {
         const int slot = (seg_beg(a, cc) / a.kb == t) ? 0 : 1;
-        s += (double)a.part[(((size_t)cc * 2 + slot) * kBM + i) * NREG + j];
+        const float y = a.part[(((size_t)cc * 2 + slot) * kBM + i) * NREG + j] - comp;
+        const float tsum = sum + y;
+        comp = (tsum - sum) - y;
+        sum = tsum;
       }
       const bool mirror = a.sym && mt != nt;
       if (out64) {
+        const double s = (double)sum - (double)comp;
         out64[m * a.N + n] = s;
         if (mirror) out64[n * a.N + m] = s;
       }
       if (a.out) {
-        float v = (float)s;
+        float v = sum - comp;
         if (a.round_out) v = round_tf32(v);
         a.out[m * a.ldo + n] = v;
-        sq += (double)v * (double)v;
+        sqf += v * v;
         if (mirror) {
           a.out[n * a.ldo + m] = v;
-          sq += (double)v * (double)v;
+          sqf += v * v;
         }
       }
     }
   }
   if (fix_sq) {
-    sq = block_sum(sq, red);
+    const double sq = block_sum((double)sqf, red);
     if (threadIdx.x == 0) fix_sq[(size_t)blockIdx.x * gridDim.y + blockIdx.y] = sq;
   }
 }
@@ -652,7 +660,7 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   p.part_bytes = ((size_t)G * 2 * kBM * p.nreg * sizeof(float) + 255) & ~(size_t)255;
   p.sq_bytes = ((size_t)G * sizeof(double) + 255) & ~(size_t)255;
   p.fix_blocks = a.all_partial ? a.ntiles : (int)G;
-  p.fix_bytes = ((size_t)p.fix_blocks * (kBM / kFixRows) * sizeof(double) + 255) & ~(size_t)255;
+  p.fix_bytes = ((size_t)p.fix_blocks * kBM * sizeof(double) + 255) & ~(size_t)255;
   return true;
 }
 
@@ -753,9 +761,10 @@ cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K,
     e = launch<128>(p, ma, mb, d, slot, st);
   if (e != cudaSuccess) return e;
   const bool need_fix = a.all_partial || a.G > 1;
+  const unsigned fg_y = a.all_partial ? kBM : 16;
   if (need_fix) {
     ++nl;
-    const dim3 fg((unsigned)p.fix_blocks, kBM / kFixRows);
+    const dim3 fg((unsigned)p.fix_blocks, fg_y);
     if (p.nreg == 32)
       tc_fixup_kernel<32><<<fg, 256, 0, st>>>(a, out64, sumsq ? fix_sq : nullptr);
     else if (p.nreg == 64)
@@ -768,7 +777,7 @@ cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K,
   if (sumsq) {
     ++nl;
     tc_sumsq_kernel<<<1, 256, 0, st>>>(sq_part, a.G, fix_sq,
-                                       need_fix ? p.fix_blocks * (kBM / kFixRows) : 0, sumsq);
+                                       need_fix ? p.fix_blocks * (int)fg_y : 0, sumsq);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
