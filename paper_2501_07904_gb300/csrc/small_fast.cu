@@ -300,41 +300,64 @@ __device__ int chol_blocked(const T (&a)[4][8], int n, double tol, T* R, int ldr
   }
   for (int kb = 0; kb < n; kb += 32) {
     const int nb = min(32, n - kb);
-    // 1. diagonal block
+    // 1. diagonal block: lane c keeps column c (rows >= c) in registers; at
+    //    step k the scaled column k is read by shuffles, row by row, and
+    //    lane c picks up L(c, k) on the way (rows >= c come after row c)
     if (warp == 0) {
-      for (int k = 0; k < nb; ++k) {
-        const T piv = S[(kb + k) * lds + kb + k];
-        const bool drop = !(piv > tol_abs);
-        T rs, inv;
-        recip_sqrt(piv, drop, rs, inv);
-        if (lane == k) {
-          S[(kb + k) * lds + kb + k] = drop ? T(0) : piv * rs;
-          rsb[k] = rs;
+      const int c = lane;
+      T v[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        v[r] = (r >= c && r < nb && c < nb) ? S[(kb + r) * lds + kb + c] : T(0);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        if (k < nb) {
+          const T piv = __shfl_sync(0xffffffffu, v[k], k);
+          const bool drop = !(piv > tol_abs);
+          T rs, inv;
+          recip_sqrt(piv, drop, rs, inv);
+          if (c == k) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+              if (r >= k) v[r] *= rs;
+            rsb[k] = rs;
+          }
+          T lck = T(0);
+#pragma unroll
+          for (int r = k + 1; r < 32; ++r) {
+            const T l = __shfl_sync(0xffffffffu, v[r], k);
+            if (r == c) lck = l;
+            if (c > k && r >= c) v[r] -= l * lck;
+          }
         }
-        T lik = T(0);
-        if (lane > k && lane < nb) {
-          lik = S[(kb + lane) * lds + kb + k] * rs;
-          S[(kb + lane) * lds + kb + k] = lik;
-        }
-        __syncwarp();
-        if (lane > k && lane < nb)
-          for (int jx = k + 1; jx <= lane; ++jx)
-            S[(kb + lane) * lds + kb + jx] -= lik * S[(kb + jx) * lds + kb + k];
-        __syncwarp();
       }
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        if (r >= c && r < nb && c < nb) S[(kb + r) * lds + kb + c] = v[r];
     }
     __syncthreads();
-    // 2. panel rows below the block: L(r, kb+c) = (S(r, kb+c) - sum_{c'<c} L(r, kb+c') L(kb+c, kb+c')) / L(kb+c, kb+c)
+    // 2. panel rows below the block, one thread per row, in registers:
+    //    L(r, kb+c) = (S(r, kb+c) - sum_{c'<c} L(r, kb+c') L(kb+c, kb+c')) / L(kb+c, kb+c)
     const int r0 = kb + nb;
     if (tid < n - r0) {
       const int r = r0 + tid;
       T* Sr = S + r * lds + kb;
-      for (int c = 0; c < nb; ++c) {
-        T x = Sr[c];
-        const T* Lc = S + (kb + c) * lds + kb;
-        for (int cp = 0; cp < c; ++cp) x -= Sr[cp] * Lc[cp];
-        Sr[c] = x * rsb[c];
+      T x[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < nb) {
+          const T* Lc = S + (kb + c) * lds + kb;
+          T acc = Sr[c];
+#pragma unroll
+          for (int cp = 0; cp < c; ++cp) acc -= x[cp] * Lc[cp];
+          x[c] = acc * rsb[c];
+        } else {
+          x[c] = T(0);
+        }
       }
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < nb) Sr[c] = x[c];
     }
     __syncthreads();
     // 3. trailing update of the lower triangle, 4 x 4 blocks per thread
@@ -392,17 +415,34 @@ __device__ void tri_inverse(const T* U, int m, int ld, T* X, T* tmp) {
   const int nb = (m + 31) / 32;
   for (int e = tid; e < m * ld; e += FT) X[e] = T(0);
   __syncthreads();
+  // diagonal blocks: warp w inverts block w; lane c keeps column c of X in
+  // registers (back substitution with the block's reciprocal diagonal)
   if (warp < nb) {
-    const int b0 = warp * 32, c = b0 + lane;
-    if (c < m && U[c * ld + c] != T(0)) {
-      X[c * ld + c] = T(1) / U[c * ld + c];
-      for (int i = c - 1; i >= b0; --i) {
-        if (U[i * ld + i] == T(0)) continue;
-        T s = T(0);
-        for (int k = i + 1; k <= c; ++k) s += U[i * ld + k] * X[k * ld + c];
-        X[i * ld + c] = -s / U[i * ld + i];
+    const int b0 = warp * 32, c = lane, mb = min(32, m - b0);
+    T* dinv = tmp + warp * 32;  // (the off-diagonal phase rewrites tmp later)
+    if (c < mb) {
+      const T u = U[(b0 + c) * ld + b0 + c];
+      dinv[c] = (u != T(0)) ? T(1) / u : T(0);
+    }
+    __syncwarp();
+    T x[32];
+#pragma unroll
+    for (int r = 31; r >= 0; --r) {
+      if (r > c || r >= mb || c >= mb) {
+        x[r] = T(0);
+      } else if (r == c) {
+        x[r] = dinv[r];
+      } else {
+        T sacc = T(0);
+#pragma unroll
+        for (int k = r + 1; k < 32; ++k)
+          if (k <= c) sacc += U[(b0 + r) * ld + b0 + k] * x[k];
+        x[r] = -sacc * dinv[r];
       }
     }
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+      if (r <= c && c < mb) X[(b0 + r) * ld + b0 + c] = x[r];
   }
   __syncthreads();
   for (int dist = 1; dist < nb; ++dist) {
