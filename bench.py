@@ -6,9 +6,11 @@ cores of ranks (1,64,64,64,1) plus Gaussian noise at 1e-3 relative norm,
 decomposed by TT-URV right-to-left (Alg. 3 with the prescribed-accuracy rule
 of Sec. 3.1) at eps = 1e-2.  One step = one full sweep (all unfoldings, all
 kernels, the per-step rank reads included).  Metric: tensor GB/s = bytes of
-the input tensor / sweep time.
+the input tensor / sweep time.  The default precision is mixed (tcgen05
+tensor cores); a mixed run also times the same sweep in plain FP32 on the
+same input and reports both, with each one's error against the FP64 oracle.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|mixed]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp32|fp64]
     python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
 
 Under torchrun (N > 1) every rank decomposes its own copy of the workload
@@ -53,10 +55,13 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    # 200 sweeps of ~4 ms: a timed region long enough for the clock sampler
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the plain-FP32 comparison timed beside a mixed-precision run")
     ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -307,6 +312,25 @@ def run_ours(args, wl, rank, world):
                "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": int(nbytes),
                "d2h_bytes_per_step": int(core_bytes)}
 
+    # the same sweep in plain FP32 on the same input, for the mixed vs FP32 comparison
+    compare = None
+    if args.precision == "mixed" and not args.no_compare:
+        kw32 = dict(kw, precision="fp32")
+        for _ in range(2):
+            r32 = tu.tt_utv(A, **kw32)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(st)
+        for _ in range(args.steps):
+            r32 = tu.tt_utv(A, **kw32)
+        c1.record(st)
+        torch.cuda.synchronize()
+        ms32 = c0.elapsed_time(c1) / args.steps
+        acc32 = accuracy(tu, torch, A, r32, args.workload)
+        compare = {"precision": "fp32", "ms_per_step": round(ms32, 4),
+                   "value": round(world * nbytes / (ms32 * 1e-3) / 1e9, 2), "unit": "GB/s",
+                   "speedup_of_mixed": round(ms32 / ms, 3), "accuracy": acc32}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
@@ -314,14 +338,15 @@ def run_ours(args, wl, rank, world):
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "tf32x2/f32", "fp32": "f32", "fp64": "f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {wl['desc']}", "precision": args.precision,
                    "l2": "inputs larger than L2 (1 GiB tensor, 512 MiB carry)",
                    "parallelism": f"replicas x{world} (independent problems)", "ranks": ranks,
                    "bytes_per_step": nbytes},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clocks, "accuracy": acc,
+        "clocks": clocks, "accuracy": acc, "plain_fp32": compare,
         "phase_ms": [{k: round(v, 4) for k, v in p.items() if v > 0} for p in phases],
         "wall_s": round(wall, 3),
     }
@@ -352,10 +377,13 @@ def accuracy(tu, torch, A, res, workload):
 
 # -------------------------------------------------------- CPU oracle arms
 
-def cpu_sample(wl):
-    """Bounded sample of the workload for the oracle: the first I1' slices of mode 1."""
+def cpu_sample(wl, steps=1):
+    """Bounded sample of the workload for the oracle: the first s slices of
+    mode 1, about 0.9 s of oracle work per slice on the GPU machine's host cores.
+    One sweep of the sample is about 10 s; for a timed loop of `steps` sweeps
+    (the reference arm) the sample shrinks so the loop stays near 2.5 min."""
     dims = list(wl["dims"])
-    s = 4
+    s = max(1, min(12, int(150.0 / (0.9 * max(1, steps)))))
     return s, dims
 
 
@@ -379,7 +407,7 @@ def cpu_baseline(wl, repeats=1):
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return None
-    s, dims = cpu_sample(wl)
+    s, dims = cpu_sample(wl, args.steps + min(args.warmup, 1))
     from oracle import tt as otc
 
     A = make_input(wl)[:s].astype(np.float64)

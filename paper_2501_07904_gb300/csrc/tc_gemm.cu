@@ -70,6 +70,10 @@ struct TcArgs {
   int round_out;     // round FP32 outputs to TF32
   int S_st, S_op;    // ring depths
   int chunk_kb;      // k-blocks per TMEM chunk
+  int res_b;         // B converted once per CTA and kept in shared memory
+  uint32_t res_b_bytes;  // its size per k-block (hi [+ lo])
+  const float* bptr; // B source for the resident copy
+  int64_t ldb;
   uint32_t stage_bytes, a_box_bytes, b_box_bytes, op_bytes;
   float* out;
   int64_t ldo;
@@ -191,6 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   double* red = (double*)(bars + 56);  // 4 doubles
   uint8_t* stage_base = smem + 1024;
   uint8_t* op_base = stage_base + (size_t)a.S_st * a.stage_bytes;
+  uint8_t* resb_base = op_base + (size_t)a.S_op * a.op_bytes;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.x;
@@ -212,6 +217,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, 4 * NREG);
+  if (a.res_b) {
+    // resident B: every thread converts chunks (k-block, row j, k quad q) of
+    // B straight from global memory (it is small and L2-resident)
+    const uint32_t rb = smem_u32(resb_base);
+    const int nchunks = a.kb * a.n_mma * 8;
+    for (int idx = tid; idx < nchunks; idx += kThreads) {
+      const int kbi = idx / (a.n_mma * 8), w = idx % (a.n_mma * 8);
+      const int j = w % a.n_mma, q = w / a.n_mma;
+      float4 v;
+      float* vv = &v.x;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t k = (int64_t)kbi * kBK + q * 4 + e;
+        vv[e] = (k < a.K && j < a.N) ? (a.b_kmajor ? a.bptr[k + (int64_t)j * a.ldb] : a.bptr[k * a.ldb + j])
+                                     : 0.f;
+      }
+      const uint32_t hi = rb + (uint32_t)kbi * a.res_b_bytes;
+      store_chunk(hi, a.b_split ? hi + (uint32_t)a.n_mma * 128u : 0u, sw128_off((uint32_t)j, (uint32_t)q * 4u), v);
+    }
+    fence_proxy_async_smem();
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -229,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     Cursor cur;
     cur.init(a, beg);
     for (int64_t pos = beg; pos < end; ++pos, cur.next(a)) {
-      const bool same = a.sym && cur.mt == cur.nt;
+      const bool same = (a.sym && cur.mt == cur.nt) || a.res_b;  // no B slab to load
       ok = __all_sync(0xffffffffu, mbar_wait(&empty[s], ph ^ 1u, a.err));
       if (!ok) break;
       if (elect_one()) {
@@ -293,7 +319,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         const uint32_t a_hi = op0 + (uint32_t)t_op * a.op_bytes;
         const uint32_t a_lo = a_hi + 16384u;
-        const uint32_t b_hi = same ? a_hi : a_hi + (a.a_split ? 32768u : 16384u);
+        uint32_t b_hi = same ? a_hi : a_hi + (a.a_split ? 32768u : 16384u);
+        if (a.res_b) b_hi = smem_u32(resb_base) + (uint32_t)kbi * a.res_b_bytes;
         const uint32_t b_lo = same ? a_lo : b_hi + (uint32_t)a.n_mma * 128u;
         const uint32_t d = tmem + (uint32_t)(buf * NREG);
         const bool chunk_end = (local % a.chunk_kb == a.chunk_kb - 1) || (kbi == kend - 1);
@@ -343,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     Cursor cur;
     cur.init(a, beg);
     for (int64_t pos = beg; pos < end; ++pos, cur.next(a)) {
-      const bool same = a.sym && cur.mt == cur.nt;
+      const bool same = (a.sym && cur.mt == cur.nt) || a.res_b;  // no B slab to convert
       bool ok = mbar_wait(&full[s], ph, a.err);
       ok = ok && mbar_wait(&opempty[t_op], ph_op ^ 1u, a.err);
       if (!__all_sync(0xffffffffu, ok)) break;
@@ -488,6 +515,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int NREG>
 __global__ void tc_fixup_kernel(TcArgs a, double* __restrict__ out64, double* __restrict__ fix_sq) {
   __shared__ double red[32];
+  __shared__ uint32_t slot_off[1024];  // per contributing CTA: offset of its partial (in floats)
   int t;
   if (a.all_partial) {
     t = blockIdx.x;
@@ -510,6 +538,13 @@ __global__ void tc_fixup_kernel(TcArgs a, double* __restrict__ out64, double* __
     const int c_lo = (int)(((p_lo + 1) * a.G - 1) / a.total);
     const int c_hi = (int)(((p_hi + 1) * a.G - 1) / a.total);
     const int64_t m0 = (int64_t)mt * kBM, n0 = (int64_t)nt * NREG;
+    const int ncc = c_hi - c_lo + 1;  // <= G <= the SM count
+    for (int q = threadIdx.x; q < ncc; q += blockDim.x) {
+      const int cc = c_lo + q;
+      const int slot = (seg_beg(a, cc) / a.kb == t) ? 0 : 1;
+      slot_off[q] = (uint32_t)(((size_t)cc * 2 + slot) * kBM * NREG);
+    }
+    __syncthreads();
     const int rows = kBM / gridDim.y;
     const int i0 = blockIdx.y * rows;
     for (int e = threadIdx.x; e < rows * NREG; e += blockDim.x) {
@@ -517,9 +552,9 @@ __global__ void tc_fixup_kernel(TcArgs a, double* __restrict__ out64, double* __
       const int64_t m = m0 + i, n = n0 + j;
       if (m >= a.M || n >= a.N) continue;
       float sum = 0.f, comp = 0.f;
-      for (int cc = c_lo; cc <= c_hi; ++cc) {
-        const int slot = (seg_beg(a, cc) / a.kb == t) ? 0 : 1;
-        const float y = a.part[(((size_t)cc * 2 + slot) * kBM + i) * NREG + j] - comp;
+      const float* pe = a.part + (size_t)i * NREG + j;
+      for (int q = 0; q < ncc; ++q) {
+        const float y = pe[slot_off[q]] - comp;
         const float tsum = sum + y;
         comp = (tsum - sum) - y;
         sum = tsum;
@@ -644,13 +679,18 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   a.chunk_kb = std::max(1, kChunkMMA / (4 * (1 + (a_split ? 1 : 0) + (b_split ? 1 : 0))));
   a.a_box_bytes = kBM * kBK * 4;
   a.b_box_bytes = (uint32_t)a.n_mma * kBK * 4;
-  // a Gram's off-diagonal tiles load B; diagonal ones reuse A
-  const bool any_b = !sym || a.ntm > 1;
+  // a Gram's off-diagonal tiles load B; diagonal ones reuse A.  A B operand
+  // of one column tile and at most 8 k-blocks (64 KB converted) stays
+  // resident: converted once per CTA instead of once per row tile.
+  a.res_b_bytes = (uint32_t)a.n_mma * 128u * (b_split ? 2u : 1u);
+  a.res_b = (!sym && a.ntn == 1 && a.kb <= 8 && (size_t)a.kb * a.res_b_bytes <= 65536u && a.ntm >= 8) ? 1 : 0;
+  const size_t res_bytes = a.res_b ? (size_t)a.kb * a.res_b_bytes : 0;
+  const bool any_b = (!sym || a.ntm > 1) && !a.res_b;
   a.stage_bytes = a.a_box_bytes + (any_b ? a.b_box_bytes : 0u);
   a.stage_bytes = (a.stage_bytes + 1023u) & ~1023u;
   a.op_bytes = 16384u * (a_split ? 2u : 1u) + (any_b ? (uint32_t)a.n_mma * 128u * (b_split ? 2u : 1u) : 0u);
   a.op_bytes = (a.op_bytes + 1023u) & ~1023u;
-  const size_t fixed = 2048 + 1024;  // barriers + alignment slack
+  const size_t fixed = 2048 + 1024 + res_bytes;  // barriers, alignment slack, resident B
   a.S_op = 2;
   if (fixed + 4 * (size_t)a.stage_bytes + 3 * (size_t)a.op_bytes <= (size_t)kSmemBudget) a.S_op = 3;
   const size_t left = kSmemBudget - fixed - (size_t)a.S_op * a.op_bytes;
@@ -737,6 +777,8 @@ cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K,
   TcArgs& a = p.a;
   a.a_kmajor = A.row ? 1 : 0;   // A(i,k) = p[i*ld + k]
   a.b_kmajor = B.row ? 0 : 1;   // B(k,j) = p[k + j*ld]
+  a.bptr = B.p;
+  a.ldb = B.ld;
   a.round_out = o.round_out ? 1 : 0;
   a.out = out;
   a.ldo = ldo;
