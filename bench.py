@@ -146,9 +146,11 @@ def measured_peaks():
 
 
 def source_hash():
+    """Hash of the sources of the kernel whose DRAM traffic profiles/ncu_traffic.json
+    records (the tensor-core product); a change there invalidates the figure."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2501_07904_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for name in ("tc_gemm.cu", "tc_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2501_07904_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
