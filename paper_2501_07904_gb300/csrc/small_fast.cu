@@ -300,40 +300,88 @@ __device__ int chol_blocked(const T (&a)[4][8], int n, double tol, T* R, int ldr
   }
   for (int kb = 0; kb < n; kb += 32) {
     const int nb = min(32, n - kb);
-    // 1. diagonal block: lane c keeps column c (rows >= c) in registers; at
-    //    step k the scaled column k is read by shuffles, row by row, and
-    //    lane c picks up L(c, k) on the way (rows >= c come after row c)
+    // 1. diagonal block, by warp 0 in shared memory, four columns per step:
+    //    every lane factors the 4 x 4 pivot block in registers (the same
+    //    drop rule, column by column), the lanes below solve their rows
+    //    against it, then each lane applies the rank-4 update to its row.
     if (warp == 0) {
-      const int c = lane;
-      T v[32];
+      for (int k0 = 0; k0 < nb; k0 += 4) {
+        const int kw = min(4, nb - k0);
+        T L4[4][4], rs4[4];
 #pragma unroll
-      for (int r = 0; r < 32; ++r)
-        v[r] = (r >= c && r < nb && c < nb) ? S[(kb + r) * lds + kb + c] : T(0);
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        if (k < nb) {
-          const T piv = __shfl_sync(0xffffffffu, v[k], k);
-          const bool drop = !(piv > tol_abs);
-          T rs, inv;
-          recip_sqrt(piv, drop, rs, inv);
-          if (c == k) {
+          for (int b = 0; b < 4; ++b)
+            L4[a][b] = (b <= a && a < kw) ? S[(kb + k0 + a) * lds + kb + k0 + b] : T(0);
 #pragma unroll
-            for (int r = 0; r < 32; ++r)
-              if (r >= k) v[r] *= rs;
-            rsb[k] = rs;
-          }
-          T lck = T(0);
+        for (int c = 0; c < 4; ++c) {
+          T dcc = L4[c][c];
 #pragma unroll
-          for (int r = k + 1; r < 32; ++r) {
-            const T l = __shfl_sync(0xffffffffu, v[r], k);
-            if (r == c) lck = l;
-            if (c > k && r >= c) v[r] -= l * lck;
+          for (int t = 0; t < c; ++t) dcc -= L4[c][t] * L4[c][t];
+          const bool drop = (c >= kw) || !(dcc > tol_abs);
+          T rsc, invc;
+          recip_sqrt(dcc, drop, rsc, invc);
+          rs4[c] = rsc;
+          L4[c][c] = drop ? T(0) : dcc * rsc;
+#pragma unroll
+          for (int a = c + 1; a < 4; ++a) {
+            T v = L4[a][c];
+#pragma unroll
+            for (int t = 0; t < c; ++t) v -= L4[a][t] * L4[c][t];
+            L4[a][c] = v * rsc;
           }
         }
-      }
+        const int i = lane;
+        T x[4] = {T(0), T(0), T(0), T(0)};
+        if (i >= k0 + kw && i < nb) {
+          T* Si = S + (kb + i) * lds + kb + k0;
 #pragma unroll
-      for (int r = 0; r < 32; ++r)
-        if (r >= c && r < nb && c < nb) S[(kb + r) * lds + kb + c] = v[r];
+          for (int c = 0; c < 4; ++c) {
+            T v = (c < kw) ? Si[c] : T(0);
+#pragma unroll
+            for (int t = 0; t < c; ++t) v -= x[t] * L4[c][t];
+            x[c] = v * rs4[c];
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (c < kw) Si[c] = x[c];
+        } else if (i >= k0 && i < k0 + kw) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (c <= i - k0) S[(kb + i) * lds + kb + k0 + c] = L4[i - k0][c];
+          rsb[i] = rs4[i - k0];
+        }
+        __syncwarp();
+        if (i >= k0 + kw && i < nb) {
+          T* row = S + (kb + i) * lds + kb;
+          const T* Lg = S + kb * lds + kb + k0;  // L(kb + j, kb + k0 + t) = Lg[j * lds + t]
+          int j = k0 + kw;
+          for (; j + 1 <= i; j += 2) {
+            const T* l0 = Lg + j * lds;
+            const T* l1 = l0 + lds;
+            const T r0 = row[j], r1 = row[j + 1];
+            T s0 = T(0), s1 = T(0);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              if (t < kw) {
+                s0 += x[t] * l0[t];
+                s1 += x[t] * l1[t];
+              }
+            }
+            row[j] = r0 - s0;
+            row[j + 1] = r1 - s1;
+          }
+          if (j <= i) {
+            const T* l0 = Lg + j * lds;
+            T s0 = T(0);
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (t < kw) s0 += x[t] * l0[t];
+            row[j] -= s0;
+          }
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
     // 2. panel rows below the block, one thread per row, in registers:
