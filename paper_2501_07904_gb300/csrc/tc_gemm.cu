@@ -1,26 +1,33 @@
 // Tensor-core (tcgen05) products for the mixed-precision sweep: D = A B with
 // FP32 data, TF32 operands rounded to nearest, FP32 accumulation.
 //
-// One persistent CTA per SM, fourteen warps with fixed roles:
+// One persistent CTA per SM, sixteen warps with fixed roles (a warp runs on
+// scheduler warp % 4; the converters stay off the MMA issuer's scheduler):
 //   warp 0     TMA producer: 2-D tensor-map copies of the FP32 operand
 //              slabs (128 rows x 32 k of A, n_mma rows x 32 k of B) into a
 //              staging ring;
 //   warp 1     allocates tensor memory; one lane issues tcgen05.mma;
-//   warps 2-9  converters: round the staged FP32 values to TF32 (and, for a
-//              split operand, keep the remainder x - hi, whose low bits the
-//              MMA ignores), writing K-major 128-byte-swizzled operand tiles;
-//   warps 10-13 epilogue: after every k-block (one TMEM chunk) the
+//   warps 2-4, 6-8, 10, 11  converters: round the staged FP32 values to TF32
+//              (and, for a split operand, keep the remainder x - hi, whose
+//              low bits the MMA ignores), writing K-major 128-byte-swizzled
+//              operand tiles;
+//   warps 5, 9 idle;
+//   warps 12-15 epilogue: after every chunk of k-blocks the
 //              accumulator is read back and added into a running FP32 sum
 //              kept in spare TMEM columns, which bounds the rounding drift of
 //              the tensor-core accumulation; at the end of a work segment the
 //              sum goes to the output or to a partial.
+// A split operand x = hi + lo (both TF32) makes the product accurate to
+// ~2^-22 relative: the main term hi*hi accumulates in its own TMEM columns
+// and the small cross terms (hi*lo, lo*hi) in a second set, so only the main
+// term's accumulation drift bounds the chunk length; with a split B the
+// MMA hi * [B_hi | B_lo] (N = 2 n_mma) gives the main term and one cross
+// term at once.
 // Work is scheduled stream-K: the (tile, k-block) sequence is cut into one
 // contiguous range per CTA, so a few output tiles over a long K (Gram
 // matrices, sketches) still occupy every SM.  Tiles covered by several CTAs
 // are finished by a fix-up kernel that adds the partials in CTA order
-// (deterministic).  A split operand x = hi + lo (both TF32) makes the
-// product accurate to ~2^-22 relative (three MMAs per k-step when both are
-// split: hi*hi + hi*lo + lo*hi).
+// (deterministic).
 //
 // Every mbarrier wait is bounded (tc_common.cuh): a stall sets the error
 // word, the roles unwind, in-flight copies and MMAs are drained and the
@@ -41,8 +48,8 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 448;
-constexpr int kConv = 256;     // converter threads (warps 2-9)
+constexpr int kThreads = 512;
+constexpr int kConv = 256;     // converter threads (eight warps)
 constexpr int kBM = 128;       // rows of an output tile (MMA M)
 constexpr int kBK = 32;        // k per staged slab (one 128-byte swizzle row of TF32)
 // The tensor-core accumulation drifts toward zero by up to about one FP32
@@ -62,7 +69,11 @@ struct TcArgs {
   int ntiles;
   int64_t total;     // ntiles * kb
   int G;             // CTAs
-  int n_mma;         // MMA N (multiple of 16, <= NREG)
+  int n_mma;         // MMA N (multiple of 16, <= NREG; of 32 for a split operand)
+  int split;         // a_split || b_split: cross terms accumulate at column n_mma
+  int merge;         // hi*[B_hi | B_lo] in one MMA of N = 2 n_mma (B tile rows contiguous)
+  int nacc;          // TMEM accumulator buffers (<= kAccBufs)
+  int acc_stride;    // TMEM columns per buffer
   int a_kmajor, b_kmajor;  // source layouts (1: contiguous along k)
   int a_split, b_split;
   int sym;           // Gram: upper tiles only, diagonal tiles use A for B
@@ -209,14 +220,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&opfull[t], kConv);
       mbar_init(&opempty[t], 1);
     }
-    for (int b = 0; b < kAccBufs; ++b) {
+    for (int b = 0; b < a.nacc; ++b) {
       mbar_init(&accfull[b], 1);
       mbar_init(&accempty[b], 128);
     }
     mbar_init(finalbar, 1);
     fence_barrier_init();
   }
-  if (warp == 1) tmem_alloc(tmem_slot, 4 * NREG);
+  if (warp == 1) tmem_alloc(tmem_slot, 512);
   if (a.res_b) {
     // resident B: every thread converts chunks (k-block, row j, k quad q) of
     // B straight from global memory (it is small and L2-resident)
@@ -295,6 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer (warp-wide loop, one elected issuer) ----------------
     const uint32_t idesc = idesc_tf32(kBM, a.n_mma);
+    const uint32_t idesc2 = idesc_tf32(kBM, 2 * a.n_mma);
     const uint32_t op0 = smem_u32(op_base);
     int t_op = 0;
     uint32_t ph_op = 0;
@@ -322,7 +334,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t b_hi = same ? a_hi : a_hi + (a.a_split ? 32768u : 16384u);
         if (a.res_b) b_hi = smem_u32(resb_base) + (uint32_t)kbi * a.res_b_bytes;
         const uint32_t b_lo = same ? a_lo : b_hi + (uint32_t)a.n_mma * 128u;
-        const uint32_t d = tmem + (uint32_t)(buf * NREG);
+        const uint32_t d = tmem + (uint32_t)(buf * a.acc_stride);
+        const uint32_t dc = d + (uint32_t)a.n_mma;  // cross terms of a split product
         const bool chunk_end = (local % a.chunk_kb == a.chunk_kb - 1) || (kbi == kend - 1);
         if (elect_one()) {
           // a TMEM buffer handed back by the epilogue is written only after
@@ -332,13 +345,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           // descriptor's 16-byte units) inside the swizzle atom
           const uint64_t dah = make_sw128_desc(a_hi), dbh = make_sw128_desc(b_hi);
           const uint64_t dal = make_sw128_desc(a_lo), dbl = make_sw128_desc(b_lo);
+          // the main term hi*hi accumulates at d, the small cross terms
+          // hi*lo and lo*hi at dc: the chunk length bounds the drift of the
+          // main term only
+          const bool merge = a.merge && !(same && a.n_mma != kBM);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t acc = (chunk_start && kk == 0) ? 0u : 1u;
             const uint64_t o = 2u * (uint64_t)kk;
-            mma_tf32(d, dah + o, dbh + o, idesc, acc);
-            if (a.b_split) mma_tf32(d, dah + o, dbl + o, idesc, 1u);
-            if (a.a_split) mma_tf32(d, dal + o, dbh + o, idesc, 1u);
+            if (merge) {
+              mma_tf32(d, dah + o, dbh + o, idesc2, acc);  // [hi*hi | hi*lo]
+            } else {
+              mma_tf32(d, dah + o, dbh + o, idesc, acc);
+              if (a.b_split) mma_tf32(dc, dah + o, dbl + o, idesc, acc);
+            }
+            if (a.a_split) mma_tf32(dc, dal + o, dbh + o, idesc, a.b_split ? 1u : acc);
           }
           mma_commit(&opempty[t_op]);
           if (chunk_end) mma_commit(&accfull[buf]);
@@ -350,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (chunk_end) {
           ++fills[buf];
-          if (++buf == kAccBufs) buf = 0;
+          if (++buf == a.nacc) buf = 0;
         }
       }
       pos += kend - kstart;
@@ -362,9 +383,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t t0 = globaltimer_ns();
     while (!mbar_try_wait(finalbar, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
     }
-  } else if (warp < 2 + kConv / 32) {
+  } else if (warp < 12 && warp != 5 && warp != 9) {
     // ---------------- converters ----------------
-    const int ct = tid - 64;  // 0 .. kConv-1
+    const int ci = warp - 2 - (warp > 5 ? 1 : 0) - (warp > 9 ? 1 : 0);
+    const int ct = ci * 32 + lane;  // 0 .. kConv-1
     int s = 0, t_op = 0;
     uint32_t ph = 0, ph_op = 0;
     Cursor cur;
@@ -394,14 +416,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         ph_op ^= 1u;
       }
     }
-  } else {
+  } else if (warp >= 12) {
     // ---------------- epilogue ----------------
-    // TMEM columns [0, 2 NREG) are the two MMA buffers, [2 NREG, 3 NREG) the
+    // TMEM: nacc accumulator buffers of acc_stride columns (a split product's
+    // cross terms at column n_mma of each), then NREG columns holding the
     // running FP32 sum of the current segment's drained chunks.
     const int q = warp & 3;               // TMEM lane quarter of this warp
     const int row = q * 32 + lane;        // tile row owned by this thread
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-    const uint32_t sum_addr = lane_addr + (uint32_t)(kAccBufs * NREG);
+    const uint32_t sum_addr = lane_addr + (uint32_t)(a.nacc * a.acc_stride);
     double sq = 0.0;
     int buf = 0;
     uint32_t drains[kAccBufs] = {0u, 0u, 0u};
@@ -433,13 +456,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c32 = 0; c32 < NREG / 32; ++c32) {
           float v[32];
           {
-            uint32_t rv[32], ru[32];
-            tmem_ld32_nowait(lane_addr + (uint32_t)(buf * NREG + c32 * 32), rv);
-            if (ch > 0) tmem_ld32_nowait(sum_addr + (uint32_t)(c32 * 32), ru);
-            tmem_wait_ld();
+            const uint32_t ab = lane_addr + (uint32_t)(buf * a.acc_stride + c32 * 32);
+            if (a.split) {
+              // main part, then the cross part and the running sum, one
+              // 32-column load in flight at a time (register budget)
+              tmem_ld32(ab, v);
+              float u[32];
+              tmem_ld32(ab + (uint32_t)a.n_mma, u);
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              v[j] = (ch > 0) ? __uint_as_float(rv[j]) + __uint_as_float(ru[j]) : __uint_as_float(rv[j]);
+              for (int j = 0; j < 32; ++j) v[j] += u[j];
+              if (ch > 0) {
+                tmem_ld32(sum_addr + (uint32_t)(c32 * 32), u);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] += u[j];
+              }
+            } else {
+              uint32_t rv[32], ru[32];
+              tmem_ld32_nowait(ab, rv);
+              if (ch > 0) tmem_ld32_nowait(sum_addr + (uint32_t)(c32 * 32), ru);
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                v[j] = (ch > 0) ? __uint_as_float(rv[j]) + __uint_as_float(ru[j]) : __uint_as_float(rv[j]);
+            }
           }
           if (!last) {
             tmem_st32(sum_addr + (uint32_t)(c32 * 32), v);
@@ -484,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         mbar_arrive(&accempty[buf]);
         ++drains[buf];
-        if (++buf == kAccBufs) buf = 0;
+        if (++buf == a.nacc) buf = 0;
       }
       sq += (double)rs;
       pos += kend - kstart;
@@ -494,14 +533,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int o2 = 16; o2 > 0; o2 >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o2);
       if (lane == 0) red[q] = sq;
       named_barrier(1, 128);
-      if (tid == 64 + kConv) a.sq_part[c] = red[0] + red[1] + red[2] + red[3];
+      if (tid == 12 * 32) a.sq_part[c] = red[0] + red[1] + red[2] + red[3];
     }
   }
 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, 4 * NREG);
+  if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
 // Finish tiles covered by more than one CTA (or every tile when all_partial):
@@ -652,7 +691,14 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   a.M = M;
   a.N = N;
   a.K = K;
-  a.n_mma = (int)std::min<int64_t>(p.nreg, ceil_div(nw, 16) * 16);
+  // a split product keeps its cross terms at column n_mma: 32-aligned for the
+  // epilogue's 32-column TMEM loads
+  a.split = (a_split || b_split) ? 1 : 0;
+  a.n_mma = (int)std::min<int64_t>(p.nreg, ceil_div(nw, a.split ? 32 : 16) * (a.split ? 32 : 16));
+  a.merge = b_split ? 1 : 0;
+  a.acc_stride = a.split ? 2 * a.n_mma : p.nreg;
+  a.nacc = std::min(kAccBufs, (512 - a.n_mma) / a.acc_stride);
+  if (a.nacc < 1) return false;
   a.kb = (int)ceil_div(K, kBK);
   a.ntm = (int)ceil_div(M, kBM);
   a.ntn = (int)ceil_div(N, p.nreg);
@@ -676,7 +722,7 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   a.G = (int)G;
   a.a_split = a_split ? 1 : 0;
   a.b_split = b_split ? 1 : 0;
-  a.chunk_kb = std::max(1, kChunkMMA / (4 * (1 + (a_split ? 1 : 0) + (b_split ? 1 : 0))));
+  a.chunk_kb = std::max(1, kChunkMMA / 4);  // main-term MMAs per k-block
   a.a_box_bytes = kBM * kBK * 4;
   a.b_box_bytes = (uint32_t)a.n_mma * kBK * 4;
   // a Gram's off-diagonal tiles load B; diagonal ones reuse A.  A B operand
