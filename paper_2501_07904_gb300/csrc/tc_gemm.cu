@@ -74,6 +74,9 @@ struct TcArgs {
   int merge;         // hi*[B_hi | B_lo] in one MMA of N = 2 n_mma (B tile rows contiguous)
   int nacc;          // TMEM accumulator buffers (<= kAccBufs)
   int acc_stride;    // TMEM columns per buffer
+  int xshared;       // split, n_mma > 102: one cross-term region per work segment
+  int cross_col;     // its first TMEM column (xshared)
+  int sum_col;       // first TMEM column of the running sum
   int a_kmajor, b_kmajor;  // source layouts (1: contiguous along k)
   int a_split, b_split;
   int sym;           // Gram: upper tiles only, diagonal tiles use A for B
@@ -202,11 +205,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* accfull = bars + 4 * kMaxStages;
   uint64_t* accempty = accfull + kAccBufs;
   uint64_t* finalbar = accfull + 2 * kAccBufs;
+  uint64_t* crossfree = finalbar + 1;  // the epilogue has read a segment's cross terms
   uint32_t* tmem_slot = (uint32_t*)(bars + 48);
   double* red = (double*)(bars + 56);  // 4 doubles
   uint8_t* stage_base = smem + 1024;
   uint8_t* op_base = stage_base + (size_t)a.S_st * a.stage_bytes;
   uint8_t* resb_base = op_base + (size_t)a.S_op * a.op_bytes;
+  // epilogue store staging, 2 KB per epilogue warp, after the resident B
+  const uint32_t stg0 = smem_u32(resb_base) + (a.res_b ? (uint32_t)a.kb * a.res_b_bytes : 0u);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.x;
@@ -225,6 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&accempty[b], 128);
     }
     mbar_init(finalbar, 1);
+    mbar_init(crossfree, 128);
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(tmem_slot, 512);
@@ -311,6 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int t_op = 0;
     uint32_t ph_op = 0;
     uint32_t fills[kAccBufs] = {0u, 0u, 0u};
+    uint32_t nseg = 0;
     int buf = 0;
     bool ok = true;
     int64_t pos = beg;
@@ -320,6 +328,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int kstart = cur.kbi;
       const int kend = (int)std::min<int64_t>((int64_t)a.kb, kstart + (end - pos));
       const bool same = a.sym && cur.mt == cur.nt;
+      if (a.xshared) {
+        // the previous segment's cross terms must have been read
+        ok = __all_sync(0xffffffffu, mbar_wait(crossfree, (nseg & 1u) ^ 1u, a.err));
+        if (!ok) break;
+        ++nseg;
+      }
       for (int kbi = kstart; kbi < kend; ++kbi) {
         const int local = kbi - kstart;
         const bool chunk_start = (local % a.chunk_kb) == 0;
@@ -335,7 +349,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (a.res_b) b_hi = smem_u32(resb_base) + (uint32_t)kbi * a.res_b_bytes;
         const uint32_t b_lo = same ? a_lo : b_hi + (uint32_t)a.n_mma * 128u;
         const uint32_t d = tmem + (uint32_t)(buf * a.acc_stride);
-        const uint32_t dc = d + (uint32_t)a.n_mma;  // cross terms of a split product
+        // cross terms of a split product: beside the main term, or one
+        // region for the whole segment
+        const uint32_t dc = a.xshared ? tmem + (uint32_t)a.cross_col : d + (uint32_t)a.n_mma;
+        const uint32_t acc_x0 = a.xshared ? (kbi == kstart ? 0u : 1u) : (chunk_start ? 0u : 1u);
         const bool chunk_end = (local % a.chunk_kb == a.chunk_kb - 1) || (kbi == kend - 1);
         if (elect_one()) {
           // a TMEM buffer handed back by the epilogue is written only after
@@ -352,14 +369,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t acc = (chunk_start && kk == 0) ? 0u : 1u;
+            const uint32_t accx = (kk == 0) ? acc_x0 : 1u;
             const uint64_t o = 2u * (uint64_t)kk;
             if (merge) {
               mma_tf32(d, dah + o, dbh + o, idesc2, acc);  // [hi*hi | hi*lo]
             } else {
               mma_tf32(d, dah + o, dbh + o, idesc, acc);
-              if (a.b_split) mma_tf32(dc, dah + o, dbl + o, idesc, acc);
+              if (a.b_split) mma_tf32(dc, dah + o, dbl + o, idesc, accx);
             }
-            if (a.a_split) mma_tf32(dc, dal + o, dbh + o, idesc, a.b_split ? 1u : acc);
+            if (a.a_split) mma_tf32(dc, dal + o, dbh + o, idesc, a.b_split ? 1u : accx);
           }
           mma_commit(&opempty[t_op]);
           if (chunk_end) mma_commit(&accfull[buf]);
@@ -424,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;               // TMEM lane quarter of this warp
     const int row = q * 32 + lane;        // tile row owned by this thread
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-    const uint32_t sum_addr = lane_addr + (uint32_t)(a.nacc * a.acc_stride);
+    const uint32_t sum_addr = lane_addr + (uint32_t)a.sum_col;
     double sq = 0.0;
     int buf = 0;
     uint32_t drains[kAccBufs] = {0u, 0u, 0u};
@@ -457,27 +475,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           float v[32];
           {
             const uint32_t ab = lane_addr + (uint32_t)(buf * a.acc_stride + c32 * 32);
-            if (a.split) {
-              // main part, then the cross part and the running sum, one
-              // 32-column load in flight at a time (register budget)
-              tmem_ld32(ab, v);
+            // main part (and a split product's cross part), then the running
+            // sum: one 32-column load in flight at a time (register budget)
+            tmem_ld32(ab, v);
+            if (a.split && (!a.xshared || last)) {
+              // a shared cross region is complete (and read) at the
+              // segment's last chunk only
               float u[32];
-              tmem_ld32(ab + (uint32_t)a.n_mma, u);
+              tmem_ld32(a.xshared ? lane_addr + (uint32_t)(a.cross_col + c32 * 32) : ab + (uint32_t)a.n_mma, u);
 #pragma unroll
               for (int j = 0; j < 32; ++j) v[j] += u[j];
-              if (ch > 0) {
-                tmem_ld32(sum_addr + (uint32_t)(c32 * 32), u);
+            }
+            if (ch > 0) {
+              float u[32];
+              tmem_ld32(sum_addr + (uint32_t)(c32 * 32), u);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] += u[j];
-              }
-            } else {
-              uint32_t rv[32], ru[32];
-              tmem_ld32_nowait(ab, rv);
-              if (ch > 0) tmem_ld32_nowait(sum_addr + (uint32_t)(c32 * 32), ru);
-              tmem_wait_ld();
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                v[j] = (ch > 0) ? __uint_as_float(rv[j]) + __uint_as_float(ru[j]) : __uint_as_float(rv[j]);
+              for (int j = 0; j < 32; ++j) v[j] += u[j];
             }
           }
           if (!last) {
@@ -485,17 +498,47 @@ __global__ void __launch_bounds__(kThreads, 1)
             continue;
           }
           if (direct) {
-            if (m < a.M) {
-              const int jb = c32 * 32;
+            const int jb = c32 * 32;
+            if (a.round_out) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] = round_tf32(v[j]);
+            }
+            if (vec && jb + 32 <= ncols) {
+              // a full 32-column chunk: the warp passes its 32 rows through
+              // its 2 KB staging buffer, 16 rows at a time (chunk positions
+              // swizzled by row), so that every store writes four whole
+              // 128-byte row segments
+              if (m < a.M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) rs += v[j] * v[j];
+              }
+              const uint32_t sbuf = stg0 + (uint32_t)q * 2048u;
+              const int64_t gr0 = (int64_t)mt * kBM + q * 32;  // this warp's first row
+              float* const ob = a.out + n0 + jb + 4 * (lane & 7);
+#pragma unroll 1
+              for (int h = 0; h < 2; ++h) {
+                if ((lane >> 4) == h) {
+                  const uint32_t r = (uint32_t)(lane & 15);
+#pragma unroll
+                  for (int jc = 0; jc < 8; ++jc)
+                    sts128(sbuf + r * 128u + ((((uint32_t)jc ^ (r & 7u)) << 4)), __float_as_uint(v[4 * jc]),
+                           __float_as_uint(v[4 * jc + 1]), __float_as_uint(v[4 * jc + 2]),
+                           __float_as_uint(v[4 * jc + 3]));
+                }
+                __syncwarp();
+#pragma unroll
+                for (int pq = 0; pq < 4; ++pq) {
+                  const uint32_t r = (uint32_t)(lane >> 3) + 4u * pq, jc = (uint32_t)(lane & 7);
+                  const float4 x = lds128(sbuf + r * 128u + ((jc ^ (r & 7u)) << 4));
+                  const int64_t gm = gr0 + 16 * h + (int)r;
+                  if (gm < a.M) *reinterpret_cast<float4*>(ob + gm * a.ldo) = x;
+                }
+                __syncwarp();
+              }
+            } else if (m < a.M) {
 #pragma unroll
               for (int j = 0; j < 32; j += 4) {
-                float v0 = v[j], v1 = v[j + 1], v2 = v[j + 2], v3 = v[j + 3];
-                if (a.round_out) {
-                  v0 = round_tf32(v0);
-                  v1 = round_tf32(v1);
-                  v2 = round_tf32(v2);
-                  v3 = round_tf32(v3);
-                }
+                const float v0 = v[j], v1 = v[j + 1], v2 = v[j + 2], v3 = v[j + 3];
                 const int jj = jb + j;
                 if (jj + 3 < ncols) {
                   if (vec) {
@@ -522,6 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_before();
         mbar_arrive(&accempty[buf]);
+        if (a.xshared && last) mbar_arrive(crossfree);
         ++drains[buf];
         if (++buf == a.nacc) buf = 0;
       }
@@ -698,7 +742,17 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   a.merge = b_split ? 1 : 0;
   a.acc_stride = a.split ? 2 * a.n_mma : p.nreg;
   a.nacc = std::min(kAccBufs, (512 - a.n_mma) / a.acc_stride);
-  if (a.nacc < 1) return false;
+  a.xshared = 0;
+  if (a.split && a.nacc < 2) {
+    // two main-term buffers, one cross region per work segment, the sum
+    a.xshared = 1;
+    a.merge = 0;
+    a.acc_stride = a.n_mma;
+    a.nacc = 2;
+    a.cross_col = 2 * a.n_mma;
+  }
+  a.sum_col = a.xshared ? 3 * a.n_mma : a.nacc * a.acc_stride;
+  if (a.nacc < 1 || a.sum_col + p.nreg > 512) return false;
   a.kb = (int)ceil_div(K, kBK);
   a.ntm = (int)ceil_div(M, kBM);
   a.ntn = (int)ceil_div(N, p.nreg);
@@ -736,7 +790,8 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   a.stage_bytes = (a.stage_bytes + 1023u) & ~1023u;
   a.op_bytes = 16384u * (a_split ? 2u : 1u) + (any_b ? (uint32_t)a.n_mma * 128u * (b_split ? 2u : 1u) : 0u);
   a.op_bytes = (a.op_bytes + 1023u) & ~1023u;
-  const size_t fixed = 2048 + 1024 + res_bytes;  // barriers, alignment slack, resident B
+  // barriers, alignment slack, resident B, epilogue store staging
+  const size_t fixed = 2048 + 1024 + res_bytes + 8192;
   a.S_op = 2;
   if (fixed + 4 * (size_t)a.stage_bytes + 3 * (size_t)a.op_bytes <= (size_t)kSmemBudget) a.S_op = 3;
   const size_t left = kSmemBudget - fixed - (size_t)a.S_op * a.op_bytes;
