@@ -409,6 +409,179 @@ __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int st
   return j;
 }
 
+// The four rows j0 .. j0 + kb - 1 (kb <= 4) of a column-order block, held by
+// this thread as tile rows I0 .. I0 + 3: row s of R (and of E) from the block
+// factor (Lt = the block's rows of R inside the block, rs = the pivots'
+// reciprocal square roots) and the thread's columns, published to the ring
+// slots slot + s * 3 NT (natural order, column-permuted, E column-permuted).
+template <bool AUG, int I0, typename T, int TI, int TJ>
+__device__ __forceinline__ void publish_block4(const T (&a)[TI][TJ], const T (&b)[TI][TJ],
+                                               const T (&Lt)[4][4], const T (&rs)[4], int j0,
+                                               int kb, T* slot) {
+  constexpr int NT = 16 * TI, CW = 16 / (int)sizeof(T), HW = 16 * CW, NH = TJ / CW;
+  const int tx = threadIdx.x & 15;
+#pragma unroll
+  for (int h = 0; h < NH; ++h) {
+    T rv[4][CW], ev[4][CW];
+#pragma unroll
+    for (int k = 0; k < CW; ++k) {
+      const int jj = h * CW + k, c = tile_c(jj);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        T x = a[I0 + s][jj];
+        T ex = AUG ? b[I0 + s][jj] : T(0);
+#pragma unroll
+        for (int u = 0; u < s; ++u) {
+          x = fma(-Lt[u][s], rv[u][k], x);
+          if (AUG) ex = fma(-Lt[u][s], ev[u][k], ex);
+        }
+        rv[s][k] = c > j0 + s ? x * rs[s] : (c == j0 + s ? Lt[s][s] : T(0));
+        ev[s][k] = ex * rs[s];
+        if (s < kb) slot[s * 3 * NT + c] = rv[s][k];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (s < kb) {
+        vstore<CW>(slot + s * 3 * NT + NT + h * HW + tx * CW, rv[s], 0);
+        if (AUG) vstore<CW>(slot + s * 3 * NT + 2 * NT + h * HW + tx * CW, ev[s], 0);
+      }
+  }
+}
+
+// Column-order Cholesky (no pivoting, all columns up to kmax) blocked by four
+// columns, with the results of chol_rl<AUG, false> up to rounding order: the
+// drop rule (a pivot not above tol * largest initial diagonal gives a zero row
+// of R and E and no elimination), R^{-1} = E^T (rows of E stored, ld ld,
+// columns < n), sc.kept.  The 16 threads holding rows j0 .. j0 + 3 (consecutive
+// rows of one tile-row group) gather the block's 4 x 4 upper triangle by
+// shuffles, factor it (every one of them, identically), form the block's rows
+// of R and E for their columns and publish them; after one barrier every
+// thread applies the four rank-1 updates in order.  One barrier per four
+// columns instead of one per column.  Ring: two sets of four row slots
+// (24 NT entries).
+template <bool AUG, typename T, int TI, int TJ>
+__device__ void chol_col4(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int kmax, T* E,
+                          int ld, T* ring, T* dsm, Scal& sc) {
+  constexpr int NT = 16 * TI;
+  constexpr int CW = 16 / (int)sizeof(T), HW = 16 * CW, NH = TJ / CW;
+  constexpr int DM = NT / 32;
+  static_assert(TI % 4 == 0, "a tile-row group must hold whole blocks of four rows");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+  for (int i = 0; i < TI; ++i)
+#pragma unroll
+    for (int jj = 0; jj < TJ; ++jj) {
+      const int r = tile_r<T>(i), c = tile_c(jj);
+      if (AUG) b[i][jj] = (r == c && r < n) ? T(1) : T(0);
+      if (r == c && r < n) dsm[r] = a[i][jj];
+    }
+  __syncthreads();
+  T dmax = T(0);
+#pragma unroll
+  for (int m = 0; m < DM; ++m) {
+    const int t = DM * lane + m;
+    dmax = fmax(dmax, t < n ? dsm[t] : T(0));
+  }
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  // tol_abs >= 0, so dd > tol_abs also means dd > 0 (and is false for NaN)
+  const T tol_abs = (T)(tol * (double)dmax);
+  const int jlim = min(kmax, n);
+  const int wr0 = 2 * TI * warp;  // this warp's rows: wr0 .. wr0 + 2 TI - 1
+  int kept = 0;
+  for (int j0 = 0, blk = 0; j0 < jlim; j0 += 4, ++blk) {
+    const int kb = min(4, jlim - j0);
+    T* slot = ring + (blk & 1) * 12 * NT;
+    if (ty == j0 / TI) {
+      // the block's upper triangle U[s][t] = A(j0 + s, j0 + t), s <= t, from
+      // the threads holding columns j0 .. j0 + 3 (all in column block jb)
+      const unsigned hm = 0xFFFFu << (lane & 16);
+      const int i0 = j0 % TI, jb = j0 / 16;
+      T colv[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        T rowv[TJ];
+#pragma unroll
+        for (int jj = 0; jj < TJ; ++jj) rowv[jj] = a[s][jj];
+#pragma unroll
+        for (int o = 4; o < TI; o += 4)
+#pragma unroll
+          for (int jj = 0; jj < TJ; ++jj) rowv[jj] = (i0 == o) ? a[o + s][jj] : rowv[jj];
+        colv[s] = sel_vec(rowv, jb);
+      }
+      T U[4][4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int src = (lane & 16) | ((j0 + t) & 15);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) U[s][t] = __shfl_sync(hm, colv[s], src);
+      }
+      // its factor: Lt[s][t] = R(j0 + s, j0 + t), t >= s
+      T Lt[4][4], rs[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        T dd = U[s][s];
+#pragma unroll
+        for (int u = 0; u < s; ++u) dd = fma(-Lt[u][s], Lt[u][s], dd);
+        const bool drop = (s >= kb) || !(dd > tol_abs);
+        rs[s] = recip_sqrt(dd, drop);
+        Lt[s][s] = drop ? T(0) : dd * rs[s];
+#pragma unroll
+        for (int t = s + 1; t < 4; ++t) {
+          T x = U[s][t];
+#pragma unroll
+          for (int u = 0; u < s; ++u) x = fma(-Lt[u][s], Lt[u][t], x);
+          Lt[s][t] = x * rs[s];
+        }
+      }
+      if (i0 == 0)
+        publish_block4<AUG, 0>(a, b, Lt, rs, j0, kb, slot);
+      else
+        publish_block4<AUG, 4 % TI>(a, b, Lt, rs, j0, kb, slot);
+    }
+    __syncthreads();
+    if (tid == 0)
+      for (int s = 0; s < kb; ++s) kept += (slot[s * 3 * NT + j0 + s] != T(0)) ? 1 : 0;
+    // the block's rank-1 updates in order; a warp whose rows are all
+    // eliminated skips, column halves as in chol_rl's column order
+    for (int s = 0; s < kb; ++s) {
+      const int j = j0 + s;
+      const T* rN = slot + s * 3 * NT;
+      if (AUG && tid < n) E[j * ld + tid] = rN[2 * NT + cperm<T>(tid)];
+      if (wr0 + 2 * TI - 1 > j) {
+        T lr[TI], lc[TJ], le[TJ];
+        vload<TI>(rN + TI * ty, lr, 0);
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+          const int clo = h * HW, chi = clo + HW - 1;
+          if (clo < n && chi > j && chi >= wr0) {
+            vload<CW>(rN + NT + clo + tx * CW, lc, h * CW);
+#pragma unroll
+            for (int i = 0; i < TI; ++i)
+#pragma unroll
+              for (int k = 0; k < CW; ++k)
+                a[i][h * CW + k] = fma(-lr[i], lc[h * CW + k], a[i][h * CW + k]);
+          }
+          if (AUG && clo < n && clo <= j) {
+            vload<CW>(rN + 2 * NT + clo + tx * CW, le, h * CW);
+#pragma unroll
+            for (int i = 0; i < TI; ++i)
+#pragma unroll
+              for (int k = 0; k < CW; ++k)
+                b[i][h * CW + k] = fma(-lr[i], le[h * CW + k], b[i][h * CW + k]);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    sc.kept = kept;
+    sc.trace = 0.0;
+  }
+  __syncthreads();
+}
+
 template <typename T, typename ZT>
 __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restrict__ G,
                                                            SmallParams prm, ZT* __restrict__ Z,
@@ -418,8 +591,8 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = prm.n, tid = threadIdx.x;
   const int nn = ((n + 31) / 32) * 32, ld = nn + 1;
-  T* ring = (T*)smem_raw;          // 7 NT: the step's rows of R and E, keep multipliers
-  T* trj = ring + 7 * NT;          // NT + 1 (padded to NT + 4): traces per step
+  T* ring = (T*)smem_raw;          // 24 NT: rows of R and E in flight, keep multipliers
+  T* trj = ring + 24 * NT;         // NT + 1 (padded to NT + 4): traces per step
   T* dsm = trj + NT + 4;           // NT: initial diagonal, completion vector
   T* R1 = dsm + NT;                // nn x ld
   T* R2 = R1 + nn * ld;            // nn x ld
@@ -473,8 +646,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
         for (int jj = 0; jj < TJ; ++jj)
           if (tile_r<T>(i) == tile_c(jj) && tile_r<T>(i) < n) a[i][jj] += sh;
     }
-    chol_rl<true, false>(a, b, n, prm.piv_tol, 0, 0.0, 0.0, 0, n, (T*)nullptr, X, ld, ring, trj,
-                         dsm, nullptr, sc);
+    chol_col4<true>(a, b, n, prm.piv_tol, n, X, ld, ring, dsm, sc);
     // Z = R^{-1} = E^T: warp w writes rows w, w + 8, ...
     for (int i = tid >> 5; i < n; i += FT / 32)
       for (int c = tid & 31; c < ldz; c += 32) Z[(size_t)i * ldz + c] = (c < n) ? (ZT)X[c * ld + i] : ZT(0);
@@ -494,8 +666,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   if (gw) {
     // W^T W = T^T T; factor A = T^{-T} G T^{-1}, the Gram of X Q for Q = W T^{-1}
     // (T^{-1} = E^T: T^{-1}(k, c) = E(c, k), upper triangular)
-    chol_rl<true, false>(a, b, n, 0.0, 0, 0.0, 0.0, 0, n, (T*)nullptr, X, ld, ring, trj, dsm,
-                         nullptr, sc);
+    chol_col4<true>(a, b, n, 0.0, n, X, ld, ring, dsm, sc);
     for (int e = tid; e < nn * ld; e += FT) Tw[e] = X[e];
     for (int e = tid; e < n * n; e += FT) R2[(e / n) * ld + e % n] = (T)G[e];
     __syncthreads();
@@ -542,8 +713,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
     // one more Cholesky-QR pass: Zs <- Zs R^{-1}, R^T R = Zs^T Zs, R^{-1} = E^T
     tile_product(a, rz, rz, n, [&](int rr, int q) { return R2[q * ld + rr]; },
                  [&](int c, int q) { return R2[q * ld + c]; });
-    chol_rl<true, false>(a, b, rz, 0.0, 0, 0.0, 0.0, 0, rz, (T*)nullptr, X, ld, ring, trj, dsm,
-                         nullptr, sc);
+    chol_col4<true>(a, b, rz, 0.0, rz, X, ld, ring, dsm, sc);
     tile_product(a, n, rz, rz, [&](int i, int q) { return R2[i * ld + q]; },
                  [&](int c, int q) { return q <= c ? X[c * ld + q] : T(0); });
     __syncthreads();
@@ -612,7 +782,7 @@ template <typename T>
 size_t fast_smem_bytes(int n) {
   constexpr int NT = tile_n<T>();
   const int nn = ((n + 31) / 32) * 32, ld = nn + 1;
-  return (size_t)(3 * nn * ld + 9 * NT + 4) * sizeof(T);
+  return (size_t)(3 * nn * ld + 26 * NT + 4) * sizeof(T);
 }
 
 template <typename T, typename ZT>
