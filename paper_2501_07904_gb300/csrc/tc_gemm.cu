@@ -51,7 +51,7 @@ using namespace tc;
 constexpr int kThreads = 512;
 constexpr int kConv = 256;     // converter threads (eight warps)
 constexpr int kBM = 128;       // rows of an output tile (MMA M)
-constexpr int kBK = 32;        // k per staged slab (one 128-byte swizzle row of TF32)
+constexpr int kBK = 32;        // k per 128-byte swizzle atom row of TF32 (a k-block holds 1 or 2)
 // The tensor-core accumulation drifts toward zero by up to about one FP32
 // ulp per accumulate step, so the epilogue drains TMEM into a running
 // round-to-nearest FP32 sum after at most kChunkMMA MMAs (a chunk of
@@ -65,6 +65,7 @@ constexpr int kSmemBudget = 225 * 1024;
 struct TcArgs {
   int64_t M, N, K;
   int kb;            // k-blocks per tile
+  int natoms;        // swizzle atoms (32 k each) per k-block: 2 for unsplit products, else 1
   int ntm, ntn;      // tile grid (rows, cols of tiles)
   int ntiles;
   int64_t total;     // ntiles * kb
@@ -154,37 +155,54 @@ __device__ __forceinline__ void store_chunk(uint32_t hi, uint32_t lo, uint32_t o
            __float_as_uint(v.z - __uint_as_float(h2)), __float_as_uint(v.w - __uint_as_float(h3)));
 }
 
+template <int NA>
 __device__ __forceinline__ void convert_slab(uint32_t stg, int kmajor, int R, uint32_t hi,
                                              uint32_t lo, int ct) {
-  constexpr int kPer = 1024 / kConv;  // chunks per thread for R = 128
-  float4 v[kPer];
+  // NA atoms of 32 k: atom t of the destination at hi + t * R * 128; a thread
+  // converts four chunks per group (group g: chunks ct + kConv (4 g + j))
+  constexpr int kPer = 1024 / kConv;  // chunks per thread and group for R = 128
   if (kmajor) {
-    const int nchunks = R * 8;
+    const int nchunks = R * 8 * NA;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int idx = ct + kConv * j;
-      if (idx < nchunks) v[j] = lds128(stg + (uint32_t)idx * 16u);  // row idx/8, chunk idx%8
-    }
+    for (int g = 0; g < NA; ++g) {
+      float4 v[kPer];
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int idx = ct + kConv * j;
-      if (idx < nchunks) store_chunk(hi, lo, sw128_off((uint32_t)(idx >> 3), (uint32_t)(idx & 7) * 4u), v[j]);
+      for (int j = 0; j < kPer; ++j) {
+        const int idx = ct + kConv * (kPer * g + j);
+        if (idx < nchunks) v[j] = lds128(stg + (uint32_t)idx * 16u);  // row idx/(8 NA), chunk idx%(8 NA)
+      }
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int idx = ct + kConv * (kPer * g + j);
+        if (idx < nchunks) {
+          const uint32_t row = (uint32_t)(idx / (8 * NA)), ch = (uint32_t)(idx % (8 * NA));
+          const uint32_t at = (ch >> 3) * (uint32_t)R * 128u;
+          store_chunk(hi + at, lo ? lo + at : 0u, sw128_off(row, (ch & 7u) * 4u), v[j]);
+        }
+      }
     }
   } else {
-    // thread ct owns row ct % 128, chunks q = kPer (ct / 128) ... + kPer - 1
-    const int row = ct & 127, q0 = (ct >> 7) * kPer;
+    // thread ct owns row ct % 128, chunks q = kPer NA (ct / 128) ... + kPer NA - 1
+    const int row = ct & 127, q0 = (ct >> 7) * kPer * NA;
     if (row >= R) return;
     const uint32_t p0 = stg + (uint32_t)row * 4u;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const uint32_t p = p0 + (uint32_t)((q0 + j) * 4 * R) * 4u;
-      v[j].x = lds32(p);
-      v[j].y = lds32(p + 4u * R);
-      v[j].z = lds32(p + 8u * R);
-      v[j].w = lds32(p + 12u * R);
-    }
+    for (int g = 0; g < NA; ++g) {
+      float4 v[kPer];
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) store_chunk(hi, lo, sw128_off((uint32_t)row, (uint32_t)(q0 + j) * 4u), v[j]);
+      for (int j = 0; j < kPer; ++j) {
+        const uint32_t p = p0 + (uint32_t)((q0 + kPer * g + j) * 4 * R) * 4u;
+        v[j].x = lds32(p);
+        v[j].y = lds32(p + 4u * R);
+        v[j].z = lds32(p + 8u * R);
+        v[j].w = lds32(p + 12u * R);
+      }
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const uint32_t q = (uint32_t)(q0 + kPer * g + j), at = (q >> 3) * (uint32_t)R * 128u;
+        store_chunk(hi + at, lo ? lo + at : 0u, sw128_off((uint32_t)row, (q & 7u) * 4u), v[j]);
+      }
+    }
   }
 }
 
@@ -279,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (elect_one()) {
         uint8_t* st = stage_base + (size_t)s * a.stage_bytes;
         mbar_arrive_expect_tx(&full[s], a.a_box_bytes + (same ? 0u : a.b_box_bytes));
-        const int k0 = cur.kbi * kBK;
+        const int k0 = cur.kbi * kBK * a.natoms;
         if (a.a_kmajor)
           tma_load_2d(st, &mapA, k0, cur.mt * kBM, &full[s]);
         else
@@ -345,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         const uint32_t a_hi = op0 + (uint32_t)t_op * a.op_bytes;
         const uint32_t a_lo = a_hi + 16384u;
-        uint32_t b_hi = same ? a_hi : a_hi + (a.a_split ? 32768u : 16384u);
+        uint32_t b_hi = same ? a_hi : a_hi + (a.a_split || a.natoms == 2 ? 32768u : 16384u);
         if (a.res_b) b_hi = smem_u32(resb_base) + (uint32_t)kbi * a.res_b_bytes;
         const uint32_t b_lo = same ? a_lo : b_hi + (uint32_t)a.n_mma * 128u;
         const uint32_t d = tmem + (uint32_t)(buf * a.acc_stride);
@@ -366,18 +384,30 @@ __global__ void __launch_bounds__(kThreads, 1)
           // hi*lo and lo*hi at dc: the chunk length bounds the drift of the
           // main term only
           const bool merge = a.merge && !(same && a.n_mma != kBM);
+          if (a.natoms == 2) {
+            // an unsplit product, two atoms per k-block: atom t of A at
+            // + t * 16 KB, of B at + t * n_mma * 128 bytes (16-byte units)
+            const uint64_t tb = same ? 1024u : (uint64_t)a.n_mma * 8u;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t acc = (chunk_start && kk == 0) ? 0u : 1u;
-            const uint32_t accx = (kk == 0) ? acc_x0 : 1u;
-            const uint64_t o = 2u * (uint64_t)kk;
-            if (merge) {
-              mma_tf32(d, dah + o, dbh + o, idesc2, acc);  // [hi*hi | hi*lo]
-            } else {
-              mma_tf32(d, dah + o, dbh + o, idesc, acc);
-              if (a.b_split) mma_tf32(dc, dah + o, dbl + o, idesc, accx);
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint32_t acc = (chunk_start && kk == 0) ? 0u : 1u;
+              const uint64_t k4 = 2u * (uint64_t)(kk & 3);
+              mma_tf32(d, dah + k4 + (kk >> 2) * 1024u, dbh + k4 + (kk >> 2) * tb, idesc, acc);
             }
-            if (a.a_split) mma_tf32(dc, dal + o, dbh + o, idesc, a.b_split ? 1u : accx);
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t acc = (chunk_start && kk == 0) ? 0u : 1u;
+              const uint32_t accx = (kk == 0) ? acc_x0 : 1u;
+              const uint64_t o = 2u * (uint64_t)kk;
+              if (merge) {
+                mma_tf32(d, dah + o, dbh + o, idesc2, acc);  // [hi*hi | hi*lo]
+              } else {
+                mma_tf32(d, dah + o, dbh + o, idesc, acc);
+                if (a.b_split) mma_tf32(dc, dah + o, dbl + o, idesc, accx);
+              }
+              if (a.a_split) mma_tf32(dc, dal + o, dbh + o, idesc, a.b_split ? 1u : accx);
+            }
           }
           mma_commit(&opempty[t_op]);
           if (chunk_end) mma_commit(&accfull[buf]);
@@ -416,11 +446,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!__all_sync(0xffffffffu, ok)) break;
       const uint32_t st = smem_u32(stage_base) + (uint32_t)s * a.stage_bytes;
       const uint32_t op = smem_u32(op_base) + (uint32_t)t_op * a.op_bytes;
-      convert_slab(st, a.a_kmajor, kBM, op, a.a_split ? op + 16384u : 0u, ct);
-      if (!same) {
-        const uint32_t bh = op + (a.a_split ? 32768u : 16384u);
-        convert_slab(st + a.a_box_bytes, a.b_kmajor, a.n_mma, bh,
-                     a.b_split ? bh + (uint32_t)a.n_mma * 128u : 0u, ct);
+      if (a.natoms == 2) {
+        // unsplit operands only
+        convert_slab<2>(st, a.a_kmajor, kBM, op, 0u, ct);
+        if (!same) convert_slab<2>(st + a.a_box_bytes, a.b_kmajor, a.n_mma, op + 32768u, 0u, ct);
+      } else {
+        convert_slab<1>(st, a.a_kmajor, kBM, op, a.a_split ? op + 16384u : 0u, ct);
+        if (!same) {
+          const uint32_t bh = op + (a.a_split ? 32768u : 16384u);
+          convert_slab<1>(st + a.a_box_bytes, a.b_kmajor, a.n_mma, bh,
+                          a.b_split ? bh + (uint32_t)a.n_mma * 128u : 0u, ct);
+        }
       }
       fence_proxy_async_smem();
       mbar_arrive(&opfull[t_op]);
@@ -753,7 +789,10 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   }
   a.sum_col = a.xshared ? 3 * a.n_mma : a.nacc * a.acc_stride;
   if (a.nacc < 1 || a.sum_col + p.nreg > 512) return false;
-  a.kb = (int)ceil_div(K, kBK);
+  // an unsplit product takes two swizzle atoms (64 k) per k-block: half the
+  // per-k-block hand-offs for the same bytes
+  a.natoms = (!a_split && !b_split) ? 2 : 1;
+  a.kb = (int)ceil_div(K, (int64_t)kBK * a.natoms);
   a.ntm = (int)ceil_div(M, kBM);
   a.ntn = (int)ceil_div(N, p.nreg);
   if (sym) {
@@ -776,19 +815,21 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   a.G = (int)G;
   a.a_split = a_split ? 1 : 0;
   a.b_split = b_split ? 1 : 0;
-  a.chunk_kb = std::max(1, kChunkMMA / 4);  // main-term MMAs per k-block
-  a.a_box_bytes = kBM * kBK * 4;
-  a.b_box_bytes = (uint32_t)a.n_mma * kBK * 4;
+  a.chunk_kb = std::max(1, kChunkMMA / (4 * a.natoms));  // main-term MMAs per k-block
+  a.a_box_bytes = kBM * kBK * 4 * a.natoms;
+  a.b_box_bytes = (uint32_t)a.n_mma * kBK * 4 * a.natoms;
   // a Gram's off-diagonal tiles load B; diagonal ones reuse A.  A B operand
   // of one column tile and at most 8 k-blocks (64 KB converted) stays
   // resident: converted once per CTA instead of once per row tile.
   a.res_b_bytes = (uint32_t)a.n_mma * 128u * (b_split ? 2u : 1u);
-  a.res_b = (!sym && a.ntn == 1 && a.kb <= 8 && (size_t)a.kb * a.res_b_bytes <= 65536u && a.ntm >= 8) ? 1 : 0;
+  a.res_b = (a.natoms == 1 && !sym && a.ntn == 1 && a.kb <= 8 &&
+             (size_t)a.kb * a.res_b_bytes <= 65536u && a.ntm >= 8) ? 1 : 0;
   const size_t res_bytes = a.res_b ? (size_t)a.kb * a.res_b_bytes : 0;
   const bool any_b = (!sym || a.ntm > 1) && !a.res_b;
   a.stage_bytes = a.a_box_bytes + (any_b ? a.b_box_bytes : 0u);
   a.stage_bytes = (a.stage_bytes + 1023u) & ~1023u;
-  a.op_bytes = 16384u * (a_split ? 2u : 1u) + (any_b ? (uint32_t)a.n_mma * 128u * (b_split ? 2u : 1u) : 0u);
+  a.op_bytes = 16384u * (uint32_t)a.natoms * (a_split ? 2u : 1u) +
+               (any_b ? (uint32_t)a.n_mma * 128u * (uint32_t)a.natoms * (b_split ? 2u : 1u) : 0u);
   a.op_bytes = (a.op_bytes + 1023u) & ~1023u;
   // barriers, alignment slack, resident B, epilogue store staging
   const size_t fixed = 2048 + 1024 + res_bytes + 8192;
@@ -807,19 +848,19 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
 
 // Tensor map of an FP32 operand: rows R (the M or N side) by K.
 bool encode(CUtensorMap* map, const float* p, int64_t ld, bool kmajor, int64_t R, int64_t K,
-            int box_rows) {
+            int box_rows, int box_k) {
   cuuint64_t dims[2], strides[1];
   cuuint32_t box[2], estr[2] = {1, 1};
   if (kmajor) {
     dims[0] = (cuuint64_t)K;
     dims[1] = (cuuint64_t)R;
-    box[0] = kBK;
+    box[0] = (cuuint32_t)box_k;
     box[1] = (cuuint32_t)box_rows;
   } else {
     dims[0] = (cuuint64_t)R;
     dims[1] = (cuuint64_t)K;
     box[0] = (cuuint32_t)box_rows;
-    box[1] = kBK;
+    box[1] = (cuuint32_t)box_k;
   }
   strides[0] = (cuuint64_t)ld * sizeof(float);
   CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)p, dims, strides, box, estr,
@@ -891,8 +932,8 @@ cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K,
   a.sq_part = sumsq ? sq_part : nullptr;
 
   CUtensorMap ma, mb;
-  if (!encode(&ma, A.p, A.ld, a.a_kmajor != 0, M, K, kBM)) return cudaErrorInvalidValue;
-  if (!encode(&mb, B.p, B.ld, a.b_kmajor != 0, N, K, a.n_mma)) return cudaErrorInvalidValue;
+  if (!encode(&ma, A.p, A.ld, a.a_kmajor != 0, M, K, kBM, kBK * a.natoms)) return cudaErrorInvalidValue;
+  if (!encode(&mb, B.p, B.ld, a.b_kmajor != 0, N, K, a.n_mma, kBK * a.natoms)) return cudaErrorInvalidValue;
 
   const int slot = p.nreg == 32 ? 0 : (p.nreg == 64 ? 1 : 2);
   int nl = 1;
