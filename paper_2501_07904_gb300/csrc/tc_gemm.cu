@@ -208,7 +208,8 @@ __device__ __forceinline__ void convert_slab(uint32_t stg, int kmajor, int R, ui
 
 __device__ __forceinline__ float round_tf32(float x) { return __uint_as_float(to_tf32(x)); }
 
-template <int NREG>
+// NA: swizzle atoms per k-block (a compile-time copy of TcArgs::natoms)
+template <int NREG, int NA>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const TcArgs a) {
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (elect_one()) {
         uint8_t* st = stage_base + (size_t)s * a.stage_bytes;
         mbar_arrive_expect_tx(&full[s], a.a_box_bytes + (same ? 0u : a.b_box_bytes));
-        const int k0 = cur.kbi * kBK * a.natoms;
+        const int k0 = cur.kbi * kBK * NA;
         if (a.a_kmajor)
           tma_load_2d(st, &mapA, k0, cur.mt * kBM, &full[s]);
         else
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) break;
         const uint32_t a_hi = op0 + (uint32_t)t_op * a.op_bytes;
         const uint32_t a_lo = a_hi + 16384u;
-        uint32_t b_hi = same ? a_hi : a_hi + (a.a_split || a.natoms == 2 ? 32768u : 16384u);
+        uint32_t b_hi = same ? a_hi : a_hi + (a.a_split || NA == 2 ? 32768u : 16384u);
         if (a.res_b) b_hi = smem_u32(resb_base) + (uint32_t)kbi * a.res_b_bytes;
         const uint32_t b_lo = same ? a_lo : b_hi + (uint32_t)a.n_mma * 128u;
         const uint32_t d = tmem + (uint32_t)(buf * a.acc_stride);
@@ -384,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // hi*lo and lo*hi at dc: the chunk length bounds the drift of the
           // main term only
           const bool merge = a.merge && !(same && a.n_mma != kBM);
-          if (a.natoms == 2) {
+          if (NA == 2) {
             // an unsplit product, two atoms per k-block: atom t of A at
             // + t * 16 KB, of B at + t * n_mma * 128 bytes (16-byte units)
             const uint64_t tb = same ? 1024u : (uint64_t)a.n_mma * 8u;
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!__all_sync(0xffffffffu, ok)) break;
       const uint32_t st = smem_u32(stage_base) + (uint32_t)s * a.stage_bytes;
       const uint32_t op = smem_u32(op_base) + (uint32_t)t_op * a.op_bytes;
-      if (a.natoms == 2) {
+      if (NA == 2) {
         // unsplit operands only
         convert_slab<2>(st, a.a_kmajor, kBM, op, 0u, ct);
         if (!same) convert_slab<2>(st + a.a_box_bytes, a.b_kmajor, a.n_mma, op + 32768u, 0u, ct);
@@ -720,7 +721,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 struct DevInfo {
   int sms = 0;
-  bool attr_set[3] = {false, false, false};
+  bool attr_set[4] = {false, false, false, false};
 };
 
 std::mutex g_mu;
@@ -791,7 +792,7 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   if (a.nacc < 1 || a.sum_col + p.nreg > 512) return false;
   // an unsplit product takes two swizzle atoms (64 k) per k-block: half the
   // per-k-block hand-offs for the same bytes
-  a.natoms = (!a_split && !b_split) ? 2 : 1;
+  a.natoms = (!a_split && !b_split && p.nreg == 128) ? 2 : 1;
   a.kb = (int)ceil_div(K, (int64_t)kBK * a.natoms);
   a.ntm = (int)ceil_div(M, kBM);
   a.ntn = (int)ceil_div(N, p.nreg);
@@ -869,16 +870,16 @@ bool encode(CUtensorMap* map, const float* p, int64_t ld, bool kmajor, int64_t R
   return r == CUDA_SUCCESS;
 }
 
-template <int NREG>
+template <int NREG, int NA>
 cudaError_t launch(const Plan& p, const CUtensorMap& ma, const CUtensorMap& mb, DevInfo* d,
                    int slot, cudaStream_t st) {
   if (!d->attr_set[slot]) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<NREG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBudget);
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<NREG, NA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
     if (e != cudaSuccess) return e;
     d->attr_set[slot] = true;
   }
-  tc_gemm_kernel<NREG><<<p.a.G, kThreads, p.smem, st>>>(ma, mb, p.a);
+  tc_gemm_kernel<NREG, NA><<<p.a.G, kThreads, p.smem, st>>>(ma, mb, p.a);
   return cudaGetLastError();
 }
 
@@ -935,14 +936,16 @@ cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K,
   if (!encode(&ma, A.p, A.ld, a.a_kmajor != 0, M, K, kBM, kBK * a.natoms)) return cudaErrorInvalidValue;
   if (!encode(&mb, B.p, B.ld, a.b_kmajor != 0, N, K, a.n_mma, kBK * a.natoms)) return cudaErrorInvalidValue;
 
-  const int slot = p.nreg == 32 ? 0 : (p.nreg == 64 ? 1 : 2);
+  const int slot = a.natoms == 2 ? 3 : (p.nreg == 32 ? 0 : (p.nreg == 64 ? 1 : 2));
   int nl = 1;
-  if (p.nreg == 32)
-    e = launch<32>(p, ma, mb, d, slot, st);
+  if (a.natoms == 2)
+    e = launch<128, 2>(p, ma, mb, d, slot, st);
+  else if (p.nreg == 32)
+    e = launch<32, 1>(p, ma, mb, d, slot, st);
   else if (p.nreg == 64)
-    e = launch<64>(p, ma, mb, d, slot, st);
+    e = launch<64, 1>(p, ma, mb, d, slot, st);
   else
-    e = launch<128>(p, ma, mb, d, slot, st);
+    e = launch<128, 1>(p, ma, mb, d, slot, st);
   if (e != cudaSuccess) return e;
   const bool need_fix = a.all_partial || a.G > 1;
   const unsigned fg_y = a.all_partial ? kBM : 16;
