@@ -214,27 +214,21 @@ __device__ __forceinline__ T remaining_trace(const T (&d)[DM], unsigned dmask) {
 // Row p of the Schur complement (held by the 16 threads with ty = p / TI as
 // tile row IP = p % TI) scaled into row j of R, and row p of the identity
 // tile b into row j of E: R's row in natural order (rN) and column-permuted
-// (rC), E's row column-permuted (eC).  Eliminated columns give zeros in R:
-// pivoted, the keep multipliers (kC, column-permuted, 0 once eliminated);
-// column order, every column left of p.
-template <bool AUG, bool PIV, int IP, typename T, int TI, int TJ>
+// (rC), E's row column-permuted (eC).  Eliminated columns give zeros in R
+// through the keep multipliers (kC, column-permuted, 0 once eliminated).
+template <bool AUG, int IP, typename T, int TI, int TJ>
 __device__ __forceinline__ void emit_row(const T (&a)[TI][TJ], const T (&b)[TI][TJ], int p, T dp,
-                                         T rs, bool drop, T* rN, T* rC, T* eC, const T* kC) {
+                                         T rs, T* rN, T* rC, T* eC, const T* kC) {
   constexpr int CW = 16 / (int)sizeof(T), HW = 16 * CW;
   const int tx = threadIdx.x & 15;
   T v[TJ], w[TJ], kp[TJ];
-  if (PIV) {
 #pragma unroll
-    for (int h = 0; h < TJ / CW; ++h) vload<CW>(kC + h * HW + tx * CW, kp, h * CW);
-  }
+  for (int h = 0; h < TJ / CW; ++h) vload<CW>(kC + h * HW + tx * CW, kp, h * CW);
 #pragma unroll
   for (int jj = 0; jj < TJ; ++jj) {
     const int c = tile_c(jj);
-    if (PIV)
-      v[jj] = a[IP][jj] * rs * kp[jj];
-    else
-      v[jj] = c > p ? a[IP][jj] * rs : T(0);
-    if (c == p) v[jj] = drop ? T(0) : dp * rs;
+    v[jj] = a[IP][jj] * rs * kp[jj];
+    if (c == p) v[jj] = dp * rs;
     rN[c] = v[jj];
     if (AUG) w[jj] = b[IP][jj] * rs;
   }
@@ -245,12 +239,10 @@ __device__ __forceinline__ void emit_row(const T (&a)[TI][TJ], const T (&b)[TI][
   }
 }
 
-// Cholesky of the symmetric n x n matrix held in the register tiles a.
-//   PIV        largest remaining diagonal first (lowest index on ties); else
-//              column order, a column whose remaining diagonal is not above
-//              tol * (largest initial diagonal) being dropped (zero row of R,
-//              no elimination);
-//   stop_mode  0: tolerance (pivoted) or all columns (column order);
+// Pivoted Cholesky of the symmetric n x n matrix held in the register tiles
+// a: largest remaining diagonal first (lowest index on ties), stopping at a
+// pivot not above tol * (largest initial diagonal) or as stop_mode says:
+//   stop_mode  0: tolerance only;
 //              1: first j >= 1 with base + trace <= delta2;
 //              2: j == r_stop;
 //   kmax       at most this many steps.
@@ -267,11 +259,8 @@ __device__ __forceinline__ void emit_row(const T (&a)[TI][TJ], const T (&b)[TI][
 // double-buffered ring slot, one barrier, every thread applies the rank-1
 // update to its tile.  Each warp keeps its own copy of the remaining diagonal
 // (DM = NT / 32 entries a lane) and so chooses the next pivot without a
-// further barrier.  Column order updates only the upper triangle of the
-// trailing matrix (the pivot row's entries left of the pivot belong to
-// eliminated columns) and E only in columns <= j (E is lower triangular),
-// skipping whole warps and column halves.
-template <bool AUG, bool PIV, typename T, int TI, int TJ>
+// further barrier.  (Column order: chol_col4.)
+template <bool AUG, typename T, int TI, int TJ>
 __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int stop_mode,
                        double base, double delta2, int r_stop, int kmax, T* R, T* E, int ld,
                        T* ring, T* trace_j, T* dsm, double* tails, Scal& sc) {
@@ -289,7 +278,7 @@ __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int st
       if (AUG) b[i][jj] = (r == c && r < n) ? T(1) : T(0);
       if (r == c && r < n) dsm[r] = a[i][jj];
     }
-  if (PIV && tid < NT) kC[cperm<T>(tid)] = tid < n ? T(1) : T(0);
+  if (tid < NT) kC[cperm<T>(tid)] = tid < n ? T(1) : T(0);
   __syncthreads();
   // this warp's copy of the remaining diagonal, d[m] = entry DM lane + m;
   // bit m of dmask is set once that entry is eliminated (or lies beyond n)
@@ -320,7 +309,7 @@ __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int st
     const T trt = need_trace ? remaining_trace(d, dmask) : T(0);
     int p;
     T dp;
-    if (PIV) {
+    {
       bool has = false;
       T bv = T(0);
       int bi = 0;
@@ -335,25 +324,19 @@ __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int st
           }
         }
       p = warp_argmax(has, bv, bi, dp);
-    } else {
-      const int jc = min(j, NT - 1);
-      dp = __shfl_sync(0xffffffffu, sel_vec(d, jc % DM), jc / DM);
-      p = j;
     }
-    const bool ok = dp > tol_abs;
     const bool stop = j >= jlim || p < 0 || (stop_mode == 1 && j >= 1 && trt <= stop_trace) ||
-                      (PIV && !ok);
+                      !(dp > tol_abs);
     if (need_trace && tid == 0) trace_j[j] = trt;
     if (stop) break;
-    const bool drop = !ok;  // column order only: a pivoted step stops instead
-    kept += drop ? 0 : 1;
-    const T rs = recip_sqrt(dp, drop);
-    if (PIV && tid == 0) kC[cperm<T>(p)] = T(0);
+    ++kept;
+    const T rs = recip_sqrt(dp, false);
+    if (tid == 0) kC[cperm<T>(p)] = T(0);
     if (ty == (unsigned)p / TI) {
       switch ((unsigned)p % TI) {
 #define TT_EMIT(K)                                                          \
   case K:                                                                   \
-    emit_row<AUG, PIV, K % TI>(a, b, p, dp, rs, drop, rN, rC, eC, kC);    \
+    emit_row<AUG, K % TI>(a, b, p, dp, rs, rN, rC, eC, kC);               \
     break;
         TT_EMIT(0) TT_EMIT(1) TT_EMIT(2) TT_EMIT(3) TT_EMIT(4) TT_EMIT(5) TT_EMIT(6) TT_EMIT(7)
 #undef TT_EMIT
@@ -366,16 +349,12 @@ __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int st
     vload<TI>(rN + TI * ty, lr, 0);
     if (R != nullptr && tid < n) R[j * ld + tid] = rN[tid];
     if (AUG && tid < n) E[j * ld + tid] = eC[cperm<T>(tid)];
-    // rank-1 update.  Pivoted: every tile column below n.  Column order:
-    // warps whose rows are all eliminated skip; column block jj (columns
-    // 16 jj .. 16 jj + 15) updates a while some column lies right of the
-    // pivot and not below this warp's rows, and E while some column lies at
-    // or left of the pivot.
-    if (PIV ? warp_rows : wr0 + 2 * TI - 1 > j) {
+    // rank-1 update of every tile column below n
+    if (warp_rows) {
 #pragma unroll
       for (int h = 0; h < NH; ++h) {
-        const int clo = h * HW, chi = clo + HW - 1;
-        if (clo < n && (PIV || (chi > j && chi >= wr0))) {
+        const int clo = h * HW;
+        if (clo < n) {
           vload<CW>(rC + clo + tx * CW, lc, h * CW);
 #pragma unroll
           for (int i = 0; i < TI; ++i)
@@ -383,7 +362,7 @@ __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int st
             for (int k = 0; k < CW; ++k)
               a[i][h * CW + k] = fma(-lr[i], lc[h * CW + k], a[i][h * CW + k]);
         }
-        if (AUG && clo < n && (PIV || clo <= j)) {
+        if (AUG && clo < n) {
           vload<CW>(eC + clo + tx * CW, le, h * CW);
 #pragma unroll
           for (int i = 0; i < TI; ++i)
@@ -450,10 +429,11 @@ __device__ __forceinline__ void publish_block4(const T (&a)[TI][TJ], const T (&b
 }
 
 // Column-order Cholesky (no pivoting, all columns up to kmax) blocked by four
-// columns, with the results of chol_rl<AUG, false> up to rounding order: the
-// drop rule (a pivot not above tol * largest initial diagonal gives a zero row
-// of R and E and no elimination), R^{-1} = E^T (rows of E stored, ld ld,
-// columns < n), sc.kept.  The 16 threads holding rows j0 .. j0 + 3 (consecutive
+// columns: the same fused multiply-adds in the same order as a right-looking
+// elimination with one column per barrier, so the same results.  A pivot not
+// above tol * (largest initial diagonal) is dropped (zero row of R and E, no
+// elimination); R^{-1} = E^T (rows of E stored, ld ld, columns < n); sc.kept
+// counts the pivots kept.  The 16 threads holding rows j0 .. j0 + 3 (consecutive
 // rows of one tile-row group) gather the block's 4 x 4 upper triangle by
 // shuffles, factor it (every one of them, identically), form the block's rows
 // of R and E for their columns and publish them; after one barrier every
@@ -690,7 +670,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
   const double mu2 = prm.x2_dev ? fmax(0.0, x2 - tr) : 0.0;
 
   // phase 1: pivoted Cholesky of G
-  const int k1 = chol_rl<false, true>(a, b, n, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, (T*)nullptr,
+  const int k1 = chol_rl<false>(a, b, n, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, (T*)nullptr,
                                       ld, ring, trj, dsm, nullptr, sc);
   const double s1 = sc.trace;
   // phase 2: pivoted Cholesky of M = R_1 R_1^T, with E
@@ -698,7 +678,7 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
                [&](int c, int q) { return R1[c * ld + q]; });
   const bool fixed = prm.r_fixed >= 1;
   const int rt = fixed ? min(prm.r_fixed, prm.r_cap) : -1;
-  const int r2 = chol_rl<true, true>(a, b, k1, 0.0, fixed ? 2 : 1, mu2 + s1, delta2, rt,
+  const int r2 = chol_rl<true>(a, b, k1, 0.0, fixed ? 2 : 1, mu2 + s1, delta2, rt,
                                      min(k1, prm.r_cap), (T*)nullptr, X, ld, ring, trj, dsm,
                                      info->tails, sc);
   const int r = fixed ? rt : max(1, r2);
