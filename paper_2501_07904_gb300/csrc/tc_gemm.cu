@@ -4,8 +4,8 @@
 // One persistent CTA per SM, sixteen warps with fixed roles (a warp runs on
 // scheduler warp % 4; the converters stay off the MMA issuer's scheduler):
 //   warp 0     TMA producer: 2-D tensor-map copies of the FP32 operand
-//              slabs (128 rows x 32 k of A, n_mma rows x 32 k of B) into a
-//              staging ring;
+//              slabs (128 rows of A and n_mma rows of B by one k-block: 32 k,
+//              or 64 k for an unsplit product) into a staging ring;
 //   warp 1     allocates tensor memory; one lane issues tcgen05.mma;
 //   warps 2-4, 6-8, 10, 11  converters: round the staged FP32 values to TF32
 //              (and, for a split operand, keep the remainder x - hi, whose
@@ -16,13 +16,16 @@
 //              accumulator is read back and added into a running FP32 sum
 //              kept in spare TMEM columns, which bounds the rounding drift of
 //              the tensor-core accumulation; at the end of a work segment the
-//              sum goes to the output or to a partial.
+//              sum goes to the output (through a per-warp staging buffer, so
+//              that every store writes whole 128-byte row segments) or to a
+//              partial.
 // A split operand x = hi + lo (both TF32) makes the product accurate to
 // ~2^-22 relative: the main term hi*hi accumulates in its own TMEM columns
 // and the small cross terms (hi*lo, lo*hi) in a second set, so only the main
-// term's accumulation drift bounds the chunk length; with a split B the
+// term's accumulation drift bounds the chunk length.  With a split B the
 // MMA hi * [B_hi | B_lo] (N = 2 n_mma) gives the main term and one cross
-// term at once.
+// term at once; a split product wider than 102 columns keeps one cross-term
+// region per work segment (two main-term buffers then fit in TMEM).
 // Work is scheduled stream-K: the (tile, k-block) sequence is cut into one
 // contiguous range per CTA, so a few output tiles over a long K (Gram
 // matrices, sketches) still occupy every SM.  Tiles covered by several CTAs
