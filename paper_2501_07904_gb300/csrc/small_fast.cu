@@ -4,11 +4,12 @@
 //
 // The symmetric n x n matrix is held in registers, a TI x TJ tile per thread
 // (256 threads: FP32 8 x 8 tiles cover 128 x 128, FP64 4 x 4 tiles 64 x 64).
-// Every Cholesky factorization is right-looking on these tiles with one
-// pivot per step: the 16 threads holding the pivot row write row j of R to
-// shared memory, one barrier, then every thread applies the rank-1 update to
-// its tile.  Each warp keeps its own copy of the remaining diagonal and so
-// chooses the next pivot without a further barrier.  Pivoting is virtual
+// Every Cholesky factorization is right-looking on these tiles.  Pivoted
+// (chol_rl): one pivot per step, the 16 threads holding the pivot row write
+// row j of R to shared memory, one barrier, then every thread applies the
+// rank-1 update to its tile; each warp keeps its own copy of the remaining
+// diagonal and so chooses the next pivot without a further barrier.  Column
+// order (chol_col4): the same, four columns per barrier.  Pivoting is virtual
 // (nothing is swapped): R's rows come out in step order and its columns keep
 // the original coordinates.  The same row operations applied to an identity
 // tile give E = L^{-1} P (row j of E belongs to step j), so R^{-1} = E^T comes
