@@ -343,7 +343,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
 
     // A tolerance below ~n u_fp32 of ||C||^2 cannot be resolved from an
     // FP32-accumulated Gram or an FP32 factorization: such steps form the
-    // Gram with exact products and FP64 sums, and factor it in FP64.
+    // Gram with compensated sums of exact products, and factor it in FP64.
     auto tight = [&](int64_t nsz) {
       return !fixed && !(dscale >= 2.0 * (double)nsz * 5.9604644775390625e-08);
     };
@@ -467,8 +467,8 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         po.r_cap = (int)l;
         // With a tight tolerance the sketch may carry directions near the
         // FP32 floor; W_1 is then too ill-conditioned for an FP32-summed
-        // Gram to stay positive definite, so those Grams use exact products
-        // and FP64 sums and the Cholesky runs in FP64.
+        // Gram to stay positive definite, so those Grams use compensated sums
+        // of exact products and the Cholesky runs in FP64.
         const bool orth64 = o.orth_precision == TT_SMALL_FP64 ||
                             (o.orth_precision == TT_SMALL_AUTO && (small64 || W64));
         const double u_c = orth64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
@@ -506,7 +506,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
               "Gram B^T B");
         // FP32 W is orthonormal only to ~1e-7, which biases ||X W||^2 and so
         // the range miss mu^2; with a tight tolerance the small factor
-        // whitens by W^T W (exact products, FP64 sums).
+        // whitens by W^T W (compensated sums of exact products).
         const bool whiten = !W64 && small64;
         if (whiten) {
           TT_ALLOC(gwb, (size_t)l * l * sizeof(double));

@@ -12,13 +12,39 @@
 namespace ttk {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, NT = 256;
+constexpr int BK = 16, NT = 256;
 constexpr int FLUSH_TILES = 32;  // FP32 tile sums folded into FP64 every 32 k-tiles (512 products)
+constexpr int FLUSH_DF = 8;      // compensated sums folded into FP64 every 8 k-tiles (128 products)
 constexpr int kTargetBlocks = 152 * 8;
 
-// Acc = float: two-level FP32 sums folded into FP64; Acc = double: every
-// product formed and accumulated in FP64 (exact products of FP32 operands).
-template <typename T, typename Acc, bool AR, bool BR>
+// Accumulation modes.
+//   kF32: FP32 products summed in FP32 over one k-tile, those sums in FP32
+//         over FLUSH_TILES tiles, then in FP64;
+//   kF64: FP64 data, FP64 products and sums;
+//   kDF:  FP32 data, each product split exactly into p + e (e by an FMA:
+//         a b - p is representable) and summed by Knuth's TwoSum into a
+//         running (hi, lo) pair of FP32 words (Ogita, Rump and Oishi's
+//         compensated dot product, "Dot2"), folded into FP64 every FLUSH_DF
+//         tiles.  Over a window of n = 128 products the error is at most
+//         ~n u^2 sum|a b| (u = 2^-24), i.e. below 5e-13 of sum|a b| -- the
+//         order of an FP64 sum of exact products over the same split-K chunk
+//         -- at FP32 instruction rates (FP64 runs at a small fraction of them
+//         on this part).  The __f*_rn intrinsics keep the compiler from
+//         contracting the error-free transformations into FMAs.
+enum AccMode { kF32 = 0, kF64 = 1, kDF = 2 };
+
+__device__ __forceinline__ void two_prod_sum(float a, float b, float& hi, float& lo) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);  // a b = p + e exactly (no underflow)
+  const float s = __fadd_rn(hi, p);
+  const float bv = __fsub_rn(s, hi);
+  const float q = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));  // hi + p = s + q
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(q, e));
+}
+
+// One BMX x BMX output tile per block (16 x 16 threads, TMX x TMX each).
+template <typename T, int MODE, int BMX, bool AR, bool BR>
 __global__ void __launch_bounds__(NT) gemm_tile_kernel(const T* __restrict__ A, int64_t lda,
                                                        const T* __restrict__ B, int64_t ldb,
                                                        int64_t M, int64_t N, int64_t K,
@@ -26,6 +52,7 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(const T* __restrict__ A, 
                                                        T* __restrict__ out, int64_t ldo,
                                                        double* __restrict__ part,
                                                        double* __restrict__ sq_part) {
+  constexpr int BM = BMX, BN = BMX, TM = BMX / 16, TN = BMX / 16;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   __shared__ double red[32];
@@ -37,14 +64,16 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(const T* __restrict__ A, 
   const int64_t kb = (int64_t)blockIdx.z * kchunk;
   const int64_t ke = min(K, kb + kchunk);
 
-  constexpr bool two_level = std::is_same<Acc, float>::value;
+  using Acc = typename std::conditional<MODE == kF64, double, float>::type;
   Acc acc[TM][TN];
+  float lo[TM][TN];
   double acc64[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       acc[i][j] = Acc(0);
+      lo[i][j] = 0.0f;
       acc64[i][j] = 0.0;
     }
 
@@ -80,7 +109,7 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(const T* __restrict__ A, 
         Bs[kk][j] = v;
       }
       __syncthreads();
-      if constexpr (two_level) {
+      if constexpr (MODE == kF32) {
         float t[TM][TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
@@ -112,6 +141,30 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(const T* __restrict__ A, 
               acc[i][j] = 0.0f;
             }
         }
+      } else if constexpr (MODE == kDF) {
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+          float a[TM], b[TN];
+#pragma unroll
+          for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+          for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) two_prod_sum(a[i], b[j], acc[i][j], lo[i][j]);
+        }
+        if (++tiles == FLUSH_DF) {
+          tiles = 0;
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+              acc64[i][j] += (double)acc[i][j] + (double)lo[i][j];
+              acc[i][j] = 0.0f;
+              lo[i][j] = 0.0f;
+            }
+        }
       } else {
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
@@ -131,7 +184,7 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(const T* __restrict__ A, 
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) acc64[i][j] += (double)acc[i][j];
+      for (int j = 0; j < TN; ++j) acc64[i][j] += (double)acc[i][j] + (double)lo[i][j];
   }
 
   double sq = 0.0;
@@ -163,7 +216,7 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(const T* __restrict__ A, 
 // Sum the split-K partials in order z = 0..S-1; mirror Gram tiles.
 template <typename T>
 __global__ void reduce_partials_kernel(const double* __restrict__ part, int S, int64_t M,
-                                       int64_t N, bool sym, T* __restrict__ out, int64_t ldo,
+                                       int64_t N, bool sym, int bt, T* __restrict__ out, int64_t ldo,
                                        double* __restrict__ out64, double* __restrict__ sq_part) {
   __shared__ double red[32];
   double sq = 0.0;
@@ -172,7 +225,7 @@ __global__ void reduce_partials_kernel(const double* __restrict__ part, int S, i
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / N, j = e % N;
     int64_t si = i, sj = j;
-    if (sym && (j / BN) < (i / BM)) {
+    if (sym && (j / bt) < (i / bt)) {
       si = j;
       sj = i;
     }
@@ -201,16 +254,18 @@ __global__ void sum_scalars_kernel(const double* __restrict__ v, int64_t n, doub
 }
 
 struct Plan {
+  int bt;  // square output tile: 64 (kF32, kF64) or 32 (kDF)
   int64_t gm, gn;
   int S;
   int64_t kchunk;
   int reduce_blocks;
 };
 
-Plan make_plan(int64_t M, int64_t N, int64_t K) {
+Plan make_plan(int64_t M, int64_t N, int64_t K, int bt) {
   Plan p;
-  p.gm = (M + BM - 1) / BM;
-  p.gn = (N + BN - 1) / BN;
+  p.bt = bt;
+  p.gm = (M + bt - 1) / bt;
+  p.gn = (N + bt - 1) / bt;
   const int64_t tiles = p.gm * p.gn;
   int64_t S = 1;
   if (tiles < kTargetBlocks / 2) {
@@ -234,15 +289,15 @@ void launch_tiles(dim3 grid, cudaStream_t st, Mat<T> A, Mat<T> B, int64_t M, int
                   int64_t kchunk, bool sym, T* out, int64_t ldo, double* part, double* sqp,
                   bool accurate) {
   if constexpr (std::is_same<T, double>::value) {
-    gemm_tile_kernel<double, double, AR, BR><<<grid, NT, 0, st>>>(A.p, A.ld, B.p, B.ld, M, N, K,
-                                                                  kchunk, sym, out, ldo, part, sqp);
+    gemm_tile_kernel<double, kF64, 64, AR, BR><<<grid, NT, 0, st>>>(A.p, A.ld, B.p, B.ld, M, N, K,
+                                                                   kchunk, sym, out, ldo, part, sqp);
   } else {
     if (accurate)
-      gemm_tile_kernel<float, double, AR, BR><<<grid, NT, 0, st>>>(A.p, A.ld, B.p, B.ld, M, N, K,
+      gemm_tile_kernel<float, kDF, 32, AR, BR><<<grid, NT, 0, st>>>(A.p, A.ld, B.p, B.ld, M, N, K,
                                                                    kchunk, sym, out, ldo, part, sqp);
     else
-      gemm_tile_kernel<float, float, AR, BR><<<grid, NT, 0, st>>>(A.p, A.ld, B.p, B.ld, M, N, K,
-                                                                  kchunk, sym, out, ldo, part, sqp);
+      gemm_tile_kernel<float, kF32, 64, AR, BR><<<grid, NT, 0, st>>>(A.p, A.ld, B.p, B.ld, M, N, K,
+                                                                    kchunk, sym, out, ldo, part, sqp);
   }
 }
 
@@ -250,11 +305,15 @@ void launch_tiles(dim3 grid, cudaStream_t st, Mat<T> A, Mat<T> B, int64_t M, int
 
 template <typename T>
 size_t gemm_ws_bytes(int64_t M, int64_t N, int64_t K, bool fp64_out_or_sym) {
-  const Plan p = make_plan(M, N, K);
-  size_t b = 0;
-  if (p.S > 1 || fp64_out_or_sym) b += (size_t)p.S * M * N * sizeof(double);
-  b += (size_t)std::max<int64_t>(p.gm * p.gn, p.reduce_blocks) * sizeof(double) + 512;
-  return b;
+  size_t best = 0;
+  for (int bt : {64, 32}) {
+    const Plan p = make_plan(M, N, K, bt);
+    size_t b = 0;
+    if (p.S > 1 || fp64_out_or_sym) b += (size_t)p.S * M * N * sizeof(double);
+    b += (size_t)std::max<int64_t>(p.gm * p.gn, p.reduce_blocks) * sizeof(double) + 512;
+    best = std::max(best, b);
+  }
+  return best;
 }
 
 template <typename T>
@@ -264,7 +323,8 @@ cudaError_t gemm(Mat<T> A, Mat<T> B, int64_t M, int64_t N, int64_t K, T* out, in
     if (sumsq) return cudaMemsetAsync(sumsq, 0, sizeof(double), st);
     return cudaSuccess;
   }
-  const Plan p = make_plan(M, N, K);
+  const bool df = accurate && std::is_same<T, float>::value;
+  const Plan p = make_plan(M, N, K, df ? 32 : 64);
   const bool use_part = (p.S > 1) || (out64 != nullptr) || sym;
   double* part = (double*)ws;
   double* sq_part = (double*)((char*)ws + (use_part ? (size_t)p.S * M * N * sizeof(double) : 0));
@@ -302,7 +362,7 @@ if (A.row && B.row)
   if (e != cudaSuccess) return e;
   if (use_part) {
     reduce_partials_kernel<T><<<p.reduce_blocks, 256, 0, st>>>(
-        part, p.S, M, N, sym, out, ldo, out64, (sumsq && out) ? sq_part : nullptr);
+        part, p.S, M, N, sym, p.bt, out, ldo, out64, (sumsq && out) ? sq_part : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (sumsq) {
