@@ -376,12 +376,8 @@ def l2_note(wl):
 
 def accuracy(tu, torch, A, res, workload):
     out = {"ranks": res.ranks}
-    normA2 = float((A.double() ** 2).sum())
-    full = tu.tt_full(res.cores)
-    err2 = 0.0
-    for a, b in zip(A.reshape(-1).split(1 << 26), full.reshape(-1).split(1 << 26)):
-        err2 += float(((a.double() - b.double()) ** 2).sum())
-    del full
+    # ||A - A_TT||^2 and ||A||^2 streamed by the library (FP64 sums)
+    err2, normA2 = tu.tt_rse(A.to(res.cores[0].dtype), res.cores)
     out["rse"] = (err2 / normA2) ** 0.5
     out["tails_over_err2"] = sum(res.tail_sq) / err2 if err2 > 0 else None
     gold = os.path.join(ROOT, "tests", "golden", f"{workload.split('-')[0]}_URV.npz")
@@ -391,6 +387,9 @@ def accuracy(tu, torch, A, res, workload):
                              torch.from_numpy(g["sample_idx"]).to(A.device)).double().cpu().numpy()
         out["oracle_ranks"] = [int(x) for x in g["ranks"]]
         out["oracle_rse"] = float(g["rse"])
+        # tails ||E_k||^2 / ||A||^2 per unfolding k = 1..d-1 beside the oracle's
+        out["tails_rel"] = [float(t) / normA2 for t in res.tail_sq]
+        out["oracle_tails_rel"] = [float(t) / float(g["normA2"]) for t in g["tails"]]
         out["rel_err_vs_oracle_sampled"] = float(
             np.sqrt(np.sum((vals - g["sample_val"]) ** 2) / np.sum(g["sample_ref"] ** 2)))
     return out

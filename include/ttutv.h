@@ -63,9 +63,10 @@ typedef enum { TT_RL = 0, TT_LR = 1 } tt_direction;
  *              TF32; every other product carries each FP32 operand as two
  *              TF32 terms (~2^-22 relative), so the sketch, Cholesky-QR,
  *              projection, carry and core match the FP32 form to within a
- *              few 1e-6.  Tight steps (see TT_SMALL_AUTO) run on the FP32
- *              SIMT path, as do products whose leading dimensions are not
- *              multiples of 4. */
+ *              few 1e-6.  Tight steps (see TT_SMALL_AUTO) find their range
+ *              (Grams, sketch, projection) on the FP32 SIMT path and form
+ *              carry and core on the tensor cores; products whose leading
+ *              dimensions are not multiples of 4 run on the SIMT path. */
 typedef enum { TT_P_FP64 = 0, TT_P_FP32 = 1, TT_P_MIXED = 2 } tt_precision;
 
 /* Arithmetic of the small (<= 256 x 256) factorizations:
@@ -96,7 +97,13 @@ typedef struct {
   const double* weights;    /* host, d-1 error weights w_k with sum w_k^2 = 1; NULL = equal 1/sqrt(d-1) */
   int32_t orth_precision;   /* tt_small_precision of the Cholesky-QR passes of a sketched step;
                                default TT_SMALL_AUTO = FP64 for FP64 data or a tight step, else FP32 */
-  int32_t pad_;
+  int32_t reverse;          /* 1: factor the index-reversed tensor A'(i_d..i_1) = A(i_1..i_d) and
+                               read its cores back as cores of A (Remark after Thm 3.2): TT-URV
+                               right-to-left then gives left-orthogonal cores of A, TT-ULV
+                               left-to-right right-orthogonal ones.  Costs one device copy of A
+                               (reversed in a tiled transposition kernel).  Weights, fixed ranks
+                               and every per-unfolding result refer to the unfoldings of A.
+                               Default 0. */
   double* phase_ms;         /* host, TT_MAXD * TT_NPHASES doubles [sweep step][tt_phase], or NULL.
                                Milliseconds of device time are ADDED to it; the sweep step index is
                                0 for the first factored unfolding. */
@@ -124,7 +131,11 @@ typedef struct {
   int64_t ranks[TT_MAXD + 1];    /* r_0 .. r_d, r_0 = r_d = 1 */
   void* cores[TT_MAXD];          /* device, row-major [r_{k-1}][I_k][r_k] */
   double norm_sq;                /* ||A||_F^2 (FP64) */
-  double tail_sq[TT_MAXD];       /* per unfolding k = 1..d-1 (index k-1): ||E_k||_F^2 of its truncation */
+  double tail_sq[TT_MAXD];       /* per unfolding k = 1..d-1 (index k-1): ||E_k||_F^2 of its truncation:
+                                    for a tight step the small factor's estimate (compensated Gram,
+                                    FP64 factorization), otherwise ||C_k||^2 - ||carry||^2 summed in
+                                    FP64 over the stored values (FP32 data: accurate to a few
+                                    n u_fp32 ||C_k||^2) */
   double delta_sq[TT_MAXD];      /* per unfolding: the tolerance eps_k^2 (0 for fixed ranks) */
   int32_t sketch_l[TT_MAXD];     /* per unfolding: 0 = exact Gram path, else sketch width l */
   int32_t small_fp64[TT_MAXD];   /* per unfolding: 1 if its small factor ran in FP64 */
@@ -193,6 +204,22 @@ tt_status tt_full(int32_t d, const int64_t* dims, const int64_t* ranks, const vo
 size_t tt_full_noalloc_max_work_bytes(void);
 tt_status tt_full_noalloc(int32_t d, const int64_t* dims, const int64_t* ranks,
                           const void* const* cores, int32_t dtype, void* out, void* stream);
+
+/* Reconstruction error of a TT against a full tensor, streamed: the TT is
+ * contracted one slab of the first mode at a time into scratch (as tt_full
+ * does) and compared with the matching slab of A, so the full TT tensor is
+ * never formed.  The relative error of Sec. 4 (RSE) is sqrt(out[0] / out[1]).
+ *   d, dims, ranks, cores, dtype  as for tt_full (cores device, [r_{k-1}][I_k][r_k]);
+ *   A      device, prod(dims) elements of `dtype`, row-major;
+ *   work   device scratch of at least tt_rse_work_bytes(...) bytes (a slab of
+ *          at most 2^24 entries, or one slice of the first mode if larger,
+ *          plus the contraction's scratch);
+ *   out    device double[2]: out[0] = ||A - A_TT||_F^2, out[1] = ||A||_F^2,
+ *          both summed in FP64 in a fixed order (deterministic).
+ * Asynchronous on `stream`. */
+size_t tt_rse_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks, int32_t dtype);
+tt_status tt_rse(int32_t d, const int64_t* dims, const int64_t* ranks, const void* const* cores,
+                 int32_t dtype, const void* A, void* work, double* out, void* stream);
 
 /* Masked TT evaluation x_e = G_1[i_1] G_2[:, i_2, :] ... G_d[:, i_d] at n
  * row-major linear indices idx[e] (device int64, 0 <= idx < prod(dims)).

@@ -34,7 +34,8 @@ TT_RL, TT_LR = 0, 1
 
 # Every symbol include/ttutv.h declares.
 EXPORTS = ["tt_opts_default", "tt_utv", "tt_svd", "tt_result_free", "tt_full_work_bytes",
-           "tt_full", "tt_full_noalloc", "tt_full_noalloc_max_work_bytes", "tt_eval_at",
+           "tt_full", "tt_full_noalloc", "tt_full_noalloc_max_work_bytes", "tt_rse_work_bytes",
+           "tt_rse", "tt_eval_at",
            "tt_eval_at_backward", "tt_sketch_matrix", "tt_kernel_launches", "tt_last_error",
            "tt_version"]
 PHASES = ["gram", "small", "carry", "core", "sketch", "orth", "project"]
@@ -51,7 +52,7 @@ class tt_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("small_precision", ctypes.c_int32),
                 ("oversample", ctypes.c_int32), ("l_full", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("weights", ctypes.POINTER(ctypes.c_double)),
-                ("orth_precision", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("orth_precision", ctypes.c_int32), ("reverse", ctypes.c_int32),
                 ("phase_ms", ctypes.POINTER(ctypes.c_double))]
 
 
@@ -99,6 +100,10 @@ def lib():
     L.tt_full_noalloc.restype = I32
     L.tt_full_noalloc_max_work_bytes.argtypes = []
     L.tt_full_noalloc_max_work_bytes.restype = SZ
+    L.tt_rse_work_bytes.argtypes = [I32, PI64, PI64, I32]
+    L.tt_rse_work_bytes.restype = SZ
+    L.tt_rse.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), I32, P, P, P, P]
+    L.tt_rse.restype = I32
     L.tt_eval_at.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P, P]
     L.tt_eval_at.restype = I32
     L.tt_eval_at_backward.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P,
@@ -174,7 +179,7 @@ class TTResult:
 
 
 def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream,
-           timing=False, orth="auto"):
+           timing=False, orth="auto", reverse=False):
     if not isinstance(A, torch.Tensor):
         raise TypeError("A must be a torch.Tensor")
     if A.dtype not in (torch.float32, torch.float64):
@@ -191,6 +196,7 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
     opts.oversample = int(oversample)
     opts.l_full = int(l_full)
     opts.seed = int(seed)
+    opts.reverse = 1 if reverse else 0
     wbuf = None
     if weights is not None:
         wbuf = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
@@ -230,17 +236,21 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
 
 
 def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, oversample=16,
-           l_full=256, small="auto", weights=None, stream=None, timing=False, orth="auto"):
+           l_full=256, small="auto", weights=None, stream=None, timing=False, orth="auto",
+           reverse=False):
     """TT-URV right-to-left (Alg. 3) or TT-ULV left-to-right (Alg. 1/2).
 
     Give ``eps`` (prescribed relative accuracy, Alg. 2) or ``ranks``
     (r_1..r_{d-1}).  ``A`` may live on the GPU or on the host (copied in).
+    ``reverse`` factors the index-reversed tensor and returns its cores read
+    back as cores of ``A`` (Remark after Thm 3.2: URV then gives a
+    left-orthogonal TT).
     """
     if (eps is None) == (ranks is None):
         raise ValueError("give exactly one of eps or ranks")
     v = {"URV": (TT_URV, TT_RL), "ULV": (TT_ULV, TT_LR)}[variant]
     return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
-                  weights, stream, timing, orth)
+                  weights, stream, timing, orth, reverse)
 
 
 def tt_svd(A, eps=None, ranks=None, direction="LR", precision="fp32", l_full=256, small="auto",
@@ -277,6 +287,34 @@ def tt_full(cores, stream=None):
         _check(lib().tt_full(d, D, R, ptrs, code, ctypes.c_void_p(out.data_ptr()),
                              ctypes.c_void_p(work.data_ptr()), st_ptr))
     return out
+
+
+def tt_rse(A, cores, stream=None):
+    """Streamed (||A - A_TT||_F^2, ||A||_F^2) in FP64, computed by the library
+    (the TT is contracted slab by slab, never as a whole); the relative error
+    of Sec. 4 is the square root of their ratio."""
+    d, dims, ranks = _core_meta(cores)
+    if list(A.shape) != dims:
+        raise ValueError(f"A has shape {tuple(A.shape)}, the cores describe {tuple(dims)}")
+    dtype = cores[0].dtype
+    if A.dtype != dtype or not A.is_cuda:
+        raise TypeError("A must be a device tensor of the cores' dtype")
+    A = A.contiguous()
+    cores = [g.contiguous() for g in cores]
+    st, st_ptr = _stream(stream)
+    code = TT_F64 if dtype == torch.float64 else TT_F32
+    D, R = _i64(dims), _i64(ranks)
+    nbytes = lib().tt_rse_work_bytes(d, D, R, code)
+    dev = A.device
+    with torch.cuda.device(dev), torch.cuda.stream(st):
+        out = torch.empty(2, dtype=torch.float64, device=dev)
+        work = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=dev)
+        ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores])
+        _check(lib().tt_rse(d, D, R, ptrs, code, ctypes.c_void_p(A.data_ptr()),
+                            ctypes.c_void_p(work.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                            st_ptr))
+        err2, norm2 = (float(x) for x in out.cpu())
+    return err2, norm2
 
 
 def tt_eval_at(cores, idx, stream=None):

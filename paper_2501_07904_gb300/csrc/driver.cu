@@ -236,6 +236,16 @@ struct SweepCfg {
   bool svd;   // Jacobi small factor (TT-SVD)
 };
 
+// True for host memory (pageable or pinned), false for device memory.
+bool host_pointer(const void* p) {
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered;
+}
+
 template <typename W>
 tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* dims, double eps,
                     const int64_t* fixed, SweepCfg cfg, const tt_opts& o, Alloc& al,
@@ -253,14 +263,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   for (int k = 0; k < d; ++k) total *= dims[k];
 
   // Input in the working precision, on the device.
-  cudaPointerAttributes pa;
-  bool host_in = false;
-  if (cudaPointerGetAttributes(&pa, A_in) != cudaSuccess) {
-    cudaGetLastError();
-    host_in = true;
-  } else {
-    host_in = (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered);
-  }
+  const bool host_in = host_pointer(A_in);
   const bool in64 = dtype_in == TT_F64;
   const size_t in_el = in64 ? 8 : 4;
   Buf staged(&al), conv(&al);
@@ -314,6 +317,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   tm.out = o.phase_ms;
   tm.st = st;
   std::vector<double> x2s(d, 0.0);
+  std::vector<double> ftail(d, -1.0);
   const W* C = A;
   Buf cbuf(&al);
   double normA2 = -1.0;
@@ -366,18 +370,21 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     Buf omega(&al), yb(&al), s1b(&al), w1b(&al), wb(&al), bb(&al), gy(&al), gwb(&al);
     int64_t r = 1, l = 0;
     bool small64 = false;
+    bool acc_gram = false;  // the factored Gram was formed with compensated sums
     const W* Zp = nullptr;
     const W* Wfin = nullptr;  // final sketch basis (sketch path)
     int64_t ldz = 0;
 
-    // Tight steps run entirely on the SIMT path: their tail estimates must be
-    // unbiased below FP32 rounding, which the tensor cores' accumulation is not.
+    // A tight step's range finding (Grams, sketch, projection) runs on the
+    // SIMT path: its tail estimates must be unbiased below FP32 rounding,
+    // which the tensor cores' accumulation is not.
     MM mm = mm_all;
     if (exact) {
       mm.tc = mm_all.tc && !tight(nb);
       TT_ALLOC(gb, (size_t)nb * nb * sizeof(double));
       TT_ALLOC(ws, std::max(mm_ws<W>(mm, nb, nb, no, true), ttk::small_ws_bytes((int)nb, true)));
       const bool acc = !W64 && tight(nb);
+      acc_gram = acc;
       tm.begin(s, TT_PH_GRAM);
       if (cfg.urv)
         TT_CK(mm_run<W>(mm, {C, n, false}, {C, n, true}, n, n, m, nullptr, 0, gb.as<double>(), true,
@@ -494,6 +501,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         const W* Wm = src_pass;
         Wfin = Wm;
         TT_ALLOC(bb, (size_t)no * l * sizeof(W));
+        acc_gram = !W64 && tight(l);
         tm.begin(s, TT_PH_PROJECT);
         if (cfg.urv)
           TT_CK(mm_run<W>(mm, {C, n, true}, {Wm, l, true}, m, l, n, bb.as<W>(), l, nullptr, false,
@@ -502,7 +510,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
           TT_CK(mm_run<W>(mm, {C, n, false}, {Wm, l, true}, n, l, m, bb.as<W>(), l, nullptr, false,
                           nullptr, ws.p, false, true, true, false), "project C^T W");
         TT_CK(mm_run<W>(mm, {bb.as<W>(), l, false}, {bb.as<W>(), l, true}, l, l, no, nullptr, 0,
-                        gy.as<double>(), true, nullptr, ws.p, !W64 && tight(l), true, true, false),
+                        gy.as<double>(), true, nullptr, ws.p, acc_gram, true, true, false),
               "Gram B^T B");
         // FP32 W is orthonormal only to ~1e-7, which biases ||X W||^2 and so
         // the range miss mu^2; with a tight tolerance the small factor
@@ -518,6 +526,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         prm.n = (int)l;
         prm.r_cap = (int)std::min<int64_t>(rcap, l);
         prm.x2_dev = x2_dev;
+        prm.range_exact = identity ? 1 : 0;
         prm.piv_tol = small64 ? 1e-15 : 1e-6;
         TT_ALLOC(zb, (size_t)l * l * sizeof(W));
         ldz = l;
@@ -550,6 +559,11 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
 
     if (first) normA2 = hinfo->normA2;
     x2s[s] = hinfo->x2;
+    // A tight step's tail from the small factor (compensated Gram, FP64
+    // factorization) resolves errors far below FP32 rounding; the difference
+    // ||C||^2 - ||carry||^2 is limited by the carry's own rounding (and by the
+    // tensor cores' accumulation drift, ~1e-6 of ||C||^2) and is used otherwise.
+    ftail[s] = (acc_gram && small64) ? hinfo->tail : -1.0;
     if (debug_trace())
       fprintf(stderr,
               "[ttutv] step k=%d %s m=%lld n=%lld l=%lld small=%s r=%d k1=%d nsteps=%d x2=%.6e "
@@ -561,7 +575,17 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     out->sketch_l[u - 1] = exact ? 0 : (int32_t)l;
     out->small_fp64[u - 1] = small64 ? 1 : 0;
 
-    // carry and core
+    // carry and core.  A tight step's carry and core may use the tensor
+    // cores again: neither enters this step's tail, and the next step forms
+    // its tail from the carry as stored (its sum of squares and its Gram), so
+    // a ~2^-22 relative error in the carry only adds ~2^-44 of its squared
+    // norm to that tail.
+    mm = mm_all;
+    // The next step's ||C||^2 is this carry's sum of squares.  The tensor-core
+    // epilogue sums each row's squares in FP32 (~u/sqrt(rows) relative); after
+    // a tight step the carry's squares are summed again exactly (FP64).
+    const bool sq_pass = mm.tc && acc_gram;
+    double* carry_sq = sq_pass ? nullptr : d_carry2 + s;
     const int64_t crow = cfg.urv ? m : r, ccol = cfg.urv ? r : n;
     TT_ALLOC(carry, (size_t)crow * ccol * sizeof(W));
     const int64_t corerows = cfg.urv ? r : m, corecols = cfg.urv ? n : r;
@@ -574,16 +598,17 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         wsz = std::max(cfg.urv ? mm_ws<W>(mm, m, r, l, false) : mm_ws<W>(mm, r, n, l, false),
                        cfg.urv ? mm_ws<W>(mm, r, n, l, false) : mm_ws<W>(mm, m, r, l, false));
       }
+      if (sq_pass) wsz = std::max(wsz, ttk::sumsq_ws_bytes(crow * ccol));
       TT_ALLOC(ws, wsz);
     }
     if (exact) {
       tm.begin(s, TT_PH_CARRY);
       if (cfg.urv)
         TT_CK(mm_run<W>(mm, {C, n, true}, {Zp, ldz, true}, m, r, n, carry.as<W>(), r, nullptr, false,
-                        d_carry2 + s, ws.p, false, true, true, false), "carry C Z1");
+                        carry_sq, ws.p, false, true, true, false), "carry C Z1");
       else
         TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {C, n, true}, r, n, m, carry.as<W>(), n, nullptr, false,
-                        d_carry2 + s, ws.p, false, true, true, false), "carry Z1^T C");
+                        carry_sq, ws.p, false, true, true, false), "carry Z1^T C");
       tm.end();
       tm.begin(s, TT_PH_CORE);
       if (cfg.urv)
@@ -597,10 +622,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       tm.begin(s, TT_PH_CARRY);
       if (cfg.urv)
         TT_CK(mm_run<W>(mm, {Bm, l, true}, {Zp, ldz, true}, m, r, l, carry.as<W>(), r, nullptr, false,
-                        d_carry2 + s, ws.p, false, true, true, false), "carry B Z1");
+                        carry_sq, ws.p, false, true, true, false), "carry B Z1");
       else
         TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {Bm, l, false}, r, n, l, carry.as<W>(), n, nullptr, false,
-                        d_carry2 + s, ws.p, false, true, true, false), "carry (B Z1)^T");
+                        carry_sq, ws.p, false, true, true, false), "carry (B Z1)^T");
       tm.end();
       tm.begin(s, TT_PH_CORE);
       if (cfg.urv)
@@ -611,6 +636,8 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
                         nullptr, ws.p, false, true, true, false), "core W Z1");
       tm.end();
     }
+    if (sq_pass)
+      TT_CK(ttk::sumsq(carry.p, W64, crow * ccol, d_carry2 + s, ws.p, st), "carry sum of squares");
     cores[k - 1] = core.release();
     if (cfg.urv)
       out->ranks[k - 1] = r;
@@ -638,7 +665,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   for (int s = 0; s < d - 1; ++s) {
     const int k = cfg.urv ? d - s : s + 1;
     const int u = cfg.urv ? k - 1 : k;
-    const double t = x2s[s] - h_carry2[s];
+    const double t = ftail[s] >= 0.0 ? ftail[s] : x2s[s] - h_carry2[s];
     out->tail_sq[u - 1] = t > 0.0 ? t : 0.0;
   }
   out->norm_sq = normA2;
@@ -671,6 +698,7 @@ tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims,
     return fail(TT_EINVAL, "bad small_precision");
   if (o.orth_precision < TT_SMALL_AUTO || o.orth_precision > TT_SMALL_FP64)
     return fail(TT_EINVAL, "bad orth_precision");
+  if (o.reverse != 0 && o.reverse != 1) return fail(TT_EINVAL, "reverse must be 0 or 1");
   if (o.weights) {
     double s = 0.0;
     for (int k = 0; k < d - 1; ++k) {
@@ -680,6 +708,84 @@ tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims,
     if (fabs(s - 1.0) > 1e-6) return fail(TT_EINVAL, "weights must satisfy sum w_k^2 = 1");
   }
   return TT_OK;
+}
+
+// reverse = 1 (the Remark after Thm 3.2): the sweep factors the index-reversed
+// tensor A'(i_d, ..., i_1) = A(i_1, ..., i_d) and its cores are read back as
+// cores of A -- core k of A is core d+1-k of A' with its two rank axes
+// swapped, so a right-to-left TT-URV of A' is a left-orthogonal TT of A.
+// Unfolding k of A' is the transpose of unfolding d-k of A: per-unfolding
+// weights, fixed ranks and results are mapped accordingly.
+tt_status run_reversed(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
+                       const int64_t* fixed, SweepCfg cfg, tt_opts o, Alloc& al,
+                       tt_result* out) {
+  cudaStream_t st = al.st;
+  const bool in64 = dtype == TT_F64;
+  const size_t el = in64 ? 8 : 4;
+  int64_t total = 1;
+  for (int k = 0; k < d; ++k) total *= dims[k];
+  Buf staged(&al), rev(&al);
+  const void* src = A;
+  if (host_pointer(A)) {
+    TT_ALLOC(staged, (size_t)total * el);
+    TT_CK(cudaMemcpyAsync(staged.p, A, (size_t)total * el, cudaMemcpyHostToDevice, st), "copy input");
+    src = staged.p;
+  }
+  TT_ALLOC(rev, (size_t)total * el);
+  TT_CK(ttk::reverse_modes(src, rev.p, in64, d, dims, st), "reverse modes");
+  staged.reset();
+  int64_t rdims[TT_MAXD], rfixed[TT_MAXD];
+  double rw[TT_MAXD];
+  for (int k = 0; k < d; ++k) rdims[k] = dims[d - 1 - k];
+  if (fixed)
+    for (int k = 0; k < d - 1; ++k) rfixed[k] = fixed[d - 2 - k];
+  if (o.weights) {
+    for (int k = 0; k < d - 1; ++k) rw[k] = o.weights[d - 2 - k];
+    o.weights = rw;
+  }
+  o.reverse = 0;
+  tt_result r;
+  const tt_status sr =
+      o.precision == TT_P_FP64
+          ? run_sweep<double>(rev.p, dtype, d, rdims, eps, fixed ? rfixed : nullptr, cfg, o, al, &r)
+          : run_sweep<float>(rev.p, dtype, d, rdims, eps, fixed ? rfixed : nullptr, cfg, o, al, &r);
+  if (sr != TT_OK) return sr;
+  rev.reset();
+
+  memset(out, 0, sizeof(*out));
+  out->d = d;
+  out->dtype = r.dtype;
+  out->orth = 1 - r.orth;
+  out->norm_sq = r.norm_sq;
+  for (int k = 0; k < d; ++k) out->dims[k] = dims[k];
+  for (int k = 0; k <= d; ++k) out->ranks[k] = r.ranks[d - k];
+  for (int k = 0; k < d - 1; ++k) {
+    out->tail_sq[k] = r.tail_sq[d - 2 - k];
+    out->delta_sq[k] = r.delta_sq[d - 2 - k];
+    out->sketch_l[k] = r.sketch_l[d - 2 - k];
+    out->small_fp64[k] = r.small_fp64[d - 2 - k];
+  }
+  const bool c64 = r.dtype == TT_F64;
+  const size_t cel = c64 ? 8 : 4;
+  tt_status sc = TT_OK;
+  for (int k = 0; k < d && sc == TT_OK; ++k) {
+    const int kr = d - 1 - k;  // core k of A is core kr of A'
+    const int64_t Ar = r.ranks[kr], Br = r.ranks[kr + 1];
+    void* c = al.get((size_t)Ar * dims[k] * Br * cel);
+    if (!c) {
+      sc = fail(TT_ENOMEM, "allocator returned NULL for a core");
+      break;
+    }
+    out->cores[k] = c;
+    const cudaError_t e = ttk::swap_outer(r.cores[kr], c, c64, Ar, dims[k], Br, st);
+    if (e != cudaSuccess) sc = cuda_fail(e, "core axes");
+  }
+  for (int k = 0; k < d; ++k) al.put(r.cores[k]);
+  if (sc != TT_OK) {
+    for (int k = 0; k < d; ++k) al.put(out->cores[k]);
+    memset(out, 0, sizeof(*out));
+  }
+  return sc;
 }
 
 tt_status sweep_entry(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
@@ -694,6 +800,7 @@ tt_status sweep_entry(const void* A, int32_t dtype, int32_t d, const int64_t* di
   if ((alloc == nullptr) != (free_fn == nullptr))
     return fail(TT_EINVAL, "alloc and free must both be given or both be NULL");
   Alloc al{alloc, free_fn, ctx, (cudaStream_t)stream};
+  if (o.reverse) return run_reversed(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
   if (o.precision == TT_P_FP64)
     return run_sweep<double>(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
   return run_sweep<float>(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
@@ -815,6 +922,70 @@ tt_status tt_full(int32_t d, const int64_t* dims, const int64_t* ranks, const vo
     cur = nxt;
     rows *= dims[k];
   }
+  return TT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Slab of the first mode for tt_rse: as many slices as fit in 2^24 entries
+// (at least one).
+int64_t rse_slab_rows(int32_t d, const int64_t* dims) {
+  int64_t p = 1;
+  for (int k = 1; k < d; ++k) p *= dims[k];
+  return std::max<int64_t>(1, std::min<int64_t>(dims[0], ((int64_t)1 << 24) / std::max<int64_t>(1, p)));
+}
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace
+
+extern "C" {
+
+size_t tt_rse_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks, int32_t dtype) {
+  if (d < 2 || d > TT_MAXD || !dims || !ranks) return 0;
+  const size_t el = dtype == TT_F64 ? 8 : 4;
+  int64_t sd[TT_MAXD];
+  for (int k = 0; k < d; ++k) sd[k] = dims[k];
+  sd[0] = rse_slab_rows(d, dims);
+  int64_t n = 1;
+  for (int k = 0; k < d; ++k) n *= sd[k];
+  return align256((size_t)n * el) + align256(tt_full_work_bytes(d, sd, ranks, dtype)) +
+         align256(ttk::diff_sumsq_parts_bytes());
+}
+
+tt_status tt_rse(int32_t d, const int64_t* dims, const int64_t* ranks, const void* const* cores,
+                 int32_t dtype, const void* A, void* work, double* out, void* stream) {
+  g_err.clear();
+  if (d < 2 || d > TT_MAXD || !dims || !ranks || !cores || !A || !work || !out)
+    return fail(TT_EINVAL, "bad argument");
+  if (dtype != TT_F32 && dtype != TT_F64) return fail(TT_EINVAL, "bad dtype");
+  for (int k = 0; k < d; ++k)
+    if (dims[k] < 1 || ranks[k + 1] < 1 || !cores[k]) return fail(TT_EINVAL, "bad dims/ranks/cores");
+  if (ranks[0] != 1 || ranks[d] != 1) return fail(TT_EINVAL, "r_0 and r_d must be 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool f64 = dtype == TT_F64;
+  const size_t el = f64 ? 8 : 4;
+  const int64_t s1 = rse_slab_rows(d, dims);
+  int64_t p = 1;
+  for (int k = 1; k < d; ++k) p *= dims[k];
+  int64_t sd[TT_MAXD];
+  for (int k = 0; k < d; ++k) sd[k] = dims[k];
+  sd[0] = s1;
+  char* chunk = (char*)work;
+  char* fw = chunk + align256((size_t)(s1 * p) * el);
+  double* part = (double*)(fw + align256(tt_full_work_bytes(d, sd, ranks, dtype)));
+  const void* sc[TT_MAXD];
+  for (int k = 1; k < d; ++k) sc[k] = cores[k];
+  for (int64_t a = 0; a < dims[0]; a += s1) {
+    sd[0] = std::min<int64_t>(s1, dims[0] - a);
+    // core 1 is [1][I_1][r_1]: slices a .. a + sd[0] - 1 start at row a
+    sc[0] = (const char*)cores[0] + (size_t)a * ranks[1] * el;
+    const tt_status s = tt_full(d, sd, ranks, sc, dtype, chunk, fw, stream);
+    if (s != TT_OK) return s;
+    TT_CK(ttk::diff_sumsq((const char*)A + (size_t)(a * p) * el, chunk, f64, sd[0] * p, part, a == 0,
+                          st),
+          "difference sums");
+  }
+  TT_CK(ttk::sum_pairs(part, out, st), "difference totals");
   return TT_OK;
 }
 

@@ -82,6 +82,7 @@ struct SmallParams {
   double piv_tol;         // relative pivot tolerance of the (pivoted) Cholesky
   double shift_rel;       // SM_ORTH: diagonal shift, relative to trace(G)
   const double* Gw;       // QLP/Jacobi on a sketch: W^T W of the range basis, or null
+  int range_exact;        // 1: the sketch is the identity, so W spans X's row space (mu^2 = 0)
 };
 size_t small_ws_bytes(int n, bool fp64);
 // Register-resident fast path (small_fast.cu) for SM_QLP / SM_ORTH with
@@ -102,6 +103,19 @@ cudaError_t copy2d(const void* in, int64_t ldi, bool trans, void* out, int64_t l
                    int64_t cols, bool fp64, cudaStream_t st);
 size_t sumsq_ws_bytes(int64_t n);
 cudaError_t sumsq(const void* x, bool fp64, int64_t n, double* out, void* ws, cudaStream_t st);
+// out = in with its d modes in reverse order (dims are in's mode sizes).
+cudaError_t reverse_modes(const void* in, void* out, bool fp64, int d, const int64_t* dims,
+                          cudaStream_t st);
+// out[b][i][a] = in[a][i][b] for an [A][I][B] array.
+cudaError_t swap_outer(const void* in, void* out, bool fp64, int64_t A, int64_t I, int64_t B,
+                       cudaStream_t st);
+// Streamed ||A - X||^2 and ||A||^2 in FP64 over slabs: part (diff_sumsq_parts_bytes())
+// is started by the first slab (first = true) and accumulated by the later ones;
+// sum_pairs writes the two totals to out[0], out[1].
+size_t diff_sumsq_parts_bytes();
+cudaError_t diff_sumsq(const void* a, const void* x, bool fp64, int64_t n, double* part,
+                       bool first, cudaStream_t st);
+cudaError_t sum_pairs(const double* part, double* out, cudaStream_t st);
 cudaError_t eval_at(int d, const int64_t* dims, const int64_t* ranks, const float* const* cores,
                     const int64_t* idx, int64_t n, float* out, cudaStream_t st);
 cudaError_t eval_at_backward(int d, const int64_t* dims, const int64_t* ranks,

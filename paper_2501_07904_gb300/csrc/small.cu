@@ -225,7 +225,9 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
     normA2 = prm.normA2_is_trace ? tr : *prm.normA2_dev;
     delta2 = prm.delta2_scale * normA2;
   }
-  const double mu2 = prm.x2_dev ? fmax(0.0, x2 - tr) : 0.0;
+  // range miss mu^2 = ||X||^2 - ||X P_W||^2; zero by construction when W
+  // spans the whole row space (Omega = I), where the difference is rounding
+  const double mu2 = (prm.x2_dev && !prm.range_exact) ? fmax(0.0, x2 - tr) : 0.0;
   const bool finite = isfinite(tr) && isfinite(x2) && (normA2 < 0.0 || isfinite(normA2));
   if (tid == 0) {
     info->x2 = x2;

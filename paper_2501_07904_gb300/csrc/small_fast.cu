@@ -668,7 +668,9 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
         if (tile_r<T>(i) == tile_c(jj)) t2 += (double)a[i][jj];
     tr = block_sum(t2, redd);
   }
-  const double mu2 = prm.x2_dev ? fmax(0.0, x2 - tr) : 0.0;
+  // range miss mu^2 = ||X||^2 - ||X P_W||^2; zero by construction when W
+  // spans the whole row space (Omega = I), where the difference is rounding
+  const double mu2 = (prm.x2_dev && !prm.range_exact) ? fmax(0.0, x2 - tr) : 0.0;
 
   // phase 1: pivoted Cholesky of G
   const int k1 = chol_rl<false>(a, b, n, prm.piv_tol, 0, 0.0, 0.0, 0, n, R1, (T*)nullptr,

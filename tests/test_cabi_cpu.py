@@ -85,3 +85,33 @@ def test_full_work_bytes(L):
     n = L.tt_full_work_bytes(3, tu._i64([4, 5, 6]), tu._i64([1, 2, 3, 1]), 0)
     assert n >= 2 * 4 * 5 * 3 * 4
     assert L.tt_full_work_bytes(1, tu._i64([4]), tu._i64([1, 1]), 0) == 0
+
+
+def test_reverse_option(L):
+    o = tu.tt_opts()
+    L.tt_opts_default(ctypes.byref(o))
+    assert o.reverse == 0
+    o.reverse = 2
+    assert _call(L, opts=ctypes.byref(o)) == 1
+
+
+def test_rse_arguments_and_work_bytes(L):
+    dims, ranks = tu._i64([300, 256, 256]), tu._i64([1, 6, 5, 1])
+    ptrs = (ctypes.c_void_p * 3)(1, 1, 1)
+    out = ctypes.c_void_p(1)
+    # NULL A, NULL work, NULL out, d = 1, r_0 != 1: rejected before any device work
+    assert L.tt_rse(3, dims, ranks, ptrs, 0, None, ctypes.c_void_p(1), out, None) == 1
+    assert L.tt_rse(3, dims, ranks, ptrs, 0, ctypes.c_void_p(1), None, out, None) == 1
+    assert L.tt_rse(3, dims, ranks, ptrs, 0, ctypes.c_void_p(1), ctypes.c_void_p(1), None, None) == 1
+    assert L.tt_rse(1, dims, ranks, ptrs, 0, ctypes.c_void_p(1), ctypes.c_void_p(1), out, None) == 1
+    assert L.tt_rse(3, dims, tu._i64([2, 6, 5, 1]), ptrs, 0, ctypes.c_void_p(1),
+                    ctypes.c_void_p(1), out, None) == 1
+    # scratch: a slab of 256 first-mode slices (2^24 entries) plus the contraction's scratch
+    n32 = L.tt_rse_work_bytes(3, dims, ranks, 0)
+    n64 = L.tt_rse_work_bytes(3, dims, ranks, 1)
+    assert n32 >= 256 * 256 * 256 * 4 and n64 >= 256 * 256 * 256 * 8
+    assert n32 < 3 * 256 * 256 * 256 * 4
+    # one slice of the first mode larger than a slab: the slab is that slice
+    big = L.tt_rse_work_bytes(3, tu._i64([2, 4096, 4200]), tu._i64([1, 2, 2, 1]), 0)
+    assert 4096 * 4200 * 4 <= big < 2 * 4096 * 4200 * 4
+    assert L.tt_rse_work_bytes(1, tu._i64([4]), tu._i64([1, 1]), 0) == 0

@@ -8,7 +8,8 @@ cores.  Tolerance 5e-5 relative to ||A||_F: the range-finding products
 their operands to TF32 (2^-11), which tilts the kept subspace by a few 1e-6
 on these spectra; every product that becomes part of the result carries its
 operands as two TF32 terms (~2^-22).  Tight steps (eps^2 w_k^2 below
-2 n u_fp32) run on the FP32 path and so match it bit for bit.
+2 n u_fp32) find their range on the FP32 path and form their carries and
+cores on the tensor cores; they are held to the FP32 tolerance.
 """
 import os
 
@@ -17,7 +18,8 @@ import pytest
 import torch
 
 import synth
-from test_gpu_parity import check_against_oracle, check_gold, np_cores, run_gpu
+from test_gpu_parity import (check_against_oracle, check_gold, check_tight_tails, np_cores,
+                             run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -62,14 +64,15 @@ def test_mixed_deterministic(tu):
     assert a.tail_sq == b.tail_sq
 
 
-def test_mixed_tight_steps_are_fp32(tu):
-    # eps = 1e-3 on 32^5 makes every step tight: mixed equals FP32 exactly
-    A = torch.from_numpy(np.ascontiguousarray(synth.make_config("c3"))).cuda()
-    a = tu.tt_utv(A, eps=1e-3, precision="mixed")
-    b = tu.tt_utv(A, eps=1e-3, precision="fp32")
-    assert a.ranks == b.ranks == [1, 20, 20, 20, 20, 1]
-    for x, y in zip(a.cores, b.cores):
-        assert torch.equal(x, y)
+@pytest.mark.parametrize("method", ["URV", "ULV"])
+def test_mixed_c3_tight_steps(tu, method):
+    # eps = 1e-3 on 32^5 makes every step tight: Grams, sketches and
+    # projections run on the SIMT path, carries and cores on the tensor cores
+    # with split operands; held to the FP32 tolerance
+    A = synth.make_config("c3")
+    res = check_gold(tu, A, method, f"c3_{method}", 1e-5, 1e-3, precision="mixed")
+    assert res.ranks == [1, 20, 20, 20, 20, 1]
+    check_tight_tails(tu, A, res, method, "c3")
 
 
 def test_mixed_c5_128pow4(tu):

@@ -258,6 +258,25 @@ def test_c3_32pow5(tu, method):
     A = synth.make_config("c3")
     res = check_gold(tu, A, method, f"c3_{method}", 1e-5, 1e-3, precision="fp32")
     assert res.ranks == [1, 20, 20, 20, 20, 1]
+    check_tight_tails(tu, A, res, method, "c3")
+
+
+def check_tight_tails(tu, A, res, method, name):
+    """Every step of c3 is tight: its reported errors come from compensated
+    Grams and FP64 factorizations.  The first step's (an exact Gram step)
+    matches the oracle's to 1e-3 relative, far below FP32 rounding of ||A||^2.
+    The sum matches ||A - A_TT||^2 (Thm 3.1/3.2) to 25% plus the floor of the
+    sketched steps' estimates: their range miss ||C||^2 - ||C W||^2 carries
+    the FP32 rounding of B = C W, about u_fp32 sqrt(2 / entries of B) of
+    ||C||^2 (4e-9 of ||A||^2 for the 32 x 32 B of the last step), against
+    tolerances delta_k^2 of 2.5e-7 ||A||^2."""
+    g = load_gold(f"{name}_{method}")
+    normA2 = float(g["normA2"])
+    first = len(res.tail_sq) - 1 if method == "URV" else 0
+    t, t_ref = res.tail_sq[first], float(g["tails"][first])
+    assert abs(t - t_ref) <= 1e-3 * t_ref + 1e-13 * normA2, (t, t_ref)
+    err2, _ = tu.tt_rse(torch.from_numpy(np.ascontiguousarray(A)).cuda(), res.cores)
+    assert abs(sum(res.tail_sq) - err2) <= 0.25 * err2 + 1e-8 * normA2, (res.tail_sq, err2)
 
 
 def test_c5_128pow4(tu):
