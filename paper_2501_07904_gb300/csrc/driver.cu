@@ -936,6 +936,22 @@ int64_t rse_slab_rows(int32_t d, const int64_t* dims) {
   return std::max<int64_t>(1, std::min<int64_t>(dims[0], ((int64_t)1 << 24) / std::max<int64_t>(1, p)));
 }
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+// Contraction scratch of tt_rse: the larger of a full slab's and the last
+// (ragged) slab's -- a smaller product may split its inner dimension and so
+// need more scratch.
+size_t rse_full_work(int32_t d, const int64_t* dims, const int64_t* ranks, int32_t dtype,
+                     int64_t s1) {
+  int64_t sd[TT_MAXD];
+  for (int k = 0; k < d; ++k) sd[k] = dims[k];
+  sd[0] = s1;
+  size_t w = tt_full_work_bytes(d, sd, ranks, dtype);
+  const int64_t last = dims[0] % s1;
+  if (last) {
+    sd[0] = last;
+    w = std::max(w, tt_full_work_bytes(d, sd, ranks, dtype));
+  }
+  return w;
+}
 }  // namespace
 
 extern "C" {
@@ -943,12 +959,10 @@ extern "C" {
 size_t tt_rse_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks, int32_t dtype) {
   if (d < 2 || d > TT_MAXD || !dims || !ranks) return 0;
   const size_t el = dtype == TT_F64 ? 8 : 4;
-  int64_t sd[TT_MAXD];
-  for (int k = 0; k < d; ++k) sd[k] = dims[k];
-  sd[0] = rse_slab_rows(d, dims);
-  int64_t n = 1;
-  for (int k = 0; k < d; ++k) n *= sd[k];
-  return align256((size_t)n * el) + align256(tt_full_work_bytes(d, sd, ranks, dtype)) +
+  const int64_t s1 = rse_slab_rows(d, dims);
+  int64_t n = s1;
+  for (int k = 1; k < d; ++k) n *= dims[k];
+  return align256((size_t)n * el) + align256(rse_full_work(d, dims, ranks, dtype, s1)) +
          align256(ttk::diff_sumsq_parts_bytes());
 }
 
@@ -972,7 +986,7 @@ tt_status tt_rse(int32_t d, const int64_t* dims, const int64_t* ranks, const voi
   sd[0] = s1;
   char* chunk = (char*)work;
   char* fw = chunk + align256((size_t)(s1 * p) * el);
-  double* part = (double*)(fw + align256(tt_full_work_bytes(d, sd, ranks, dtype)));
+  double* part = (double*)(fw + align256(rse_full_work(d, dims, ranks, dtype, s1)));
   const void* sc[TT_MAXD];
   for (int k = 1; k < d; ++k) sc[k] = cores[k];
   for (int64_t a = 0; a < dims[0]; a += s1) {

@@ -115,3 +115,14 @@ def test_rse_arguments_and_work_bytes(L):
     big = L.tt_rse_work_bytes(3, tu._i64([2, 4096, 4200]), tu._i64([1, 2, 2, 1]), 0)
     assert 4096 * 4200 * 4 <= big < 2 * 4096 * 4200 * 4
     assert L.tt_rse_work_bytes(1, tu._i64([4]), tu._i64([1, 1]), 0) == 0
+
+
+def test_rse_work_covers_the_ragged_slab(L):
+    # slabs of 1024 first-mode slices and a last one of 276: a smaller
+    # contraction may split its inner dimension, so both sizes must fit
+    dims, ranks = [1300, 128, 128], [1, 256, 128, 1]
+    w = L.tt_rse_work_bytes(3, tu._i64(dims), tu._i64(ranks), 0)
+    slab = 1024 * 128 * 128 * 4
+    for rows in (1024, 276):
+        need = L.tt_full_work_bytes(3, tu._i64([rows, 128, 128]), tu._i64(ranks), 0)
+        assert w >= slab + need
