@@ -51,17 +51,25 @@ def sketch_size(n_basis, n_other, r_prev, p=OVERSAMPLE, fixed_r=None):
     return int(min(l, n_basis, n_other))
 
 
-def range_step(X, l, seed, step):
+def range_step(X, l, seed, step, q=0):
     """Range of the basis side of X (N_o x N_b): returns (W, B, mu2).
 
-    l >= N_o uses Omega = I (the sketch then spans the whole row space);
-    otherwise Omega is the Philox Rademacher matrix of this step.
+    l >= N_o uses Omega = I (the sketch then spans the whole row space, and
+    power iterations change nothing); otherwise Omega is the Philox
+    Rademacher matrix of this step and Y = X^T Omega is followed by q power
+    (subspace) iterations Y <- X^T X Q, Q an orthonormal basis of the previous
+    Y, so that span(Y) = span((X^T X)^q X^T Omega) with the weak directions
+    damped by the squared singular values (the randomized range finder the
+    paper's randUTV reference builds on).
     """
     n_o, n_b = X.shape
     if l >= n_o:
         Y = X.T.copy()
     else:
         Y = X.T @ rademacher(n_o, l, seed, step)
+        for _ in range(q):
+            Q, _, _ = householder_qr(Y)
+            Y = X.T @ (X @ Q)
     W, _, _ = householder_qr(Y)
     B = X @ W
     E = X - B @ W.T
@@ -116,7 +124,7 @@ def choose_rank(tails, delta2, r_fixed, r_max):
 
 
 def factor_step(X, delta2, r_fixed, r_prev, seed, step, kind="qlp",
-                l_full=L_FULL, p=OVERSAMPLE):
+                l_full=L_FULL, p=OVERSAMPLE, q=0):
     """One truncated UTV of X (N_o x N_b, basis on the column side).
 
     Returns dict(r, basis (N_b x r), carry (N_o x r) = X basis, tail, l, path).
@@ -134,7 +142,7 @@ def factor_step(X, delta2, r_fixed, r_prev, seed, step, kind="qlp",
         path = "sketch"
     while True:
         if path == "sketch":
-            W, B, mu2 = range_step(X, l, seed, step)
+            W, B, mu2 = range_step(X, l, seed, step, q)
         if kind == "qlp":
             Z, L, _ = qlp(B)
             tails = mu2 + qlp_tails(L)
@@ -168,7 +176,7 @@ def _weights(d, weights):
 
 
 def tt_sweep(A, eps=None, ranks=None, variant="URV", kind="qlp", direction=None,
-             weights=None, l_full=L_FULL, p=OVERSAMPLE, seed=0):
+             weights=None, l_full=L_FULL, p=OVERSAMPLE, seed=0, q=0):
     """TT decomposition by a sweep of truncated UTVs.
 
     variant 'URV' -> right-to-left (Alg. 3), right-orthogonal cores;
@@ -209,7 +217,7 @@ def tt_sweep(A, eps=None, ranks=None, variant="URV", kind="qlp", direction=None,
             C = C.reshape(m, n)
             u = k - 1
             st = factor_step(C, delta2_of(u) if eps is not None else 0.0, fixed_of(u), r_prev,
-                             seed, k, kind, l_full, p)
+                             seed, k, kind, l_full, p, q)
             r = st["r"]
             cores[k - 1] = st["basis"].T.reshape(r, dims[k - 1], r_next)
             C = st["carry"]
@@ -228,7 +236,7 @@ def tt_sweep(A, eps=None, ranks=None, variant="URV", kind="qlp", direction=None,
             C = C.reshape(m, n)
             u = k
             st = factor_step(C.T, delta2_of(u) if eps is not None else 0.0, fixed_of(u), r_prev,
-                             seed, k, kind, l_full, p)
+                             seed, k, kind, l_full, p, q)
             r = st["r"]
             cores[k - 1] = st["basis"].reshape(r_left, dims[k - 1], r)
             C = st["carry"].T

@@ -192,6 +192,46 @@ def test_sketch_path_is_exact_when_l_covers_rank():
     np.testing.assert_allclose(tt.tt_full(a["cores"]), tt.tt_full(b["cores"]), atol=1e-7)
 
 
+@pytest.mark.parametrize("q", [1, 2])
+def test_power_iterations_span_the_closed_form(q):
+    # span(Y) after q power iterations = span(V S^{2q+1} U^T Omega) for
+    # X = U S V^T: the re-orthonormalizations between them change no span.
+    # X has a slowly decaying spectrum (1 .. 0.05), where iterations matter.
+    rng = np.random.default_rng(31)
+    n_o, n_b, l = 90, 70, 12
+    U, _ = np.linalg.qr(rng.standard_normal((n_o, n_b)))
+    V, _ = np.linalg.qr(rng.standard_normal((n_b, n_b)))
+    s = np.geomspace(1.0, 0.05, n_b)
+    X = (U * s) @ V.T
+    W, B, mu2 = tt.range_step(X, l, seed=3, step=2, q=q)
+    from oracle.philox import rademacher
+    Om = rademacher(n_o, l, 3, 2)
+    Q_ref, _ = np.linalg.qr((V * s ** (2 * q + 1)) @ (U.T @ Om))
+    cosines = np.linalg.svd(W.T @ Q_ref, compute_uv=False)
+    assert np.all(cosines > 1 - 1e-10), cosines.min()
+    np.testing.assert_allclose(W.T @ W, np.eye(l), atol=1e-13)
+    np.testing.assert_allclose(B, X @ W, atol=1e-13)
+    assert mu2 == pytest.approx(np.sum((X - B @ W.T) ** 2), rel=1e-12)
+    # q = 0 is the plain sketch, which misses more of X on this spectrum
+    _, _, mu2_0 = tt.range_step(X, l, seed=3, step=2, q=0)
+    assert mu2 < mu2_0
+
+
+def test_power_iterations_keep_exactness_and_identity():
+    # l >= rank: every q gives the exact-path ranks and tensor; Omega = I: q ignored
+    A = synth.gaussian_tt((8, 8, 8, 8), (1, 3, 5, 3, 1), rel_noise=1e-9, seed=19, dtype=np.float64)
+    a = tt.tt_utv(A, eps=1e-6, variant="URV")
+    for q in (1, 2):
+        b = tt.tt_utv(A, eps=1e-6, variant="URV", l_full=4, q=q)
+        assert b["ranks"] == a["ranks"] == [1, 3, 5, 3, 1]
+        np.testing.assert_allclose(tt.tt_full(a["cores"]), tt.tt_full(b["cores"]), atol=1e-7)
+    X = np.random.default_rng(5).standard_normal((6, 40))
+    W0, _, m0 = tt.range_step(X, 6, seed=0, step=1, q=0)
+    W2, _, m2 = tt.range_step(X, 6, seed=0, step=1, q=2)
+    np.testing.assert_array_equal(W0, W2)
+    assert m0 == m2
+
+
 def test_sketch_grows_when_too_small():
     # rank 40 at the sketched step but the first sketch has l = 32 columns
     A = synth.gaussian_tt((50, 50, 50), (1, 40, 40, 1), rel_noise=1e-10, seed=20, dtype=np.float64)
