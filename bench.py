@@ -249,12 +249,8 @@ def run_ours(args, wl, rank, world):
         wall = time.perf_counter() - t0
     barrier()
     launches = tu.kernel_launches() - l0
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nbytes / (ms * 1e-3) / 1e9
+    ms = slowest_ms(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    value = job_gbs(nbytes, world, ms)
     clocks = clk.summary()
     phases = [{k: v / args.steps for k, v in p.items()} for p in phase_sum]
 
@@ -312,12 +308,8 @@ def run_ours(args, wl, rank, world):
                 o.copy_(c, non_blocking=True)
         e1.record(st)
         torch.cuda.synchronize()
-        ms_e2e = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            t = torch.tensor([ms_e2e], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": round(world * nbytes / (ms_e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
+        ms_e2e = slowest_ms(e0.elapsed_time(e1) / args.steps, world, dev)
+        e2e = {"value": round(job_gbs(nbytes, world, ms_e2e), 2), "unit": "GB/s",
                "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": int(nbytes),
                "d2h_bytes_per_step": int(core_bytes)}
 
@@ -334,10 +326,10 @@ def run_ours(args, wl, rank, world):
             r32 = tu.tt_utv(A, **kw32)
         c1.record(st)
         torch.cuda.synchronize()
-        ms32 = c0.elapsed_time(c1) / args.steps
+        ms32 = slowest_ms(c0.elapsed_time(c1) / args.steps, world, dev)
         acc32 = accuracy(tu, torch, A, r32, args.workload)
         compare = {"precision": "fp32", "ms_per_step": round(ms32, 4),
-                   "value": round(world * nbytes / (ms32 * 1e-3) / 1e9, 2), "unit": "GB/s",
+                   "value": round(job_gbs(nbytes, world, ms32), 2), "unit": "GB/s",
                    "speedup_of_mixed": round(ms32 / ms, 3), "accuracy": acc32}
 
     cpu = None
@@ -360,6 +352,23 @@ def run_ours(args, wl, rank, world):
         "wall_s": round(wall, 3),
     }
     return out
+
+
+def slowest_ms(ms, world, device):
+    """Max over ranks of a per-rank time (ms): the job is as slow as its
+    slowest replica."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(nbytes, world, ms):
+    """Whole-job tensor GB/s: each of `world` replicas decomposes its own
+    `nbytes` tensor, the slowest in `ms` milliseconds."""
+    return world * nbytes / (ms * 1e-3) / 1e9
 
 
 def l2_note(wl):
