@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "TT-UTV sweep tensor GB/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz max clock / 1e3
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1e3  # 152 SMs x 128 FP32 lanes x FMA (2 flop) x 2.07 GHz
 
 L2_BYTES = 129 * 10**6
 
@@ -176,7 +176,7 @@ def ncu_traffic(kernel_key, workload):
     return None if ent is None else ent.get("traffic_bytes")
 
 
-def phase_model(wl, res):
+def phase_model(wl, res, precision="mixed"):
     """Algorithmic bytes and flops of the streaming products of every step of
     the right-to-left sweep, keyed (step, phase).  Step s factors unfolding
     C (m x n), m = I_1...I_{k-1}, n = I_k r_k, k = d - s: an exact step reads C
@@ -194,6 +194,10 @@ def phase_model(wl, res):
         l = res.sketch_l[k - 2]
         if l == 0:
             out[(s, "gram")] = dict(bytes=4.0 * m * n, flops=float(m) * n * (n + 1))
+            if precision != "fp64" and res.small_fp64[k - 2]:
+                # a tight step's Gram: compensated sums of exact products on
+                # the FP32 pipes, 10 FP32 instructions per product (symmetric half)
+                out[(s, "gram")]["fp32_instr"] = 10.0 * m * n * (n + 1) / 2
             out[(s, "carry")] = dict(bytes=4.0 * m * n + 4.0 * m * r, flops=2.0 * m * n * r)
         else:
             out[(s, "sketch")] = dict(bytes=4.0 * m * n + 4.0 * n * l, flops=2.0 * m * n * l)
@@ -255,7 +259,7 @@ def run_ours(args, wl, rank, world):
     phases = [{k: v / args.steps for k, v in p.items()} for p in phase_sum]
 
     # roofline of the dominant streaming product (largest modeled phase time)
-    model = phase_model(wl, res)
+    model = phase_model(wl, res, args.precision)
     peaks, peak_src = measured_peaks()
     roof = None
     timed = [(sk, phases[sk[0]].get(sk[1], 0.0)) for sk in model]
@@ -276,9 +280,18 @@ def run_ours(args, wl, rank, world):
             c_name = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
             c_bound = "alu"
         f_c = tfl / c_peak
+        if "fp32_instr" in mm:
+            # compensated Gram: bound by FP32 instruction issue, 152 SMs x 128
+            # lanes x 2.07 GHz = 40.3 T lane-instructions/s
+            c_peak = FP32_PEAK_TFLOPS / 2
+            tfl = mm["fp32_instr"] / (dom_ms * 1e-3) / 1e12
+            c_name = "FP32 issue: 152 SMs x 128 lanes x 2.07 GHz (lane-instructions)"
+            c_bound = "alu"
+            f_c = tfl / c_peak
         if f_c > f_hbm:
             roof = {"bound": c_bound, "achieved": round(tfl, 2), "peak": round(c_peak, 1),
-                    "unit": "TFLOP/s", "frac": round(f_c, 4), "peak_source": c_name,
+                    "unit": "Tinstr/s" if "fp32_instr" in mm else "TFLOP/s",
+                    "frac": round(f_c, 4), "peak_source": c_name,
                     "hbm_frac": round(f_hbm, 4), "hbm_gbs": round(gbs, 1)}
         else:
             roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
