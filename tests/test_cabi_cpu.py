@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2501_07904_gb300 as tu
@@ -126,3 +127,31 @@ def test_rse_work_covers_the_ragged_slab(L):
     for rows in (1024, 276):
         need = L.tt_full_work_bytes(3, tu._i64([rows, 128, 128]), tu._i64(ranks), 0)
         assert w >= slab + need
+
+
+@pytest.mark.parametrize("reverse", [0, 1])
+def test_allocator_failure_reports_enomem(L, reverse):
+    # a host input is staged through the caller's allocator first; an
+    # allocator that returns NULL ends the call with TT_ENOMEM before any
+    # device work (no GPU needed)
+    calls = []
+
+    def alloc(nbytes, stream, ctx):
+        calls.append(nbytes)
+        return None
+
+    def free(p, stream, ctx):
+        raise AssertionError("nothing was allocated")
+
+    af, ff = tu.ALLOC_FN(alloc), tu.FREE_FN(free)
+    A = np.ones((4, 5, 6), np.float32)
+    o = tu.tt_opts()
+    L.tt_opts_default(ctypes.byref(o))
+    o.reverse = reverse
+    res = tu.tt_result()
+    st = L.tt_utv(ctypes.c_void_p(A.ctypes.data), 0, 3, tu._i64(A.shape), 0.1, None, 0, 0,
+                  ctypes.byref(o), af, ff, None, None, ctypes.byref(res))
+    assert st == 3                                   # TT_ENOMEM
+    assert b"allocator returned NULL" in L.tt_last_error()
+    assert calls and calls[0] >= A.nbytes
+    assert all(res.cores[k] is None for k in range(3))
