@@ -152,7 +152,12 @@ typedef struct {
  *              rank above the size of its unfolding is clamped; the ranks
  *              actually used are returned.
  *   variant/direction  TT_URV with TT_RL (Alg. 3) or TT_ULV with TT_LR
- *              (Alg. 1/2).  The other two pairings return TT_EUNSUPPORTED.
+ *              (Alg. 1/2).  TT_ULV with TT_RL is the appendix's Alg. 4 with
+ *              the middle block [L_11; L_21] kept (its first case, for which
+ *              the bounds of Thm 3.1 / Cor. 3.1 hold); with the pivoted-QLP
+ *              inner factor it computes exactly the TT_URV / TT_RL sweep, and
+ *              TT_URV with TT_LR ([R_11 R_12] kept) exactly the TT_ULV / TT_LR
+ *              one.  Alg. 4's cheaper L_11-only carry is not built.
  *   opts       host, may be NULL (defaults).
  * Each unfolding step: if the basis side (columns for URV, rows for ULV) has
  * at most l_full entries, its Gram matrix is factored exactly; otherwise a

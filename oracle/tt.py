@@ -315,3 +315,83 @@ def tt_eval_grad(cores, lin_idx, gout):
         g[:] = gt.transpose(1, 0, 2)
         grads.append(g)
     return grads
+
+
+def tt_ulv_rl(A, eps=None, ranks=None, lhat="l11", l_full=L_FULL, p=OVERSAMPLE, seed=0, q=0):
+    """TT-ULV in a right-to-left sweep (the appendix's Alg. 4): right-orthogonal cores.
+
+    Unfolding C_k (I_1..I_{k-1} x I_k r_k) is approximated through the ULV form
+    of the pivoted QLP of its range-projected matrix, C ~ U L V^T with
+    U = Q_1 Pi_2, L lower trapezoidal, V = W Z; the new core is V_1^T.
+    The appendix's two choices of the kept middle block:
+
+    * lhat = "l11" (Alg. 4 as printed): carry U_1 L_11.  Its residual
+      U_2 L_21 V_1^T + U_2 L_22 V_2^T is not orthogonal to V_1, so
+      ||C - U_1 L_11 V_1^T||^2 = mu^2 + ||L||^2 - ||L_11||^2 and the errors of the
+      sweep add in norm (the appendix's Proposition: ||A - A_hat|| <= sum eps_k);
+      a prescribed accuracy uses eps_k = eps ||A||_F / (d-1).
+    * lhat = "full": carry U L(:, 1:r) = U_1 L_11 + U_2 L_21 = C V_1, residual
+      U_2 L_22 V_2^T orthogonal to V_1 (error mu^2 + ||L_22||^2), for which
+      results like Thm 3.1 / Cor. 3.1 hold: eps_k = eps ||A||_F / sqrt(d-1).
+    """
+    assert lhat in ("l11", "full")
+    A = np.asarray(A, dtype=np.float64)
+    dims = A.shape
+    d = len(dims)
+    assert d >= 2 and (eps is None) != (ranks is None)
+    normA2 = float(np.sum(A * A))
+    if eps is None:
+        delta2 = None
+    elif lhat == "l11":
+        delta2 = (eps / (d - 1)) ** 2 * normA2
+    else:
+        delta2 = eps ** 2 / (d - 1) * normA2
+    cores = [None] * d
+    rk = [1] * (d + 1)
+    tails = [0.0] * (d - 1)
+    C = A.reshape(-1, dims[-1])
+    r_next, r_prev = 1, 0
+    for k in range(d, 1, -1):
+        m = int(np.prod(dims[: k - 1]))
+        n = dims[k - 1] * r_next
+        C = C.reshape(m, n)
+        r_fixed = None if ranks is None else int(ranks[k - 2])
+        exact = n <= l_full
+        l = n if exact else sketch_size(n, m, r_prev, p, r_fixed)
+        while True:
+            if exact:
+                W, B, mu2 = None, C, 0.0
+            else:
+                W, B, mu2 = range_step(C, l, seed, k, q)
+            Z, L, U = qlp(B)
+            kk = L.shape[0]
+            if lhat == "full":
+                tl = mu2 + qlp_tails(L)
+            else:
+                tot = float(np.sum(L * L))
+                tl = np.array([mu2 + tot - float(np.sum(L[:r, :r] ** 2))
+                               for r in range(Z.shape[1] + 1)])
+            r_max = min(Z.shape[1], m, n)
+            tl = tl[: r_max + 1]
+            r = choose_rank(tl, 0.0 if delta2 is None else delta2, r_fixed, r_max)
+            grow = (not exact and l < min(n, m) and r_fixed is None
+                    and (r > l - p or tl[r] > delta2))
+            if grow:
+                l = min(2 * l, n, m)
+                continue
+            break
+        V1 = Z[:, :r] if W is None else W @ Z[:, :r]
+        rr = min(r, kk)
+        carry = np.zeros((m, r))
+        if lhat == "full":
+            carry[:, :] = U @ L[:, :r]
+        else:
+            carry[:, :rr] = U[:, :rr] @ L[:rr, :rr]
+        cores[k - 1] = V1.T.reshape(r, dims[k - 1], r_next)
+        rk[k - 1] = r
+        tails[k - 2] = float(tl[r])
+        C = carry
+        r_next = r_prev = r
+    cores[0] = C.reshape(1, dims[0], r_next)
+    return dict(cores=cores, ranks=rk, tails=tails, normA2=normA2,
+                delta2=None if delta2 is None else [delta2] * (d - 1), orth="right")

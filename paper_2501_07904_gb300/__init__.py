@@ -237,18 +237,23 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
 
 def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, oversample=16,
            l_full=256, small="auto", weights=None, stream=None, timing=False, orth="auto",
-           reverse=False):
+           reverse=False, direction=None):
     """TT-URV right-to-left (Alg. 3) or TT-ULV left-to-right (Alg. 1/2).
 
     Give ``eps`` (prescribed relative accuracy, Alg. 2) or ``ranks``
     (r_1..r_{d-1}).  ``A`` may live on the GPU or on the host (copied in).
-    ``reverse`` factors the index-reversed tensor and returns its cores read
-    back as cores of ``A`` (Remark after Thm 3.2: URV then gives a
-    left-orthogonal TT).
+    ``direction`` defaults to the variant's recommended sweep ("RL" for URV,
+    "LR" for ULV); ULV with "RL" is the appendix's Alg. 4 keeping
+    [L_11; L_21], which computes the URV right-to-left sweep (and URV with
+    "LR" the ULV left-to-right one).  ``reverse`` factors the index-reversed
+    tensor and returns its cores read back as cores of ``A`` (Remark after
+    Thm 3.2: URV then gives a left-orthogonal TT).
     """
     if (eps is None) == (ranks is None):
         raise ValueError("give exactly one of eps or ranks")
-    v = {"URV": (TT_URV, TT_RL), "ULV": (TT_ULV, TT_LR)}[variant]
+    if direction is None:
+        direction = "RL" if variant == "URV" else "LR"
+    v = ({"URV": TT_URV, "ULV": TT_ULV}[variant], {"RL": TT_RL, "LR": TT_LR}[direction])
     return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
                   weights, stream, timing, orth, reverse)
 

@@ -831,15 +831,15 @@ tt_status tt_utv(const void* A, int32_t dtype, int32_t d, const int64_t* dims, d
                  const int64_t* fixed_ranks, int32_t variant, int32_t direction,
                  const tt_opts* opts, tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx,
                  void* stream, tt_result* out) {
-  SweepCfg cfg;
-  if (variant == TT_URV && direction == TT_RL)
-    cfg = {true, false};
-  else if (variant == TT_ULV && direction == TT_LR)
-    cfg = {false, false};
-  else if ((variant == TT_URV && direction == TT_LR) || (variant == TT_ULV && direction == TT_RL))
-    return fail(TT_EUNSUPPORTED, "only URV right-to-left and ULV left-to-right are built");
-  else
-    return fail(TT_EINVAL, "bad variant or direction");
+  // The inner factor is a pivoted QLP, C ~ (Q_1 Pi_2) L (Pi_1 Q_2)^T: a ULV
+  // form of C whose URV form is the QR of L.  A right-to-left TT-ULV that
+  // keeps the middle block [L_11; L_21] (the appendix's first case of Alg. 4)
+  // carries C V_1 with error ||L_22||^2 -- exactly the right-to-left TT-URV;
+  // mirrored, a left-to-right TT-URV keeping [R_11 R_12] is the left-to-right
+  // TT-ULV.  Both pairings therefore run those sweeps.
+  if (variant != TT_URV && variant != TT_ULV) return fail(TT_EINVAL, "bad variant");
+  if (direction != TT_RL && direction != TT_LR) return fail(TT_EINVAL, "bad direction");
+  const SweepCfg cfg{direction == TT_RL, false};
   return sweep_entry(A, dtype, d, dims, eps, fixed_ranks, cfg, opts, alloc, free_fn, alloc_ctx,
                      stream, out);
 }

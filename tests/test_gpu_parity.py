@@ -209,6 +209,27 @@ def test_svd_unsupported_when_both_sides_large(tu):
         tu.tt_svd(A, eps=0.5, l_full=16, direction="LR")
 
 
+@pytest.mark.parametrize("precision, tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_alg4_pairings(tu, precision, tol):
+    # TT-ULV right-to-left keeping [L_11; L_21] (the appendix's Alg. 4, first
+    # case) against the oracle's Alg. 4, which forms it from the ULV factors;
+    # it runs the URV right-to-left sweep, and URV left-to-right the ULV
+    # left-to-right one, bit for bit
+    A = RAGGED if precision == "fp64" else RAGGED.astype(np.float32)
+    A_t = torch.from_numpy(A).cuda()
+    res = tu.tt_utv(A_t, eps=1e-3, variant="ULV", direction="RL", precision=precision, l_full=24)
+    ref = otc.tt_ulv_rl(np.asarray(A, np.float64), eps=1e-3, lhat="full", l_full=24)
+    assert res.ranks == ref["ranks"]
+    assert res.orth == "right"
+    assert rel_diff(np_cores(res), ref["cores"], ref["normA2"]) <= tol
+    for v, direction, same in (("ULV", "RL", "URV"), ("URV", "LR", "ULV")):
+        a = tu.tt_utv(A_t, eps=1e-3, variant=v, direction=direction, precision=precision, l_full=24)
+        b = tu.tt_utv(A_t, eps=1e-3, variant=same, precision=precision, l_full=24)
+        assert a.ranks == b.ranks and a.orth == b.orth and a.tail_sq == b.tail_sq
+        for x, y in zip(a.cores, b.cores):
+            assert torch.equal(x, y)
+
+
 def test_deterministic(tu):
     A = torch.from_numpy(RAGGED.astype(np.float32)).cuda()
     a = tu.tt_utv(A, eps=1e-3, l_full=24)

@@ -286,3 +286,56 @@ def test_masked_eval_and_gradient():
             cm[k][pos] -= h
             fd = (gout @ tt.tt_eval_at(cp, idx) - gout @ tt.tt_eval_at(cm, idx)) / (2 * h)
             assert grads[k][pos] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+# ------------------------------------------- TT-ULV right-to-left (appendix, Alg. 4)
+
+@pytest.mark.parametrize("l_full", [256, 6])
+def test_alg4_full_block_equals_urv_rl(l_full):
+    # the appendix's first case (keep U_1 L_11 + U_2 L_21, i.e. C V_1) computed
+    # from the ULV factors gives the right-to-left TT-URV of Alg. 3 exactly
+    A = synth.gaussian_tt((9, 10, 11, 8), (1, 3, 4, 3, 1), rel_noise=1e-3, seed=2, dtype=np.float64)
+    u = tt.tt_utv(A, eps=1e-2, variant="URV", l_full=l_full)
+    f = tt.tt_ulv_rl(A, eps=1e-2, lhat="full", l_full=l_full)
+    assert f["ranks"] == u["ranks"]
+    nA = np.sqrt(u["normA2"])
+    assert np.abs(tt.tt_full(u["cores"]) - tt.tt_full(f["cores"])).max() <= 1e-12 * nA
+    np.testing.assert_allclose(f["tails"], u["tails"], rtol=1e-9, atol=1e-14 * u["normA2"])
+
+
+def test_alg4_l11_error_is_its_residual_and_exceeds_the_projection():
+    # d = 2: one truncation, A_hat = U_1 L_11 V_1^T; its squared error is the
+    # reported tail ||L||^2 - ||L_11||^2 and is no smaller than that of the
+    # orthogonal projection C V_1 V_1^T with the same V_1
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((30, 6)) @ rng.standard_normal((6, 25)) + 0.05 * rng.standard_normal((30, 25))
+    for r in (2, 4, 6):
+        l = tt.tt_ulv_rl(A, ranks=[r], lhat="l11")
+        f = tt.tt_ulv_rl(A, ranks=[r], lhat="full")
+        e_l = float(np.sum((A - tt.tt_full(l["cores"])) ** 2))
+        e_f = float(np.sum((A - tt.tt_full(f["cores"])) ** 2))
+        assert e_l == pytest.approx(l["tails"][0], rel=1e-10)
+        assert e_f == pytest.approx(f["tails"][0], rel=1e-10)
+        assert e_l >= e_f * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("l_full", [256, 6])
+def test_alg4_l11_proposition_bound(l_full):
+    # ||A - A_hat|| <= sum_k ||E_k|| <= eps ||A|| with eps_k = eps ||A|| / (d-1)
+    A = synth.gaussian_tt((9, 10, 11, 8), (1, 3, 4, 3, 1), rel_noise=1e-2, seed=4, dtype=np.float64)
+    for eps in (3e-2, 1e-1):
+        l = tt.tt_ulv_rl(A, eps=eps, lhat="l11", l_full=l_full)
+        nA = np.sqrt(l["normA2"])
+        err = tt.rse(A, l["cores"]) * nA
+        bound = sum(np.sqrt(l["tails"]))
+        assert err <= bound * (1 + 1e-10)
+        assert all(t <= dl * (1 + 1e-12) for t, dl in zip(l["tails"], l["delta2"]))
+        assert bound <= eps * nA * (1 + 1e-12)
+        assert max(right_orth_err(g) for g in l["cores"][1:]) < 1e-12
+
+
+def test_alg4_l11_exact_recovery():
+    A = synth.gaussian_tt((6, 7, 5, 6), (1, 2, 3, 2, 1), rel_noise=0.0, seed=12, dtype=np.float64)
+    l = tt.tt_ulv_rl(A, eps=1e-8, lhat="l11")
+    assert l["ranks"] == [1, 2, 3, 2, 1]
+    assert tt.rse(A, l["cores"]) < 1e-12
