@@ -13,7 +13,9 @@ Modules
 linalg  Householder QR (optionally column-pivoted) and one-sided Jacobi SVD.
 philox  Philox4x32-10 counter-based generator and the Rademacher sketch matrix.
 tt      TT format (Eq. TT), TT-ULV (Alg. 1/2), TT-URV (Alg. 3 and its
-        prescribed-accuracy analogue), TT-SVD, masked evaluation and gradients.
+        prescribed-accuracy analogue), TT-ULV right-to-left (the appendix's
+        Alg. 4, both middle blocks), TT-SVD, the range step with optional
+        power iterations, masked evaluation and gradients.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, LAPACK, brute force or the paper's Table (tab: Beps),
