@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace ttk {
@@ -29,16 +30,14 @@ constexpr int kTargetBlocks = 152 * 8;
 //         ~n u^2 sum|a b| (u = 2^-24), i.e. below 5e-13 of sum|a b| -- the
 //         order of an FP64 sum of exact products over the same split-K chunk
 //         -- at FP32 instruction rates (FP64 runs at a small fraction of them
-//         on this part).  The __f*_rn intrinsics keep the compiler from
-//         contracting the error-free transformations into FMAs.
+//         on this part).  The error-free transformations (dfloat.cuh) use
+//         the _rn intrinsics, which the compiler never contracts into FMAs.
 enum AccMode { kF32 = 0, kF64 = 1, kDF = 2 };
 
 __device__ __forceinline__ void two_prod_sum(float a, float b, float& hi, float& lo) {
-  const float p = __fmul_rn(a, b);
-  const float e = __fmaf_rn(a, b, -p);  // a b = p + e exactly (no underflow)
-  const float s = __fadd_rn(hi, p);
-  const float bv = __fsub_rn(s, hi);
-  const float q = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));  // hi + p = s + q
+  float p, e, s, q;
+  two_prod(a, b, p, e);  // a b = p + e exactly (no underflow)
+  two_sum(hi, p, s, q);  // hi + p = s + q exactly
   hi = s;
   lo = __fadd_rn(lo, __fadd_rn(q, e));
 }
