@@ -72,8 +72,17 @@ typedef enum { TT_P_FP64 = 0, TT_P_FP32 = 1, TT_P_MIXED = 2 } tt_precision;
 /* Arithmetic of the small (<= 256 x 256) factorizations:
  *  TT_SMALL_AUTO picks FP32 when eps^2 w_k^2 >= 2 n u_fp32 (the Gram-based
  *  truncation error is then resolved with margin) or the ranks are fixed,
- *  FP64 otherwise; TT_SMALL_FP32 / TT_SMALL_FP64 force one. */
-typedef enum { TT_SMALL_AUTO = 0, TT_SMALL_FP32 = 1, TT_SMALL_FP64 = 2 } tt_small_precision;
+ *  FP64 otherwise; TT_SMALL_FP32 / TT_SMALL_FP64 force one.  TT_SMALL_DF
+ *  (FP32 data only) takes the FP64 choices everywhere but runs factors of
+ *  n <= 64 in double-float arithmetic (an FP32 pair, ~2^-48 unit roundoff,
+ *  at FP32 instruction rates; GB300 issues FP64 at 1/64 of them); larger
+ *  factors stay FP64. */
+typedef enum {
+  TT_SMALL_AUTO = 0,
+  TT_SMALL_FP32 = 1,
+  TT_SMALL_FP64 = 2,
+  TT_SMALL_DF = 3
+} tt_small_precision;
 
 /* Phases timed when tt_opts.phase_ms is set (device time from CUDA events
  * recorded on the sweep's stream). */

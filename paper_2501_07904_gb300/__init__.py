@@ -27,7 +27,7 @@ TT_MAXD = 16
 STATUS = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENONFINITE", 3: "TT_ENOMEM", 4: "TT_ECUDA",
           5: "TT_ENOCONV", 6: "TT_ETIMEOUT", 7: "TT_EUNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
-SMALL = {"auto": 0, "fp32": 1, "fp64": 2}
+SMALL = {"auto": 0, "fp32": 1, "fp64": 2, "df": 3}
 TT_F32, TT_F64 = 0, 1
 TT_URV, TT_ULV = 0, 1
 TT_RL, TT_LR = 0, 1

@@ -113,6 +113,7 @@ DF_HD bool operator<(df32 a, df32 b) { return b > a; }
 DF_HD bool operator<=(df32 a, df32 b) { return !(a > b); }
 DF_HD bool operator>=(df32 a, df32 b) { return !(b > a); }
 DF_HD bool operator==(df32 a, df32 b) { return a.h == b.h && a.l == b.l; }
+DF_HD bool operator!=(df32 a, df32 b) { return !(a == b); }
 
 DF_HD df32 fmax_df(df32 a, df32 b) { return (b > a) ? b : a; }
 

@@ -351,8 +351,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     auto tight = [&](int64_t nsz) {
       return !fixed && !(dscale >= 2.0 * (double)nsz * 5.9604644775390625e-08);
     };
+    // double-float small factors (FP32 data only): FP64-grade in every use
+    const bool small_df = !W64 && o.small_precision == TT_SMALL_DF;
     auto choose_small64 = [&](int64_t nsz) {
-      if (o.small_precision == TT_SMALL_FP64) return true;
+      if (o.small_precision == TT_SMALL_FP64 || small_df) return true;
       if (o.small_precision == TT_SMALL_FP32) return false;
       if (W64) return true;
       return tight(nsz);
@@ -400,7 +402,8 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         prm.normA2_is_trace = 1;
       }
       prm.x2_dev = nullptr;
-      prm.piv_tol = small64 ? 1e-15 : 1e-6;
+      prm.piv_tol = small64 ? (small_df ? 1e-13 : 1e-15) : 1e-6;
+      prm.df_math = small_df ? 1 : 0;
       TT_ALLOC(zb, (size_t)nb * nb * sizeof(W));
       ldz = nb;
       tm.begin(s, TT_PH_SMALL);
@@ -476,9 +479,13 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         // FP32 floor; W_1 is then too ill-conditioned for an FP32-summed
         // Gram to stay positive definite, so those Grams use compensated sums
         // of exact products and the Cholesky runs in FP64.
-        const bool orth64 = o.orth_precision == TT_SMALL_FP64 ||
+        const bool orth_df = !W64 && o.orth_precision == TT_SMALL_DF;
+        po.df_math = orth_df ? 1 : 0;
+        const bool orth64 = o.orth_precision == TT_SMALL_FP64 || orth_df ||
                             (o.orth_precision == TT_SMALL_AUTO && (small64 || W64));
-        const double u_c = orth64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        // unit roundoff of the Cholesky's arithmetic (double-float: ~2^-48)
+        const double u_c = orth_df ? 3.552713678800501e-15
+                                   : orth64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
         const W* src_pass = yb.as<W>();
         W* dst_pass[3] = {w1b.as<W>(), wb.as<W>(), w1b.as<W>()};
         tm.begin(s, TT_PH_ORTH);
@@ -527,7 +534,8 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         prm.r_cap = (int)std::min<int64_t>(rcap, l);
         prm.x2_dev = x2_dev;
         prm.range_exact = identity ? 1 : 0;
-        prm.piv_tol = small64 ? 1e-15 : 1e-6;
+        prm.piv_tol = small64 ? (small_df ? 1e-13 : 1e-15) : 1e-6;
+        prm.df_math = small_df ? 1 : 0;
         TT_ALLOC(zb, (size_t)l * l * sizeof(W));
         ldz = l;
         tm.begin(s, TT_PH_SMALL);
@@ -694,9 +702,9 @@ tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims,
   if (o.oversample < 0 || o.oversample > 128) return fail(TT_EINVAL, "oversample must be in [0, 128]");
   if (o.l_full < 1 || o.l_full > ttk::kMaxSmall) return fail(TT_EINVAL, "l_full must be in [1, 256]");
   if (o.precision < TT_P_FP64 || o.precision > TT_P_MIXED) return fail(TT_EINVAL, "bad precision");
-  if (o.small_precision < TT_SMALL_AUTO || o.small_precision > TT_SMALL_FP64)
+  if (o.small_precision < TT_SMALL_AUTO || o.small_precision > TT_SMALL_DF)
     return fail(TT_EINVAL, "bad small_precision");
-  if (o.orth_precision < TT_SMALL_AUTO || o.orth_precision > TT_SMALL_FP64)
+  if (o.orth_precision < TT_SMALL_AUTO || o.orth_precision > TT_SMALL_DF)
     return fail(TT_EINVAL, "bad orth_precision");
   if (o.reverse != 0 && o.reverse != 1) return fail(TT_EINVAL, "reverse must be 0 or 1");
   if (o.weights) {

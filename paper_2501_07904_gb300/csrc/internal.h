@@ -83,6 +83,7 @@ struct SmallParams {
   double shift_rel;       // SM_ORTH: diagonal shift, relative to trace(G)
   const double* Gw;       // QLP/Jacobi on a sketch: W^T W of the range basis, or null
   int range_exact;        // 1: the sketch is the identity, so W spans X's row space (mu^2 = 0)
+  int df_math;            // with fp64_math: run the fast path in double-float (n <= 64)
 };
 size_t small_ws_bytes(int n, bool fp64);
 // Register-resident fast path (small_fast.cu) for SM_QLP / SM_ORTH with

@@ -1,6 +1,8 @@
 // Register-resident single-CTA small factorizations: the fast path of
 // small_factor() for the sweep's pivoted QLP (SM_QLP) and shifted
-// Cholesky-QR (SM_ORTH), for n <= 128 in FP32 and n <= 64 in FP64.
+// Cholesky-QR (SM_ORTH), for n <= 128 in FP32 and n <= 64 in FP64 or in
+// double-float (an FP32 pair, dfloat.cuh: FP64-grade tails at FP32 issue
+// rates, selected by SmallParams::df_math).
 //
 // The symmetric n x n matrix is held in registers, a TI x TJ tile per thread
 // (256 threads: FP32 8 x 8 tiles cover 128 x 128, FP64 4 x 4 tiles 64 x 64).
@@ -28,6 +30,7 @@
 // Schur complement of R_1 R_1^T after j pivots = sum_{i>j} ||L(:, i)||^2.
 #include <math.h>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace ttk {
@@ -45,6 +48,10 @@ struct Tile<float> {
 };
 template <>
 struct Tile<double> {
+  static constexpr int I = 4, J = 4;
+};
+template <>
+struct Tile<df32> {
   static constexpr int I = 4, J = 4;
 };
 template <typename T>
@@ -66,6 +73,27 @@ __device__ __forceinline__ int tile_r(int i) {
   return Tile<T>::I * (int)(threadIdx.x / 16) + i;
 }
 __device__ __forceinline__ int tile_c(int jj) { return (int)(threadIdx.x % 16) + 16 * jj; }
+
+// Arithmetic of the working type: FP32, FP64 or double-float (dfloat.cuh).
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ df32 tfma(df32 a, df32 b, df32 c) { return fma_df(a, b, c); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ df32 tmax(df32 a, df32 b) { return fmax_df(a, b); }
+__device__ __forceinline__ float tshfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double tshfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df32 tshfl_xor(df32 v, int o) {
+  return df32(__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o));
+}
+__device__ __forceinline__ float tshfl(unsigned m, float v, int src) { return __shfl_sync(m, v, src); }
+__device__ __forceinline__ double tshfl(unsigned m, double v, int src) { return __shfl_sync(m, v, src); }
+__device__ __forceinline__ df32 tshfl(unsigned m, df32 v, int src) {
+  return df32(__shfl_sync(m, v.h, src), __shfl_sync(m, v.l, src));
+}
+__device__ __forceinline__ float tinv_sqrt(float x) { return 1.0f / sqrtf(x); }
+__device__ __forceinline__ double tinv_sqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ df32 tinv_sqrt(df32 x) { return rsqrt_df(x, rsqrtf(x.h)); }
 
 // K consecutive shared-memory elements (K sizeof(T) a multiple of 16 bytes,
 // 16-byte aligned) to and from v[o .. o + K)
@@ -90,6 +118,15 @@ __device__ __forceinline__ void vload(const double* p, double (&v)[N], int o) {
   }
 }
 template <int K, int N>
+__device__ __forceinline__ void vload(const df32* p, df32 (&v)[N], int o) {
+#pragma unroll
+  for (int q = 0; q < K / 2; ++q) {
+    const float4 x = reinterpret_cast<const float4*>(p)[q];
+    v[o + 2 * q] = df32(x.x, x.y);
+    v[o + 2 * q + 1] = df32(x.z, x.w);
+  }
+}
+template <int K, int N>
 __device__ __forceinline__ void vstore(float* p, const float (&v)[N], int o) {
 #pragma unroll
   for (int q = 0; q < K / 4; ++q)
@@ -101,6 +138,14 @@ __device__ __forceinline__ void vstore(double* p, const double (&v)[N], int o) {
 #pragma unroll
   for (int q = 0; q < K / 2; ++q)
     reinterpret_cast<double2*>(p)[q] = make_double2(v[o + 2 * q], v[o + 2 * q + 1]);
+}
+
+template <int K, int N>
+__device__ __forceinline__ void vstore(df32* p, const df32 (&v)[N], int o) {
+#pragma unroll
+  for (int q = 0; q < K / 2; ++q)
+    reinterpret_cast<float4*>(p)[q] =
+        make_float4(v[o + 2 * q].h, v[o + 2 * q].l, v[o + 2 * q + 1].h, v[o + 2 * q + 1].l);
 }
 
 // Column-permuted position of column c = tx + 16 jj in a row: the CW =
@@ -149,7 +194,7 @@ __device__ __forceinline__ void tile_product(T (&a)[TI][TJ], int mr, int mc, int
 #pragma unroll
     for (int i = 0; i < TI; ++i)
 #pragma unroll
-      for (int jj = 0; jj < TJ; ++jj) a[i][jj] = fma(ra[i], cb[jj], a[i][jj]);
+      for (int jj = 0; jj < TJ; ++jj) a[i][jj] = tfma(ra[i], cb[jj], a[i][jj]);
   }
 }
 
@@ -188,6 +233,21 @@ __device__ __forceinline__ int warp_argmax(bool has, double v, int idx, double& 
   return bi == 0x7fffffff ? -1 : bi;
 }
 
+__device__ __forceinline__ int warp_argmax(bool has, df32 v, int idx, df32& best) {
+  df32 b = has ? v : df32(-1);
+  int bi = has ? idx : 0x7fffffff;
+  for (int o = 16; o > 0; o >>= 1) {
+    const df32 ob = tshfl_xor(b, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > b || (ob == b && oi < bi)) {
+      b = ob;
+      bi = oi;
+    }
+  }
+  best = b;
+  return bi == 0x7fffffff ? -1 : bi;
+}
+
 // rs = 1/sqrt(x) (0 when drop).  FP32: the hardware reciprocal square root
 // refined by one Newton step, rs (3 - x rs^2) / 2.
 __device__ __forceinline__ float recip_sqrt(float x, bool drop) {
@@ -197,6 +257,9 @@ __device__ __forceinline__ float recip_sqrt(float x, bool drop) {
 }
 __device__ __forceinline__ double recip_sqrt(double x, bool drop) {
   return drop ? 0.0 : 1.0 / sqrt(x);
+}
+__device__ __forceinline__ df32 recip_sqrt(df32 x, bool drop) {
+  return drop ? df32(0) : tinv_sqrt(x);
 }
 
 // Sum of the warp's copy of the remaining diagonal over the entries not yet
@@ -208,7 +271,7 @@ __device__ __forceinline__ T remaining_trace(const T (&d)[DM], unsigned dmask) {
 #pragma unroll
   for (int m = 0; m < DM; ++m)
     if (!((dmask >> m) & 1u)) s += d[m];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  for (int o = 16; o > 0; o >>= 1) s += tshfl_xor(s, o);
   return s > T(0) ? s : T(0);
 }
 
@@ -291,9 +354,9 @@ __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int st
     const int t = DM * lane + m;
     d[m] = t < n ? dsm[t] : T(0);
     if (t >= n) dmask |= 1u << m;
-    dmax = fmax(dmax, d[m]);
+    dmax = tmax(dmax, d[m]);
   }
-  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  for (int o = 16; o > 0; o >>= 1) dmax = tmax(dmax, tshfl_xor(dmax, o));
   // tol_abs >= 0, so dp > tol_abs also means dp > 0 (and is false for NaN)
   const T tol_abs = (T)(tol * (double)dmax);
   const T stop_trace = (T)(delta2 - base);
@@ -361,7 +424,7 @@ __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int st
           for (int i = 0; i < TI; ++i)
 #pragma unroll
             for (int k = 0; k < CW; ++k)
-              a[i][h * CW + k] = fma(-lr[i], lc[h * CW + k], a[i][h * CW + k]);
+              a[i][h * CW + k] = tfma(-lr[i], lc[h * CW + k], a[i][h * CW + k]);
         }
         if (AUG && clo < n) {
           vload<CW>(eC + clo + tx * CW, le, h * CW);
@@ -369,12 +432,12 @@ __device__ int chol_rl(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int st
           for (int i = 0; i < TI; ++i)
 #pragma unroll
             for (int k = 0; k < CW; ++k)
-              b[i][h * CW + k] = fma(-lr[i], le[h * CW + k], b[i][h * CW + k]);
+              b[i][h * CW + k] = tfma(-lr[i], le[h * CW + k], b[i][h * CW + k]);
         }
       }
     }
 #pragma unroll
-    for (int m = 0; m < DM; ++m) d[m] = fma(-l[m], l[m], d[m]);
+    for (int m = 0; m < DM; ++m) d[m] = tfma(-l[m], l[m], d[m]);
     if ((unsigned)p / DM == (unsigned)lane) dmask |= 1u << ((unsigned)p % DM);
   }
   const T trend = remaining_trace(d, dmask);
@@ -412,8 +475,8 @@ __device__ __forceinline__ void publish_block4(const T (&a)[TI][TJ], const T (&b
         T ex = AUG ? b[I0 + s][jj] : T(0);
 #pragma unroll
         for (int u = 0; u < s; ++u) {
-          x = fma(-Lt[u][s], rv[u][k], x);
-          if (AUG) ex = fma(-Lt[u][s], ev[u][k], ex);
+          x = tfma(-Lt[u][s], rv[u][k], x);
+          if (AUG) ex = tfma(-Lt[u][s], ev[u][k], ex);
         }
         rv[s][k] = c > j0 + s ? x * rs[s] : (c == j0 + s ? Lt[s][s] : T(0));
         ev[s][k] = ex * rs[s];
@@ -462,9 +525,9 @@ __device__ void chol_col4(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int
 #pragma unroll
   for (int m = 0; m < DM; ++m) {
     const int t = DM * lane + m;
-    dmax = fmax(dmax, t < n ? dsm[t] : T(0));
+    dmax = tmax(dmax, t < n ? dsm[t] : T(0));
   }
-  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  for (int o = 16; o > 0; o >>= 1) dmax = tmax(dmax, tshfl_xor(dmax, o));
   // tol_abs >= 0, so dd > tol_abs also means dd > 0 (and is false for NaN)
   const T tol_abs = (T)(tol * (double)dmax);
   const int jlim = min(kmax, n);
@@ -495,7 +558,7 @@ __device__ void chol_col4(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int
       for (int t = 0; t < 4; ++t) {
         const int src = (lane & 16) | ((j0 + t) & 15);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) U[s][t] = __shfl_sync(hm, colv[s], src);
+        for (int s = 0; s < 4; ++s) U[s][t] = tshfl(hm, colv[s], src);
       }
       // its factor: Lt[s][t] = R(j0 + s, j0 + t), t >= s
       T Lt[4][4], rs[4];
@@ -503,7 +566,7 @@ __device__ void chol_col4(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int
       for (int s = 0; s < 4; ++s) {
         T dd = U[s][s];
 #pragma unroll
-        for (int u = 0; u < s; ++u) dd = fma(-Lt[u][s], Lt[u][s], dd);
+        for (int u = 0; u < s; ++u) dd = tfma(-Lt[u][s], Lt[u][s], dd);
         const bool drop = (s >= kb) || !(dd > tol_abs);
         rs[s] = recip_sqrt(dd, drop);
         Lt[s][s] = drop ? T(0) : dd * rs[s];
@@ -511,7 +574,7 @@ __device__ void chol_col4(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int
         for (int t = s + 1; t < 4; ++t) {
           T x = U[s][t];
 #pragma unroll
-          for (int u = 0; u < s; ++u) x = fma(-Lt[u][s], Lt[u][t], x);
+          for (int u = 0; u < s; ++u) x = tfma(-Lt[u][s], Lt[u][t], x);
           Lt[s][t] = x * rs[s];
         }
       }
@@ -541,7 +604,7 @@ __device__ void chol_col4(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int
             for (int i = 0; i < TI; ++i)
 #pragma unroll
               for (int k = 0; k < CW; ++k)
-                a[i][h * CW + k] = fma(-lr[i], lc[h * CW + k], a[i][h * CW + k]);
+                a[i][h * CW + k] = tfma(-lr[i], lc[h * CW + k], a[i][h * CW + k]);
           }
           if (AUG && clo < n && clo <= j) {
             vload<CW>(rN + 2 * NT + clo + tx * CW, le, h * CW);
@@ -549,7 +612,7 @@ __device__ void chol_col4(T (&a)[TI][TJ], T (&b)[TI][TJ], int n, double tol, int
             for (int i = 0; i < TI; ++i)
 #pragma unroll
               for (int k = 0; k < CW; ++k)
-                b[i][h * CW + k] = fma(-lr[i], le[h * CW + k], b[i][h * CW + k]);
+                b[i][h * CW + k] = tfma(-lr[i], le[h * CW + k], b[i][h * CW + k]);
           }
         }
       }
@@ -717,16 +780,16 @@ __global__ void __launch_bounds__(FT, 1) small_fast_kernel(const double* __restr
           for (int bcol = 0; bcol < c; ++bcol) {
             T dot = T(0);
             for (int i = lane; i < n; i += 32) dot += R2[i * ld + bcol] * v[i];
-            for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+            for (int o = 16; o > 0; o >>= 1) dot += tshfl_xor(dot, o);
             for (int i = lane; i < n; i += 32) v[i] -= dot * R2[i * ld + bcol];
             __syncwarp();
           }
         }
         T nv = T(0);
         for (int i = lane; i < n; i += 32) nv += v[i] * v[i];
-        for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+        for (int o = 16; o > 0; o >>= 1) nv += tshfl_xor(nv, o);
         if (nv > T(0.25)) {
-          const T s = T(1) / sqrt(nv);
+          const T s = tinv_sqrt(nv);
           for (int i = lane; i < n; i += 32) R2[i * ld + c] = v[i] * s;
           __syncwarp();
           ++cand;
@@ -790,6 +853,9 @@ bool small_fast_eligible(const SmallParams& prm, bool fp64) {
 
 cudaError_t small_factor_fast(const double* G, SmallParams prm, bool fp64_math, void* Z,
                               bool z_fp64, int ldz, void* ws, StepInfo* info, cudaStream_t st) {
+  if (fp64_math && prm.df_math)
+    return z_fp64 ? launch_fast<df32, double>(G, prm, Z, ldz, ws, info, st)
+                  : launch_fast<df32, float>(G, prm, Z, ldz, ws, info, st);
   if (fp64_math)
     return z_fp64 ? launch_fast<double, double>(G, prm, Z, ldz, ws, info, st)
                   : launch_fast<double, float>(G, prm, Z, ldz, ws, info, st);

@@ -69,6 +69,12 @@ def test_invalid_options_rejected(L):
     o.l_full = 300
     assert _call(L, opts=ctypes.byref(o)) == 1
     L.tt_opts_default(ctypes.byref(o))
+    o.small_precision = 4                        # AUTO, FP32, FP64, DF are 0..3
+    assert _call(L, opts=ctypes.byref(o)) == 1
+    L.tt_opts_default(ctypes.byref(o))
+    o.orth_precision = -1
+    assert _call(L, opts=ctypes.byref(o)) == 1
+    L.tt_opts_default(ctypes.byref(o))
     w = (ctypes.c_double * 2)(0.5, 0.5)          # sum w^2 != 1
     o.weights = ctypes.cast(w, ctypes.POINTER(ctypes.c_double))
     assert _call(L, opts=ctypes.byref(o)) == 1
