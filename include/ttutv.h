@@ -116,6 +116,11 @@ typedef struct {
   double* phase_ms;         /* host, TT_MAXD * TT_NPHASES doubles [sweep step][tt_phase], or NULL.
                                Milliseconds of device time are ADDED to it; the sweep step index is
                                0 for the first factored unfolding. */
+  int32_t power_iters;      /* q in [0, 8]: power (subspace) iterations of a sketched step's range,
+                               Y <- X^T X Q with Q an orthonormal basis of the previous Y (the
+                               randomized range finder behind randUTV, Sec. 2.2); no effect when
+                               Omega = I.  Default 0. */
+  int32_t pad2_;
 } tt_opts;
 
 /* Fill *o with the defaults listed above. */

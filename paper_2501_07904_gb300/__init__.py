@@ -53,7 +53,8 @@ class tt_opts(ctypes.Structure):
                 ("oversample", ctypes.c_int32), ("l_full", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("weights", ctypes.POINTER(ctypes.c_double)),
                 ("orth_precision", ctypes.c_int32), ("reverse", ctypes.c_int32),
-                ("phase_ms", ctypes.POINTER(ctypes.c_double))]
+                ("phase_ms", ctypes.POINTER(ctypes.c_double)),
+                ("power_iters", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
 
 
 class tt_result(ctypes.Structure):
@@ -179,7 +180,7 @@ class TTResult:
 
 
 def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream,
-           timing=False, orth="auto", reverse=False):
+           timing=False, orth="auto", reverse=False, power_iters=0):
     if not isinstance(A, torch.Tensor):
         raise TypeError("A must be a torch.Tensor")
     if A.dtype not in (torch.float32, torch.float64):
@@ -197,6 +198,7 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
     opts.l_full = int(l_full)
     opts.seed = int(seed)
     opts.reverse = 1 if reverse else 0
+    opts.power_iters = int(power_iters)
     wbuf = None
     if weights is not None:
         wbuf = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
@@ -237,7 +239,7 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
 
 def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, oversample=16,
            l_full=256, small="auto", weights=None, stream=None, timing=False, orth="auto",
-           reverse=False, direction=None):
+           reverse=False, direction=None, power_iters=0):
     """TT-URV right-to-left (Alg. 3) or TT-ULV left-to-right (Alg. 1/2).
 
     Give ``eps`` (prescribed relative accuracy, Alg. 2) or ``ranks``
@@ -247,7 +249,8 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
     [L_11; L_21], which computes the URV right-to-left sweep (and URV with
     "LR" the ULV left-to-right one).  ``reverse`` factors the index-reversed
     tensor and returns its cores read back as cores of ``A`` (Remark after
-    Thm 3.2: URV then gives a left-orthogonal TT).
+    Thm 3.2: URV then gives a left-orthogonal TT).  ``power_iters`` adds q
+    subspace iterations to every sketched range.
     """
     if (eps is None) == (ranks is None):
         raise ValueError("give exactly one of eps or ranks")
@@ -255,7 +258,7 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
         direction = "RL" if variant == "URV" else "LR"
     v = ({"URV": TT_URV, "ULV": TT_ULV}[variant], {"RL": TT_RL, "LR": TT_LR}[direction])
     return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
-                  weights, stream, timing, orth, reverse)
+                  weights, stream, timing, orth, reverse, power_iters)
 
 
 def tt_svd(A, eps=None, ranks=None, direction="LR", precision="fp32", l_full=256, small="auto",

@@ -463,6 +463,48 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
                           nullptr, false, nullptr, ws.p, false, true, false, false), "sketch C Omega");
         tm.end();
         omega.reset();
+        // q power (subspace) iterations: Y <- X^T X Q, Q = Y R^{-1} from one
+        // shifted Cholesky-QR pass (Q spans what Y spans); X = C (URV) or
+        // C^T (ULV).  The same products as the sketch and the projection.
+        if (o.power_iters > 0 && !identity) {
+          Buf qb(&al), pb(&al), gq(&al), sq(&al);
+          TT_ALLOC(qb, (size_t)nb * l * sizeof(W));
+          TT_ALLOC(pb, (size_t)no * l * sizeof(W));
+          TT_ALLOC(gq, (size_t)l * l * sizeof(double));
+          TT_ALLOC(sq, (size_t)l * l * sizeof(W));
+          const bool q64 = o.orth_precision == TT_SMALL_FP64 ||
+                           (o.orth_precision == TT_SMALL_AUTO && (small64 || W64));
+          ttk::SmallParams pq;
+          memset(&pq, 0, sizeof(pq));
+          pq.n = (int)l;
+          pq.mode = ttk::SM_ORTH;
+          pq.r_fixed = -1;
+          pq.r_cap = (int)l;
+          pq.shift_rel = 4.0 * (double)l * (q64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
+          tm.begin(s, TT_PH_SKETCH);
+          for (int it = 0; it < o.power_iters; ++it) {
+            TT_CK(mm_run<W>(mm, {yb.as<W>(), l, false}, {yb.as<W>(), l, true}, l, l, nb, nullptr, 0,
+                            gq.as<double>(), true, nullptr, ws.p, !W64 && small64, true, true, false),
+                  "power iteration: Gram of Y");
+            TT_CK(ttk::small_factor(gq.as<double>(), pq, q64, sq.p, W64, (int)l, ws2.p,
+                                    dinfo.as<ttk::StepInfo>(), st), "power iteration: orthonormalize");
+            TT_CK(mm_run<W>(mm, {yb.as<W>(), l, true}, {sq.as<W>(), l, true}, nb, l, l, qb.as<W>(), l,
+                            nullptr, false, nullptr, ws.p, false, true, true, false),
+                  "power iteration: apply R^-1");
+            if (cfg.urv) {
+              TT_CK(mm_run<W>(mm, {C, n, true}, {qb.as<W>(), l, true}, m, l, n, pb.as<W>(), l, nullptr,
+                              false, nullptr, ws.p, false, true, true, false), "power iteration: C Q");
+              TT_CK(mm_run<W>(mm, {C, n, false}, {pb.as<W>(), l, true}, n, l, m, yb.as<W>(), l, nullptr,
+                              false, nullptr, ws.p, false, true, true, false), "power iteration: C^T P");
+            } else {
+              TT_CK(mm_run<W>(mm, {C, n, false}, {qb.as<W>(), l, true}, n, l, m, pb.as<W>(), l, nullptr,
+                              false, nullptr, ws.p, false, true, true, false), "power iteration: C^T Q");
+              TT_CK(mm_run<W>(mm, {C, n, true}, {pb.as<W>(), l, true}, m, l, n, yb.as<W>(), l, nullptr,
+                              false, nullptr, ws.p, false, true, true, false), "power iteration: C P");
+            }
+          }
+          tm.end();
+        }
         // W = shifted Cholesky-QR3(Y): a shifted pass that cannot break
         // down, then two plain passes; span(W[:, :j]) = span(Y[:, :j]).
         TT_ALLOC(gy, (size_t)l * l * sizeof(double));
@@ -707,6 +749,7 @@ tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims,
   if (o.orth_precision < TT_SMALL_AUTO || o.orth_precision > TT_SMALL_DF)
     return fail(TT_EINVAL, "bad orth_precision");
   if (o.reverse != 0 && o.reverse != 1) return fail(TT_EINVAL, "reverse must be 0 or 1");
+  if (o.power_iters < 0 || o.power_iters > 8) return fail(TT_EINVAL, "power_iters must be in [0, 8]");
   if (o.weights) {
     double s = 0.0;
     for (int k = 0; k < d - 1; ++k) {

@@ -161,3 +161,40 @@ def test_allocator_failure_reports_enomem(L, reverse):
     assert b"allocator returned NULL" in L.tt_last_error()
     assert calls and calls[0] >= A.nbytes
     assert all(res.cores[k] is None for k in range(3))
+
+
+def test_power_iters_option(L):
+    o = tu.tt_opts()
+    L.tt_opts_default(ctypes.byref(o))
+    assert o.power_iters == 0
+    for bad in (-1, 9):
+        o.power_iters = bad
+        assert _call(L, opts=ctypes.byref(o)) == 1
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # every field offset and the size of tt_opts and tt_result, from the C
+    # compiler's view of include/ttutv.h, against the ctypes declarations
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ttutv.h"', "int main(void) {"]
+    for st in (tu.tt_opts, tu.tt_result):
+        name = st.__name__
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    inc = os.path.join(os.path.dirname(__file__), "..", "include")
+    subprocess.run([gcc, "-I", inc, str(src), "-o", str(tmp_path / "layout")], check=True)
+    out = subprocess.run([str(tmp_path / "layout")], capture_output=True, text=True, check=True).stdout
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out.splitlines()}
+    for st in (tu.tt_opts, tu.tt_result):
+        name = st.__name__
+        assert got[(name, "size")] == ctypes.sizeof(st)
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)
