@@ -421,7 +421,7 @@ def accuracy(tu, torch, A, res, workload):
 
 def cpu_sample(wl, steps=1):
     """Bounded sample of the workload for the oracle: the first s slices of
-    mode 1, about 0.9 s of oracle work per slice on the GPU machine's host cores.
+    mode 1, about 0.9 s of oracle work per slice on a GB300 node's host cores.
     One sweep of the sample is about 10 s; for a timed loop of `steps` sweeps
     (the reference arm) the sample shrinks so the loop stays near 2.5 min."""
     dims = list(wl["dims"])

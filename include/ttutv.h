@@ -46,7 +46,7 @@ typedef enum {
   TT_ENOCONV = 5,       /* Jacobi (TT-SVD) did not converge within its sweep cap */
   TT_ETIMEOUT = 6,      /* a bounded wait inside a tensor-core kernel ran out (2 s); the
                            kernel unwound and released its resources, the context stays usable */
-  TT_EUNSUPPORTED = 7   /* valid request outside what this build implements */
+  TT_EUNSUPPORTED = 7   /* valid request outside what the library implements */
 } tt_status;
 
 typedef enum { TT_F32 = 0, TT_F64 = 1 } tt_dtype;

@@ -11,7 +11,7 @@ Storage is row-major (C order): the paper's reverse-lexicographic ivec only
 permutes the rows and columns of every unfolding, which leaves singular
 values, ranks, truncation errors and the represented tensor unchanged.
 
-Readings where the paper is silent (each listed in the design doc):
+Readings where the paper is silent:
 
 * inner UTV (the paper names the family, Sec. 2.2): a range step (identity
   when the basis side has <= l_full columns, else a Rademacher sketch

@@ -108,7 +108,7 @@ def random_indices(dims, n, seed):
 
 
 # The five workloads the sweep is validated and measured on.  Sizes follow the
-# paper's synthetic examples (Sec. 4.1) scaled to one GPU; see the design doc.
+# paper's synthetic examples (Sec. 4.1) scaled to one GPU.
 CONFIGS = {
     "c1": dict(kind="gaussian_tt", dims=(16, 16, 16, 16), ranks=(1, 4, 4, 4, 1),
                rel_noise=1e-8, seed=0, dtype="float64", eps=1e-6),
