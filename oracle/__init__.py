@@ -18,9 +18,9 @@ tt      TT format (Eq. TT), TT-ULV (Alg. 1/2), TT-URV (Alg. 3 and its
         power iterations, masked evaluation and gradients.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
-against closed forms, LAPACK, brute force or the paper's Table (tab: Beps),
-except ``philox`` (no published vectors are used; pinned only by statistical
-properties and cross-implementation equality) -- parity unpinned for the exact
-bit stream of ``philox``.
+against closed forms, LAPACK, brute force or the paper's Table (tab: Beps);
+``philox`` is pinned bit for bit against PyTorch's independently written
+Philox4x32-10 engine (ATen/core/PhiloxRNGEngine.h, compiled on the host by
+``tests/test_oracle_philox_pin.py``) and by statistical properties.
 """
 from . import linalg, philox, tt  # noqa: F401

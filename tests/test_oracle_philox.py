@@ -1,9 +1,9 @@
 """Properties of the oracle's Philox4x32-10 stream and Rademacher sketch.
 
-No published test vectors are used, so the exact bit stream is pinned only by
-these statistical properties and by bit-equality with the independently
-written CUDA generator (tests/test_gpu_*.py): parity unpinned for the bits
-themselves.
+The exact bit stream is pinned separately, block for block, against
+PyTorch's independently written Philox4x32-10 engine
+(tests/test_oracle_philox_pin.py); these tests check the statistical
+properties the sketch relies on.
 """
 import numpy as np
 
