@@ -213,13 +213,17 @@ tt_status tt_full(int32_t d, const int64_t* dims, const int64_t* ranks, const vo
  * paper has no counterpart; this is a service of the library.)
  * Same arguments and result as tt_full, without `work`: the scratch is a
  * fixed array of tt_full_noalloc_max_work_bytes() = 32 MiB of static device
- * memory, which every GPU that loads this library holds until the process
- * exits.  A contraction needing more (tt_full_work_bytes) returns TT_EINVAL.
- * The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture on the device.  All calls share the one array and nothing in it
- * needs to start at zero, but two calls whose work overlaps on the GPU (other
- * streams, other host threads) race on it: serialize them. */
+ * memory.  A contraction needing more (tt_full_work_bytes) returns TT_EINVAL.
+ * The array is reserved on a device when the CUDA runtime first loads the
+ * module that holds it there -- under the default lazy module loading, at the
+ * first tt_full_noalloc call on that device -- and stays reserved until the
+ * process exits.  That first call also looks up the array's device address
+ * (with the device current) and caches it, so it may allocate and
+ * synchronize: make it before another allocator's pool takes the device's
+ * memory and before any stream capture on the device.  Later calls allocate
+ * nothing.  All calls share the one array and nothing in it needs to start at
+ * zero, but two calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on it: serialize them. */
 size_t tt_full_noalloc_max_work_bytes(void);
 tt_status tt_full_noalloc(int32_t d, const int64_t* dims, const int64_t* ranks,
                           const void* const* cores, int32_t dtype, void* out, void* stream);

@@ -325,32 +325,62 @@ def tt_rse(A, cores, stream=None):
     return err2, norm2
 
 
+def _eval_operands(cores, idx, gout=None):
+    """Validated contiguous operands of the masked evaluation: FP32 CUDA cores,
+    int64 indices (and FP32 output gradients) on the cores' device.  The
+    returned tensors must stay referenced until the library call has been
+    enqueued (their device pointers are passed to it)."""
+    if not cores:
+        raise ValueError("no cores")
+    dev = cores[0].device
+    for g in cores:
+        if not isinstance(g, torch.Tensor) or not g.is_cuda or g.dtype != torch.float32 \
+                or g.dim() != 3 or g.device != dev:
+            raise TypeError("cores must be float32 CUDA tensors of shape (r_{k-1}, I_k, r_k) "
+                            "on one device")
+    if not isinstance(idx, torch.Tensor) or idx.dtype != torch.int64 or not idx.is_cuda \
+            or idx.device != dev:
+        raise TypeError("idx must be an int64 CUDA tensor on the cores' device")
+    cores_c = [g.contiguous() for g in cores]
+    idx_c = idx.reshape(-1).contiguous()
+    gout_c = None
+    if gout is not None:
+        if not isinstance(gout, torch.Tensor) or gout.dtype != torch.float32 or not gout.is_cuda \
+                or gout.device != dev or gout.numel() != idx_c.numel():
+            raise TypeError("gout must be a float32 CUDA tensor with one value per index, on the "
+                            "cores' device")
+        gout_c = gout.reshape(-1).contiguous()
+    return dev, cores_c, idx_c, gout_c
+
+
 def tt_eval_at(cores, idx, stream=None):
-    """x_e = G_1[i_1] ... G_d[i_d] at int64 row-major linear indices (FP32)."""
+    """x_e = G_1[i_1] ... G_d[i_d] at int64 row-major linear indices (FP32).
+    An index outside [0, prod(dims)) raises TTError(TT_EINVAL) (the kernel
+    skips it and reports it; nothing out of bounds is read)."""
     d, dims, ranks = _core_meta(cores)
-    cores = [g.contiguous() for g in cores]
-    idx = idx.contiguous()
+    dev, cores_c, idx_c, _ = _eval_operands(cores, idx)
     st, st_ptr = _stream(stream)
-    with torch.cuda.device(idx.device), torch.cuda.stream(st):
-        out = torch.empty(idx.numel(), dtype=torch.float32, device=idx.device)
-        ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores])
-        _check(lib().tt_eval_at(d, _i64(dims), _i64(ranks), ptrs, ctypes.c_void_p(idx.data_ptr()),
-                                idx.numel(), ctypes.c_void_p(out.data_ptr()), st_ptr))
-    return out
+    with torch.cuda.device(dev), torch.cuda.stream(st):
+        out = torch.empty(idx_c.numel(), dtype=torch.float32, device=dev)
+        ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores_c])
+        _check(lib().tt_eval_at(d, _i64(dims), _i64(ranks), ptrs, ctypes.c_void_p(idx_c.data_ptr()),
+                                idx_c.numel(), ctypes.c_void_p(out.data_ptr()), st_ptr))
+    return out.view(idx.shape)
 
 
 def tt_eval_at_backward(cores, idx, gout, stream=None):
-    """Core gradients of sum_e gout_e x_e (FP32), fresh zeroed buffers."""
+    """Core gradients of sum_e gout_e x_e (FP32), fresh zeroed buffers.
+    Deterministic: the same inputs give bitwise-equal gradients."""
     d, dims, ranks = _core_meta(cores)
-    cores = [g.contiguous() for g in cores]
+    dev, cores_c, idx_c, gout_c = _eval_operands(cores, idx, gout)
     st, st_ptr = _stream(stream)
-    with torch.cuda.device(idx.device), torch.cuda.stream(st):
-        grads = [torch.zeros_like(g) for g in cores]
-        ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores])
+    with torch.cuda.device(dev), torch.cuda.stream(st):
+        grads = [torch.zeros_like(g) for g in cores_c]
+        ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores_c])
         gptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in grads])
         _check(lib().tt_eval_at_backward(d, _i64(dims), _i64(ranks), ptrs,
-                                         ctypes.c_void_p(idx.contiguous().data_ptr()), idx.numel(),
-                                         ctypes.c_void_p(gout.contiguous().data_ptr()), gptrs, st_ptr))
+                                         ctypes.c_void_p(idx_c.data_ptr()), idx_c.numel(),
+                                         ctypes.c_void_p(gout_c.data_ptr()), gptrs, st_ptr))
     return grads
 
 

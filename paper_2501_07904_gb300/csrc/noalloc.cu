@@ -2,12 +2,16 @@
 // callers that cannot allocate device memory during the call.
 //
 // The scratch lives in a file-scope __device__ array of kNoAllocScratchBytes.
-// Every GPU that loads this library reserves that much memory until the
+// The CUDA runtime loads this file's module (and so reserves the array on a
+// device) when the module is first used on that device -- with the default
+// lazy module loading, that is the first tt_full_noalloc call there, not the
+// loading of the library.  From then on the device holds the array until the
 // process exits.  In host code the array's name is only a host-side stand-in,
 // so its device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and cached; the first call
-// on a device does this lookup, so make that first call before capturing work
-// on that device into a stream.
+// cudaGetSymbolAddress (with that device current) and cached.  That first
+// call on a device may therefore allocate device memory and synchronize: make
+// it before another allocator's pool takes the device's memory and before
+// capturing work on that device into a stream.
 #include <stdio.h>
 
 #include <mutex>
