@@ -184,6 +184,55 @@ tt_status tt_utv(const void* A, int32_t dtype, int32_t d, const int64_t* dims, d
                  const tt_opts* opts, tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx,
                  void* stream, tt_result* out);
 
+/* One tensor decomposed by P processes (one GPU each), every process holding
+ * an equal slab of one mode: mode 1 for the right-to-left sweep (TT-URV,
+ * Alg. 3), whose unfoldings C_k = [I_1..I_{k-1}, I_k r_k] keep i_1 as their
+ * slowest row index, and mode d for the left-to-right sweep (TT-ULV, Alg. 1/2),
+ * whose unfoldings keep i_d as their fastest column index (Def. 2.1) -- so
+ * every carry stays within its slab.  Per step the Gram matrix (exact path)
+ * or the sketch, the projection's Gram B^T B and the squared norms are
+ * partial sums over the slabs, summed over ranks by `allreduce` (FP64, in
+ * place); the small factorizations then run identically on every rank, the
+ * sketch rows a slab draws are those of its own rows of the whole unfolding,
+ * and the carries stay local.  A step whose sketch is the identity gathers
+ * its whole unfolding by `allgather` and the rest of the sweep runs on every
+ * rank alike; the partitioned last core is gathered.  Every rank returns the
+ * same ranks, errors and (whole) cores, equal to tt_utv of the whole tensor
+ * up to the summation order of the partial sums. */
+
+/* Sum of `count` doubles of device memory over all ranks, in place.  Every
+ * rank makes the same calls in the same order.  The work that produces buf
+ * is already enqueued on `stream`; the callee orders its communication after
+ * it and the library's later work after the result (e.g. a NCCL all-reduce
+ * on that stream, or a synchronize, a host-staged sum and a copy back).
+ * Returns 0 or a tt_status. */
+typedef int32_t (*tt_allreduce_fn)(double* buf, int64_t count, void* stream, void* ctx);
+/* Concatenation in rank order: every rank contributes `bytes` bytes of
+ * device memory from send; recv (nranks * bytes) receives rank 0's block
+ * first.  Same ordering rules as tt_allreduce_fn. */
+typedef int32_t (*tt_allgather_fn)(const void* send, void* recv, int64_t bytes, void* stream,
+                                   void* ctx);
+
+typedef struct {
+  int32_t nranks;             /* P >= 1 (1: no partition, tt_utv) */
+  int32_t rank;               /* this process, 0 .. P-1; its slab is rank * I_p / P .. */
+  tt_allreduce_fn allreduce;  /* required when P > 1 */
+  tt_allgather_fn allgather;  /* required when P > 1 */
+  void* ctx;                  /* passed to both */
+} tt_shard;
+
+/* tt_utv over a partitioned tensor.
+ *   A_local  device (or host), this rank's slab: dims with mode 1 (TT_RL) or
+ *            mode d (TT_LR) replaced by dims[p] / P, row-major
+ *   dims     the WHOLE tensor's mode sizes; dims[p] must be a multiple of P
+ *   the rest as tt_utv (TT_URV/TT_RL or TT_ULV/TT_LR and their Alg. 4
+ *   pairings); opts->reverse and TT-SVD return TT_EUNSUPPORTED.
+ * Every rank receives the whole result in *out. */
+tt_status tt_utv_sharded(const void* A_local, int32_t dtype, int32_t d, const int64_t* dims,
+                         double eps, const int64_t* fixed_ranks, int32_t variant, int32_t direction,
+                         const tt_opts* opts, tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx,
+                         void* stream, const tt_shard* shard, tt_result* out);
+
 /* TT-SVD (the comparison method of Sec. 4) through the same sweep: the small
  * factor is a Jacobi eigen-decomposition of the Gram matrix, so the kept
  * basis is the leading singular subspace and ||E_k||^2 = sum of the dropped

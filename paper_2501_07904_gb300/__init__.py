@@ -16,6 +16,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import threading
 from dataclasses import dataclass, field
 
 import torch
@@ -33,7 +34,8 @@ TT_URV, TT_ULV = 0, 1
 TT_RL, TT_LR = 0, 1
 
 # Every symbol include/ttutv.h declares.
-EXPORTS = ["tt_opts_default", "tt_utv", "tt_svd", "tt_result_free", "tt_full_work_bytes",
+EXPORTS = ["tt_opts_default", "tt_utv", "tt_utv_sharded", "tt_svd", "tt_result_free",
+           "tt_full_work_bytes",
            "tt_full", "tt_full_noalloc", "tt_full_noalloc_max_work_bytes", "tt_rse_work_bytes",
            "tt_rse", "tt_eval_at",
            "tt_eval_at_backward", "tt_sketch_matrix", "tt_kernel_launches", "tt_last_error",
@@ -68,6 +70,16 @@ class tt_result(ctypes.Structure):
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                ctypes.c_void_p)
+ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                ctypes.c_void_p, ctypes.c_void_p)
+
+
+class tt_shard(ctypes.Structure):
+    _fields_ = [("nranks", ctypes.c_int32), ("rank", ctypes.c_int32),
+                ("allreduce", ALLREDUCE_FN), ("allgather", ALLGATHER_FN),
+                ("ctx", ctypes.c_void_p)]
 
 _lib_handle = None
 
@@ -88,6 +100,10 @@ def lib():
     L.tt_utv.argtypes = [P, I32, I32, PI64, D, PI64, I32, I32, ctypes.POINTER(tt_opts), ALLOC_FN,
                          FREE_FN, P, P, ctypes.POINTER(tt_result)]
     L.tt_utv.restype = I32
+    L.tt_utv_sharded.argtypes = [P, I32, I32, PI64, D, PI64, I32, I32, ctypes.POINTER(tt_opts),
+                                 ALLOC_FN, FREE_FN, P, P, ctypes.POINTER(tt_shard),
+                                 ctypes.POINTER(tt_result)]
+    L.tt_utv_sharded.restype = I32
     L.tt_svd.argtypes = [P, I32, I32, PI64, D, PI64, I32, ctypes.POINTER(tt_opts), ALLOC_FN,
                          FREE_FN, P, P, ctypes.POINTER(tt_result)]
     L.tt_svd.restype = I32
@@ -161,8 +177,25 @@ class _TorchAllocator:
     def take(self, ptr, shape, dtype):
         buf = self.live.pop(ptr)
         n = math.prod(shape)
-        el = torch.empty((), dtype=dtype).element_size()
+        el = _ELSIZE[dtype]
         return buf[: n * el].view(dtype).view(shape)
+
+
+_ELSIZE = {torch.float32: 4, torch.float64: 8}
+_tls = threading.local()
+
+
+def _allocator(device):
+    """The calling thread's allocator for ``device`` (its ctypes callbacks are
+    built once and reused by every call on that thread)."""
+    cache = getattr(_tls, "alloc", None)
+    if cache is None:
+        cache = _tls.alloc = {}
+    a = cache.get(device)
+    if a is None:
+        a = cache[device] = _TorchAllocator(device)
+    a.live.clear()
+    return a
 
 
 @dataclass
@@ -180,13 +213,16 @@ class TTResult:
 
 
 def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream,
-           timing=False, orth="auto", reverse=False, power_iters=0):
+           timing=False, orth="auto", reverse=False, power_iters=0, dims=None, shard=None):
     if not isinstance(A, torch.Tensor):
         raise TypeError("A must be a torch.Tensor")
     if A.dtype not in (torch.float32, torch.float64):
         raise TypeError("A must be float32 or float64")
     A = A.contiguous()
     d = A.dim()
+    dims = list(A.shape) if dims is None else [int(x) for x in dims]
+    if len(dims) != d:
+        raise ValueError("dims must have one entry per mode of A")
     dev = A.device if A.is_cuda else torch.device("cuda", torch.cuda.current_device())
     st, st_ptr = _stream(stream)
     opts = tt_opts()
@@ -207,15 +243,16 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
     if timing:
         tbuf = (ctypes.c_double * (TT_MAXD * TT_NPHASES))()
         opts.phase_ms = ctypes.cast(tbuf, ctypes.POINTER(ctypes.c_double))
-    dims = _i64(A.shape)
+    dims = _i64(dims)
     fr = _i64(ranks) if ranks is not None else None
-    alloc = _TorchAllocator(dev)
+    alloc = _allocator(dev)
     res = tt_result()
     dtype = TT_F64 if A.dtype == torch.float64 else TT_F32
     with torch.cuda.device(dev), torch.cuda.stream(st):
+        tail = (ctypes.byref(shard.cstruct),) if shard is not None else ()
         status = fn(ctypes.c_void_p(A.data_ptr()), dtype, d, dims,
                     float(eps) if eps is not None else 0.0, fr, *extra, ctypes.byref(opts),
-                    alloc._alloc, alloc._free, None, st_ptr, ctypes.byref(res))
+                    alloc._alloc, alloc._free, None, st_ptr, *tail, ctypes.byref(res))
         if status != 0:
             msg = lib().tt_last_error().decode()
             alloc.live.clear()
@@ -259,6 +296,108 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
     v = ({"URV": TT_URV, "ULV": TT_ULV}[variant], {"RL": TT_RL, "LR": TT_LR}[direction])
     return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
                   weights, stream, timing, orth, reverse, power_iters)
+
+
+class _DevBuf:
+    """A raw device pointer seen as a 1-D torch tensor (no copy)."""
+
+    def __init__(self, ptr, n, typestr, device):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+        self.device = device
+
+
+def _device_view(ptr, n, dtype, device):
+    typestr = {torch.float64: "<f8", torch.uint8: "|u1"}[dtype]
+    return torch.as_tensor(_DevBuf(ptr, n, typestr, device), device=device)
+
+
+class ShardComm:
+    """Communication of one rank of a partitioned sweep (tt_utv_sharded).
+
+    allreduce(t) sums a 1-D FP64 device tensor over the ranks in place;
+    allgather(send, recv) concatenates 1-D uint8 device tensors in rank
+    order.  Both are called on the sweep's host thread with the sweep's CUDA
+    stream current and must order their work on it.  Subclasses provide the
+    transport; the C callbacks built here only wrap the library's raw device
+    pointers as tensors."""
+
+    def __init__(self, rank, nranks, device):
+        self.rank, self.nranks, self.device = int(rank), int(nranks), torch.device(device)
+        self._ar = ALLREDUCE_FN(self._c_allreduce)
+        self._ag = ALLGATHER_FN(self._c_allgather)
+        self.cstruct = tt_shard(self.nranks, self.rank, self._ar, self._ag, None)
+        self.calls = 0
+
+    def _c_allreduce(self, ptr, count, stream, ctx):
+        try:
+            with torch.cuda.stream(torch.cuda.ExternalStream(stream or 0, device=self.device)):
+                self.allreduce(_device_view(ptr, count, torch.float64, self.device))
+            self.calls += 1
+            return 0
+        except Exception:  # reported to the library as a failed collective
+            return 4
+
+    def _c_allgather(self, send, recv, nbytes, stream, ctx):
+        try:
+            with torch.cuda.stream(torch.cuda.ExternalStream(stream or 0, device=self.device)):
+                self.allgather(_device_view(send, nbytes, torch.uint8, self.device),
+                               _device_view(recv, nbytes * self.nranks, torch.uint8, self.device))
+            self.calls += 1
+            return 0
+        except Exception:
+            return 4
+
+    def allreduce(self, t):
+        raise NotImplementedError
+
+    def allgather(self, send, recv):
+        raise NotImplementedError
+
+
+class TorchDistComm(ShardComm):
+    """torch.distributed transport (NCCL for one GPU per process, the usual
+    multi-GPU launch).  The sweep's stream is current, so the collectives are
+    ordered after the work that produced their input and before what reads
+    their output."""
+
+    def __init__(self, group=None, device=None):
+        import torch.distributed as dist
+        self.dist, self.group = dist, group
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        super().__init__(dist.get_rank(group), dist.get_world_size(group), dev)
+
+    def allreduce(self, t):
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group)
+
+    def allgather(self, send, recv):
+        self.dist.all_gather_into_tensor(recv, send, group=self.group)
+
+
+def slab(A, nranks, rank, direction="RL"):
+    """This rank's slab of the whole tensor A for tt_utv_sharded: an equal part
+    of mode 1 (right-to-left sweep) or of mode d (left-to-right sweep)."""
+    axis = 0 if direction == "RL" else A.dim() - 1
+    size = A.shape[axis]
+    if size % nranks:
+        raise ValueError(f"mode {axis + 1} ({size}) does not split into {nranks} equal slabs")
+    b = size // nranks
+    return A.narrow(axis, rank * b, b).contiguous()
+
+
+def tt_utv_sharded(A_local, dims, comm, eps=None, ranks=None, variant="URV", direction=None,
+                   precision="fp32", seed=0, oversample=16, l_full=256, small="auto", weights=None,
+                   stream=None, timing=False, orth="auto", power_iters=0):
+    """tt_utv of a tensor partitioned over ranks (one GPU each): A_local is this
+    rank's slab (see slab()), dims the whole tensor's mode sizes, comm a
+    ShardComm.  Every rank returns the whole result."""
+    if (eps is None) == (ranks is None):
+        raise ValueError("give exactly one of eps or ranks")
+    if direction is None:
+        direction = "RL" if variant == "URV" else "LR"
+    v = ({"URV": TT_URV, "ULV": TT_ULV}[variant], {"RL": TT_RL, "LR": TT_LR}[direction])
+    return _sweep(lib().tt_utv_sharded, A_local, eps, ranks, v, precision, seed, oversample, l_full,
+                  small, weights, stream, timing, orth, False, power_iters, dims=dims, shard=comm)
 
 
 def tt_svd(A, eps=None, ranks=None, direction="LR", precision="fp32", l_full=256, small="auto",

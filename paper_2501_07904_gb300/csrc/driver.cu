@@ -101,6 +101,59 @@ struct Buf {
     if (!(buf).get(bytes)) return fail(TT_ENOMEM, "allocator returned NULL");        \
   } while (0)
 
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// One scratch block per sweep, carved step by step: every scratch buffer of
+// a step comes out of it, so a sweep makes a few allocator calls instead of
+// one per buffer (each is a round trip into the caller's allocator).  A step
+// reserves the total of its carve-outs first; the block only grows (with 25%
+// headroom, released stream-ordered) when a step needs more than it holds.
+struct Scratch {
+  Alloc* a;
+  void* p = nullptr;
+  size_t cap = 0, off = 0;
+  explicit Scratch(Alloc* a_) : a(a_) {}
+  Scratch(const Scratch&) = delete;
+  ~Scratch() {
+    if (p) a->put(p);
+  }
+  bool reserve(size_t total) {
+    off = 0;
+    if (total <= cap) return true;
+    if (p) a->put(p);
+    cap = total + total / 4;
+    p = a->get(cap);
+    if (!p) cap = 0;
+    return p != nullptr;
+  }
+  void* take(size_t bytes) {
+    bytes = align256(bytes ? bytes : 1);
+    if (!p || off + bytes > cap) return nullptr;
+    void* q = (char*)p + off;
+    off += bytes;
+    return q;
+  }
+};
+
+// A buffer carved from the step's Scratch (released with it).
+struct Piece {
+  void* p = nullptr;
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+#define TT_RESERVE(scr, bytes)                                                      \
+  do {                                                                              \
+    if (!(scr).reserve(bytes)) return fail(TT_ENOMEM, "allocator returned NULL");   \
+  } while (0)
+#define TT_TAKE(piece, bytes)                                                       \
+  do {                                                                              \
+    (piece).p = scr.take(bytes);                                                    \
+    if (!(piece).p) return fail(TT_ENOMEM, "step scratch larger than reserved");    \
+  } while (0)
+
 ttk::StepInfo* pinned_info() {
   thread_local ttk::StepInfo* h = nullptr;
   thread_local ttk::StepInfo fallback;
@@ -146,6 +199,8 @@ int64_t sketch_size(int64_t nb, int64_t no, int64_t r_prev, int64_t p, int64_t r
 }
 
 // CUDA-event timing of the sweep's phases (only when opts.phase_ms is set).
+// Events come from a per-thread pool that is created once and reused, so a
+// timed sweep adds only event records to its stream.
 struct PhaseTimer {
   double* out = nullptr;
   cudaStream_t st = nullptr;
@@ -155,13 +210,27 @@ struct PhaseTimer {
   };
   std::vector<Rec> recs;
   int open = -1;
+  static std::vector<cudaEvent_t>& pool() {
+    thread_local std::vector<cudaEvent_t> p;
+    return p;
+  }
+  size_t used = 0;  // events of the pool taken by this sweep
+  cudaEvent_t take() {
+    auto& p = pool();
+    if (used == p.size()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      p.push_back(e);
+    }
+    return p[used++];
+  }
   void begin(int step, int phase) {
     if (!out) return;
-    Rec r{step, phase, nullptr, nullptr};
-    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
-      cudaGetLastError();
-      return;
-    }
+    Rec r{step, phase, take(), take()};
+    if (!r.a || !r.b) return;
     cudaEventRecord(r.a, st);
     recs.push_back(r);
     open = (int)recs.size() - 1;
@@ -171,23 +240,16 @@ struct PhaseTimer {
     cudaEventRecord(recs[open].b, st);
     open = -1;
   }
-  // after a stream synchronization
+  // after a stream synchronization; the pool's events are free again
   void collect() {
     for (auto& r : recs) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && out)
         out[r.step * TT_NPHASES + r.phase] += ms;
       cudaGetLastError();
-      cudaEventDestroy(r.a);
-      cudaEventDestroy(r.b);
     }
     recs.clear();
-  }
-  ~PhaseTimer() {
-    for (auto& r : recs) {
-      cudaEventDestroy(r.a);
-      cudaEventDestroy(r.b);
-    }
+    used = 0;
   }
 };
 
@@ -249,7 +311,7 @@ bool host_pointer(const void* p) {
 template <typename W>
 tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* dims, double eps,
                     const int64_t* fixed, SweepCfg cfg, const tt_opts& o, Alloc& al,
-                    tt_result* out) {
+                    tt_result* out, const tt_shard* sh = nullptr) {
   constexpr bool W64 = std::is_same<W, double>::value;
   cudaStream_t st = al.st;
   const int64_t p_over = o.oversample;
@@ -259,8 +321,37 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   if (o.weights)
     for (int i = 0; i < d - 1; ++i) w[i] = o.weights[i];
 
+  // Partition over ranks (tt_utv_sharded): every rank holds the slab
+  // rank * slab .. of the partitioned mode (mode 1 for the right-to-left URV
+  // sweep, whose unfoldings keep it as their slowest row index; mode d for
+  // the left-to-right ULV sweep, their fastest column index).  dl are the
+  // local mode sizes; the unfoldings stay partitioned (`active`) until a step
+  // needs a whole unfolding (an identity sketch gathers it).
+  bool active = sh && sh->nranks > 1;
+  const int pm = cfg.urv ? 0 : d - 1;
+  int64_t dl[TT_MAXD];
+  for (int k = 0; k < d; ++k) dl[k] = dims[k];
+  const int64_t slab = active ? dims[pm] / sh->nranks : dims[pm];
+  if (active) dl[pm] = slab;
+  auto reduce = [&](double* buf, int64_t count) -> tt_status {
+    if (!active) return TT_OK;
+    const int32_t r = sh->allreduce(buf, count, (void*)st, sh->ctx);
+    return r == 0 ? TT_OK : fail(r > 0 && r <= TT_EUNSUPPORTED ? (tt_status)r : TT_ECUDA,
+                                 "the all-reduce callback failed");
+  };
+  auto gather = [&](const void* send, void* recv, int64_t bytes) -> tt_status {
+    const int32_t r = sh->allgather(send, recv, bytes, (void*)st, sh->ctx);
+    return r == 0 ? TT_OK : fail(r > 0 && r <= TT_EUNSUPPORTED ? (tt_status)r : TT_ECUDA,
+                                 "the all-gather callback failed");
+  };
+#define TT_RED(buf, count)                        \
+  do {                                            \
+    const tt_status rs_ = reduce((buf), (count)); \
+    if (rs_ != TT_OK) return rs_;                 \
+  } while (0)
+
   int64_t total = 1;
-  for (int k = 0; k < d; ++k) total *= dims[k];
+  for (int k = 0; k < d; ++k) total *= dl[k];
 
   // Input in the working precision, on the device.
   const bool host_in = host_pointer(A_in);
@@ -281,8 +372,11 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     staged.reset();
   }
 
+  // sweep-long device records: scalars, per-step carry norms, the error
+  // word and the small factor's StepInfo, in one block
+  const size_t scal_bytes = align256(sizeof(double) * (4 + 2 * TT_MAXD));
   Buf scal(&al);
-  TT_ALLOC(scal, sizeof(double) * (4 + 2 * TT_MAXD));
+  TT_ALLOC(scal, scal_bytes + sizeof(ttk::StepInfo));
   double* d_scal = scal.as<double>();
   double* d_x2first = d_scal;            // ||A||^2 when the first step is sketched
   double* d_carry2 = d_scal + 4;         // per step: ||carry||^2 (sum of squares of stored values)
@@ -291,9 +385,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   int* herr = pinned_err();
   const bool mixed = !W64 && o.precision == TT_P_MIXED;
   const MM mm_all{mixed, d_err, st};
-  Buf dinfo(&al);
-  TT_ALLOC(dinfo, sizeof(ttk::StepInfo));
+  Piece dinfo;
+  dinfo.p = (char*)scal.p + scal_bytes;
   ttk::StepInfo* hinfo = pinned_info();
+  Scratch scr(&al);
 
   memset(out, 0, sizeof(*out));
   out->d = d;
@@ -325,24 +420,44 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
 
   for (int s = 0; s < d - 1; ++s) {
     const int k = cfg.urv ? d - s : s + 1;  // core being separated (1-based)
-    int64_t m, n;
-    if (cfg.urv) {
-      m = 1;
-      for (int t = 0; t < k - 1; ++t) m *= dims[t];
-      n = dims[k - 1] * r_carry;
-    } else {
-      m = r_carry * dims[k - 1];
-      n = 1;
-      for (int t = k; t < d; ++t) n *= dims[t];
+    int64_t m, n, m_g, n_g;  // local and global unfolding sizes
+    {
+      const int64_t* cd = active ? dl : dims;
+      if (cfg.urv) {
+        m = m_g = 1;
+        for (int t = 0; t < k - 1; ++t) {
+          m *= cd[t];
+          m_g *= dims[t];
+        }
+        n = n_g = dims[k - 1] * r_carry;
+      } else {
+        m = m_g = r_carry * dims[k - 1];
+        n = n_g = 1;
+        for (int t = k; t < d; ++t) {
+          n *= cd[t];
+          n_g *= dims[t];
+        }
+      }
     }
     const int u = cfg.urv ? k - 1 : k;  // unfolding number 1..d-1
-    const int64_t nb = cfg.urv ? n : m, no = cfg.urv ? m : n;
+    // nb: the basis side (never partitioned); no: the other side's local
+    // size, no_g its size over all ranks (it decides the sketch)
+    const int64_t nb = cfg.urv ? n : m, no_g = cfg.urv ? m_g : n_g;
+    int64_t no = cfg.urv ? m : n;
     const double dscale = fixed ? 0.0 : (w[u - 1] * eps) * (w[u - 1] * eps);
     const int64_t rfix = fixed ? fixed[u - 1] : -1;
-    const int64_t rcap = std::min<int64_t>(std::min<int64_t>(nb, no), ttk::kMaxSmall);
+    // A tolerance within a few hundred FP32 ulps of ||C||^2 (eps_k^2 below
+    // 1e-10 of ||A||^2) keeps directions whose singular values are ~1e-6 of
+    // ||C||: FP32 accumulation (or the tensor cores' drift) would bury them in
+    // the sketch, the range basis, the projection B = C W, the carry and the
+    // core, whose error energy of ~1e-12 of ||C||^2 already exceeds eps_k^2.
+    // Every product of such a step then uses compensated sums of exact
+    // products on the SIMT path.
+    const bool precise = !W64 && !fixed && dscale < 1e-10;
+    const int64_t rcap = std::min<int64_t>(std::min<int64_t>(nb, no_g), ttk::kMaxSmall);
     const bool exact = nb <= l_full;
     const bool first = (s == 0);
-    if (cfg.svd && !exact && no > ttk::kMaxSmall)
+    if (cfg.svd && !exact && no_g > ttk::kMaxSmall)
       return fail(TT_EUNSUPPORTED, "TT-SVD step with both unfolding sides above 256");
 
     // A tolerance below ~n u_fp32 of ||C||^2 cannot be resolved from an
@@ -368,8 +483,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     prm.delta2_scale = dscale;
     prm.delta2 = (normA2 >= 0.0) ? dscale * normA2 : 0.0;
 
-    Buf zb(&al), carry(&al), core(&al), ws(&al), ws2(&al), gb(&al);
-    Buf omega(&al), yb(&al), s1b(&al), w1b(&al), wb(&al), bb(&al), gy(&al), gwb(&al);
+    Buf carry(&al), core(&al), ws_extra(&al);
+    Buf cfull(&al);  // the whole unfolding, gathered for an identity sketch
+    Piece zb, ws, ws2, gb, omega, yb, s1b, w1b, wb, bb, gy, gwb;
+    size_t ws_bytes = 0;  // size of ws (reused by the carry and core products)
     int64_t r = 1, l = 0;
     bool small64 = false;
     bool acc_gram = false;  // the factored Gram was formed with compensated sums
@@ -383,8 +500,16 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     MM mm = mm_all;
     if (exact) {
       mm.tc = mm_all.tc && !tight(nb);
-      TT_ALLOC(gb, (size_t)nb * nb * sizeof(double));
-      TT_ALLOC(ws, std::max(mm_ws<W>(mm, nb, nb, no, true), ttk::small_ws_bytes((int)nb, true)));
+      // the carry product's scratch is bounded by its widest rank
+      const int64_t rmax = rcap;
+      ws_bytes = std::max(mm_ws<W>(mm, nb, nb, no, true), ttk::small_ws_bytes((int)nb, true));
+      ws_bytes = std::max(ws_bytes, cfg.urv ? mm_ws<W>(mm_all, m, rmax, n, false)
+                                            : mm_ws<W>(mm_all, rmax, n, m, false));
+      TT_RESERVE(scr, align256((size_t)nb * nb * sizeof(double)) + align256((size_t)nb * nb * sizeof(W)) +
+                          align256(ws_bytes));
+      TT_TAKE(gb, (size_t)nb * nb * sizeof(double));
+      TT_TAKE(zb, (size_t)nb * nb * sizeof(W));
+      TT_TAKE(ws, ws_bytes);
       const bool acc = !W64 && tight(nb);
       acc_gram = acc;
       tm.begin(s, TT_PH_GRAM);
@@ -394,6 +519,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       else
         TT_CK(mm_run<W>(mm, {C, n, true}, {C, n, false}, m, m, n, nullptr, 0, gb.as<double>(), true,
                         nullptr, ws.p, acc, false, false, false), "Gram C C^T");
+      TT_RED(gb.as<double>(), nb * nb);
       tm.end();
       small64 = choose_small64(nb);
       prm.n = (int)nb;
@@ -404,7 +530,6 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       prm.x2_dev = nullptr;
       prm.piv_tol = small64 ? (small_df ? 1e-13 : 1e-15) : 1e-6;
       prm.df_math = small_df ? 1 : 0;
-      TT_ALLOC(zb, (size_t)nb * nb * sizeof(W));
       ldz = nb;
       tm.begin(s, TT_PH_SMALL);
       TT_CK(ttk::small_factor(gb.as<double>(), prm, small64, zb.p, W64, (int)ldz, ws.p,
@@ -420,33 +545,95 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       r = hinfo->r;
       Zp = zb.as<W>();
     } else {
-      l = cfg.svd ? std::min<int64_t>(no, ttk::kMaxSmall)
-                  : sketch_size(nb, no, r_prev, p_over, rfix);
+      l = cfg.svd ? std::min<int64_t>(no_g, ttk::kMaxSmall)
+                  : sketch_size(nb, no_g, r_prev, p_over, rfix);
       const double* x2_dev = first ? d_x2first : (d_carry2 + (s - 1));
       if (first) {
-        Buf sw(&al);
-        TT_ALLOC(sw, ttk::sumsq_ws_bytes(total));
+        TT_RESERVE(scr, ttk::sumsq_ws_bytes(total));
+        Piece sw;
+        TT_TAKE(sw, ttk::sumsq_ws_bytes(total));
         TT_CK(ttk::sumsq(C, W64, m * n, d_x2first, sw.p, st), "sum of squares");
+        TT_RED(d_x2first, 1);
         prm.normA2_dev = d_x2first;
         prm.normA2_is_trace = 0;
       }
       while (true) {
-        const bool identity = l >= no;
+        const bool identity = l >= no_g;
+        if (identity && active) {
+          // Omega = I needs the whole unfolding: gather it; this step and the
+          // rest of the sweep then run on every rank alike
+          const int64_t lb = m * n;
+          Buf gb_all(&al);
+          TT_ALLOC(cfull, (size_t)m_g * n_g * sizeof(W));
+          if (cfg.urv) {
+            const tt_status sg = gather(C, cfull.p, lb * (int64_t)sizeof(W));
+            if (sg != TT_OK) return sg;
+          } else {
+            TT_ALLOC(gb_all, (size_t)lb * sh->nranks * sizeof(W));
+            const tt_status sg = gather(C, gb_all.p, lb * (int64_t)sizeof(W));
+            if (sg != TT_OK) return sg;
+            TT_CK(ttk::unshard_cols(gb_all.p, cfull.p, W64, sh->nranks, m, n / dl[d - 1], dl[d - 1], st),
+                  "interleave gathered columns");
+          }
+          C = cfull.as<W>();
+          m = m_g;
+          n = n_g;
+          no = no_g;
+          active = false;
+        }
         small64 = choose_small64(l);
         mm.tc = mm_all.tc && !tight(l);
-        if (!identity) TT_ALLOC(omega, (size_t)no * l * sizeof(W));
+        const bool powered = o.power_iters > 0 && !identity;
+        const bool whiten_l = !W64 && small64;
+        {
+          // this width's carve-outs (the previous width's are dead)
+          size_t wsz = 0;
+          wsz = std::max(wsz, mm_ws<W>(mm, nb, l, no, false));
+          wsz = std::max(wsz, mm_ws<W>(mm, l, l, nb, true));
+          wsz = std::max(wsz, mm_ws<W>(mm, nb, l, l, false));
+          wsz = std::max(wsz, mm_ws<W>(mm, no, l, nb, false));
+          wsz = std::max(wsz, mm_ws<W>(mm, l, l, no, true));
+          const int64_t rmax = std::min<int64_t>(rcap, l);
+          wsz = std::max(wsz, cfg.urv ? mm_ws<W>(mm_all, m, rmax, l, false)
+                                      : mm_ws<W>(mm_all, rmax, n, l, false));
+          wsz = std::max(wsz, cfg.urv ? mm_ws<W>(mm_all, rmax, n, l, false)
+                                      : mm_ws<W>(mm_all, m, rmax, l, false));
+          ws_bytes = wsz;
+          const size_t nl = align256((size_t)nb * l * sizeof(W)), ol = align256((size_t)no * l * sizeof(W));
+          const size_t ll8 = align256((size_t)l * l * sizeof(double)), llw = align256((size_t)l * l * sizeof(W));
+          size_t tot = (identity ? 0 : ol) + nl + align256(wsz) + align256(ttk::small_ws_bytes((int)l, true)) +
+                       ll8 + llw + 2 * nl + ol + (whiten_l ? ll8 : 0) + llw;
+          if (powered) tot += ol;
+          if (active) {
+            // a slab's partial sketch is formed in FP64 and summed over ranks
+            wsz = std::max(wsz, mm_ws<W>(mm, nb, l, no, true));
+            ws_bytes = wsz;
+            tot += align256(wsz) + align256((size_t)nb * l * sizeof(double));
+          }
+          TT_RESERVE(scr, tot);
+        }
+        if (!identity) TT_TAKE(omega, (size_t)no * l * sizeof(W));
         tm.begin(s, TT_PH_SKETCH);
-        if (!identity)
-          TT_CK(ttk::fill_sketch(omega.p, W64, no, l, o.seed, (uint32_t)k, false, st), "sketch matrix");
-        TT_ALLOC(yb, (size_t)nb * l * sizeof(W));
-        size_t wsz = 0;
-        wsz = std::max(wsz, mm_ws<W>(mm, nb, l, no, false));
-        wsz = std::max(wsz, mm_ws<W>(mm, l, l, nb, true));
-        wsz = std::max(wsz, mm_ws<W>(mm, nb, l, l, false));
-        wsz = std::max(wsz, mm_ws<W>(mm, no, l, nb, false));
-        wsz = std::max(wsz, mm_ws<W>(mm, l, l, no, true));
-        TT_ALLOC(ws, wsz);
-        TT_ALLOC(ws2, ttk::small_ws_bytes((int)l, true));
+        if (!identity) {
+          // a slab draws the sketch rows of its own rows (URV: a contiguous
+          // block of rows; ULV: the columns of its slab of mode d, strided)
+          const int64_t blk = !active ? 0 : (cfg.urv ? no : dl[d - 1]);
+          const int64_t stride = cfg.urv ? 0 : dims[d - 1];
+          const int64_t off = !active ? 0 : (int64_t)sh->rank * (cfg.urv ? no : dl[d - 1]);
+          TT_CK(ttk::fill_sketch(omega.p, W64, no, l, o.seed, (uint32_t)k, false, st, blk, stride, off),
+                "sketch matrix");
+        }
+        TT_TAKE(yb, (size_t)nb * l * sizeof(W));
+        TT_TAKE(ws, ws_bytes);
+        TT_TAKE(ws2, ttk::small_ws_bytes((int)l, true));
+        Piece y64;  // a slab's partial sketch in FP64
+        if (active) TT_TAKE(y64, (size_t)nb * l * sizeof(double));
+        // Y = sum over ranks of the slabs' partial sketches (FP64), rounded once
+        auto sum_sketch = [&]() -> tt_status {
+          TT_RED(y64.as<double>(), nb * l);
+          TT_CK(ttk::cast_copy(y64.p, true, yb.p, W64, nb * l, st), "sketch to working precision");
+          return TT_OK;
+        };
         // Omega = I (l = N_o): Y is C^T / C itself, copied exactly.  On the
         // tensor cores C is split into two TF32 terms (Omega = +-1 is exact):
         // TF32 rounding noise in Y would enter every sketch column at ~2^-12
@@ -456,61 +643,26 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         else if (identity)
           TT_CK(ttk::copy2d(C, n, false, yb.p, l, nb, l, W64, st), "sketch C");
         else if (cfg.urv)
-          TT_CK(mm_run<W>(mm, {C, n, false}, {omega.as<W>(), l, true}, n, l, m, yb.as<W>(), l,
-                          nullptr, false, nullptr, ws.p, false, true, false, false), "sketch C^T Omega");
+          TT_CK(mm_run<W>(mm, {C, n, false}, {omega.as<W>(), l, true}, n, l, m, active ? nullptr : yb.as<W>(),
+                          l, active ? y64.as<double>() : nullptr, false, nullptr, ws.p, precise, true, false,
+                          false), "sketch C^T Omega");
         else
-          TT_CK(mm_run<W>(mm, {C, n, true}, {omega.as<W>(), l, true}, m, l, n, yb.as<W>(), l,
-                          nullptr, false, nullptr, ws.p, false, true, false, false), "sketch C Omega");
-        tm.end();
-        omega.reset();
-        // q power (subspace) iterations: Y <- X^T X Q, Q = Y R^{-1} from one
-        // shifted Cholesky-QR pass (Q spans what Y spans); X = C (URV) or
-        // C^T (ULV).  The same products as the sketch and the projection.
-        if (o.power_iters > 0 && !identity) {
-          Buf qb(&al), pb(&al), gq(&al), sq(&al);
-          TT_ALLOC(qb, (size_t)nb * l * sizeof(W));
-          TT_ALLOC(pb, (size_t)no * l * sizeof(W));
-          TT_ALLOC(gq, (size_t)l * l * sizeof(double));
-          TT_ALLOC(sq, (size_t)l * l * sizeof(W));
-          const bool q64 = o.orth_precision == TT_SMALL_FP64 ||
-                           (o.orth_precision == TT_SMALL_AUTO && (small64 || W64));
-          ttk::SmallParams pq;
-          memset(&pq, 0, sizeof(pq));
-          pq.n = (int)l;
-          pq.mode = ttk::SM_ORTH;
-          pq.r_fixed = -1;
-          pq.r_cap = (int)l;
-          pq.shift_rel = 4.0 * (double)l * (q64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
-          tm.begin(s, TT_PH_SKETCH);
-          for (int it = 0; it < o.power_iters; ++it) {
-            TT_CK(mm_run<W>(mm, {yb.as<W>(), l, false}, {yb.as<W>(), l, true}, l, l, nb, nullptr, 0,
-                            gq.as<double>(), true, nullptr, ws.p, !W64 && small64, true, true, false),
-                  "power iteration: Gram of Y");
-            TT_CK(ttk::small_factor(gq.as<double>(), pq, q64, sq.p, W64, (int)l, ws2.p,
-                                    dinfo.as<ttk::StepInfo>(), st), "power iteration: orthonormalize");
-            TT_CK(mm_run<W>(mm, {yb.as<W>(), l, true}, {sq.as<W>(), l, true}, nb, l, l, qb.as<W>(), l,
-                            nullptr, false, nullptr, ws.p, false, true, true, false),
-                  "power iteration: apply R^-1");
-            if (cfg.urv) {
-              TT_CK(mm_run<W>(mm, {C, n, true}, {qb.as<W>(), l, true}, m, l, n, pb.as<W>(), l, nullptr,
-                              false, nullptr, ws.p, false, true, true, false), "power iteration: C Q");
-              TT_CK(mm_run<W>(mm, {C, n, false}, {pb.as<W>(), l, true}, n, l, m, yb.as<W>(), l, nullptr,
-                              false, nullptr, ws.p, false, true, true, false), "power iteration: C^T P");
-            } else {
-              TT_CK(mm_run<W>(mm, {C, n, false}, {qb.as<W>(), l, true}, n, l, m, pb.as<W>(), l, nullptr,
-                              false, nullptr, ws.p, false, true, true, false), "power iteration: C^T Q");
-              TT_CK(mm_run<W>(mm, {C, n, true}, {pb.as<W>(), l, true}, m, l, n, yb.as<W>(), l, nullptr,
-                              false, nullptr, ws.p, false, true, true, false), "power iteration: C P");
-            }
-          }
-          tm.end();
+          TT_CK(mm_run<W>(mm, {C, n, true}, {omega.as<W>(), l, true}, m, l, n, active ? nullptr : yb.as<W>(),
+                          l, active ? y64.as<double>() : nullptr, false, nullptr, ws.p, precise, true, false,
+                          false), "sketch C Omega");
+        if (active && !identity) {
+          const tt_status sr = sum_sketch();
+          if (sr != TT_OK) return sr;
         }
-        // W = shifted Cholesky-QR3(Y): a shifted pass that cannot break
-        // down, then two plain passes; span(W[:, :j]) = span(Y[:, :j]).
-        TT_ALLOC(gy, (size_t)l * l * sizeof(double));
-        TT_ALLOC(s1b, (size_t)l * l * sizeof(W));
-        TT_ALLOC(w1b, (size_t)nb * l * sizeof(W));
-        TT_ALLOC(wb, (size_t)nb * l * sizeof(W));
+        tm.end();
+
+        // Shifted Cholesky-QR3: a shifted pass that cannot break down, then two
+        // plain passes; span(out[:, :j]) = span(src[:, :j]) for every j, the
+        // basis Householder QR gives up to column signs.
+        TT_TAKE(gy, (size_t)l * l * sizeof(double));
+        TT_TAKE(s1b, (size_t)l * l * sizeof(W));
+        TT_TAKE(w1b, (size_t)nb * l * sizeof(W));
+        TT_TAKE(wb, (size_t)nb * l * sizeof(W));
         ttk::SmallParams po;
         memset(&po, 0, sizeof(po));
         po.n = (int)l;
@@ -528,45 +680,85 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         // unit roundoff of the Cholesky's arithmetic (double-float: ~2^-48)
         const double u_c = orth_df ? 3.552713678800501e-15
                                    : orth64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
-        const W* src_pass = yb.as<W>();
-        W* dst_pass[3] = {w1b.as<W>(), wb.as<W>(), w1b.as<W>()};
-        tm.begin(s, TT_PH_ORTH);
-        for (int pass = 0; pass < 3; ++pass) {
-          // the smallest shift that keeps the first Cholesky positive definite
-          // (a few l u of the Gram's scale): a larger one squashes the sketch's
-          // weak directions, and the later passes then amplify rounding in them
-          po.shift_rel = pass == 0 ? 4.0 * (double)l * u_c : 0.0;
-          po.piv_tol = pass == 0 ? 0.0 : 64.0 * (double)l * u_c * u_c;
-          TT_CK(mm_run<W>(mm, {src_pass, l, false}, {src_pass, l, true}, l, l, nb, nullptr, 0,
-                          gy.as<double>(), true, nullptr, ws.p, !W64 && small64, true, true, false),
-                "Gram of sketch");
-          TT_CK(ttk::small_factor(gy.as<double>(), po, orth64, s1b.p, W64, (int)l, ws2.p,
-                                  dinfo.as<ttk::StepInfo>(), st), "orthonormalize");
-          TT_CK(mm_run<W>(mm, {src_pass, l, true}, {s1b.as<W>(), l, true}, nb, l, l, dst_pass[pass],
-                          l, nullptr, false, nullptr, ws.p, false, true, true, false), "apply R^-1");
-          src_pass = dst_pass[pass];
+        // three passes src -> d0 -> d1 -> d0; returns d0
+        auto orth3 = [&](const W* src, W* d0, W* d1) -> tt_status {
+          W* dst[3] = {d0, d1, d0};
+          for (int pass = 0; pass < 3; ++pass) {
+            // the smallest shift that keeps the first Cholesky positive definite
+            // (a few l u of the Gram's scale): a larger one squashes the sketch's
+            // weak directions, and the later passes then amplify rounding in them
+            po.shift_rel = pass == 0 ? 4.0 * (double)l * u_c : 0.0;
+            po.piv_tol = pass == 0 ? 0.0 : 64.0 * (double)l * u_c * u_c;
+            TT_CK(mm_run<W>(mm, {src, l, false}, {src, l, true}, l, l, nb, nullptr, 0,
+                            gy.as<double>(), true, nullptr, ws.p, !W64 && small64, true, true, false),
+                  "Gram of sketch");
+            TT_CK(ttk::small_factor(gy.as<double>(), po, orth64, s1b.p, W64, (int)l, ws2.p,
+                                    dinfo.as<ttk::StepInfo>(), st), "orthonormalize");
+            TT_CK(mm_run<W>(mm, {src, l, true}, {s1b.as<W>(), l, true}, nb, l, l, dst[pass], l,
+                            nullptr, false, nullptr, ws.p, precise, true, true, false), "apply R^-1");
+            src = dst[pass];
+          }
+          return TT_OK;
+        };
+        // q power (subspace) iterations: Y <- X^T X Q with Q the orthonormal
+        // basis of the previous Y (Cholesky-QR3, nested spans as above); X = C
+        // (URV) or C^T (ULV).  The same products as the sketch and the projection.
+        if (powered) {
+          Piece pb;
+          TT_TAKE(pb, (size_t)no * l * sizeof(W));
+          tm.begin(s, TT_PH_SKETCH);
+          for (int it = 0; it < o.power_iters; ++it) {
+            const tt_status so = orth3(yb.as<W>(), w1b.as<W>(), wb.as<W>());
+            if (so != TT_OK) return so;
+            const W* Q = w1b.as<W>();
+            if (cfg.urv) {
+              TT_CK(mm_run<W>(mm, {C, n, true}, {Q, l, true}, m, l, n, pb.as<W>(), l, nullptr,
+                              false, nullptr, ws.p, false, true, true, false), "power iteration: C Q");
+              TT_CK(mm_run<W>(mm, {C, n, false}, {pb.as<W>(), l, true}, n, l, m, active ? nullptr : yb.as<W>(),
+                              l, active ? y64.as<double>() : nullptr, false, nullptr, ws.p, false, true,
+                              true, false), "power iteration: C^T P");
+            } else {
+              TT_CK(mm_run<W>(mm, {C, n, false}, {Q, l, true}, n, l, m, pb.as<W>(), l, nullptr,
+                              false, nullptr, ws.p, false, true, true, false), "power iteration: C^T Q");
+              TT_CK(mm_run<W>(mm, {C, n, true}, {pb.as<W>(), l, true}, m, l, n, active ? nullptr : yb.as<W>(),
+                              l, active ? y64.as<double>() : nullptr, false, nullptr, ws.p, false, true,
+                              true, false), "power iteration: C P");
+            }
+            if (active) {
+              const tt_status sr = sum_sketch();
+              if (sr != TT_OK) return sr;
+            }
+          }
+          tm.end();
         }
+        tm.begin(s, TT_PH_ORTH);
+        {
+          const tt_status so = orth3(yb.as<W>(), w1b.as<W>(), wb.as<W>());
+          if (so != TT_OK) return so;
+        }
+        const W* src_pass = w1b.as<W>();
         tm.end();
         const W* Wm = src_pass;
         Wfin = Wm;
-        TT_ALLOC(bb, (size_t)no * l * sizeof(W));
+        TT_TAKE(bb, (size_t)no * l * sizeof(W));
         acc_gram = !W64 && tight(l);
         tm.begin(s, TT_PH_PROJECT);
         if (cfg.urv)
           TT_CK(mm_run<W>(mm, {C, n, true}, {Wm, l, true}, m, l, n, bb.as<W>(), l, nullptr, false,
-                          nullptr, ws.p, false, true, true, false), "project C W");
+                          nullptr, ws.p, precise, true, true, false), "project C W");
         else
           TT_CK(mm_run<W>(mm, {C, n, false}, {Wm, l, true}, n, l, m, bb.as<W>(), l, nullptr, false,
-                          nullptr, ws.p, false, true, true, false), "project C^T W");
+                          nullptr, ws.p, precise, true, true, false), "project C^T W");
         TT_CK(mm_run<W>(mm, {bb.as<W>(), l, false}, {bb.as<W>(), l, true}, l, l, no, nullptr, 0,
                         gy.as<double>(), true, nullptr, ws.p, acc_gram, true, true, false),
               "Gram B^T B");
+        TT_RED(gy.as<double>(), l * l);
         // FP32 W is orthonormal only to ~1e-7, which biases ||X W||^2 and so
         // the range miss mu^2; with a tight tolerance the small factor
         // whitens by W^T W (compensated sums of exact products).
-        const bool whiten = !W64 && small64;
+        const bool whiten = whiten_l;
         if (whiten) {
-          TT_ALLOC(gwb, (size_t)l * l * sizeof(double));
+          TT_TAKE(gwb, (size_t)l * l * sizeof(double));
           TT_CK(mm_run<W>(mm, {Wm, l, false}, {Wm, l, true}, l, l, nb, nullptr, 0, gwb.as<double>(),
                           true, nullptr, ws.p, true, false, false, false), "Gram W^T W");
         }
@@ -578,7 +770,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         prm.range_exact = identity ? 1 : 0;
         prm.piv_tol = small64 ? (small_df ? 1e-13 : 1e-15) : 1e-6;
         prm.df_math = small_df ? 1 : 0;
-        TT_ALLOC(zb, (size_t)l * l * sizeof(W));
+        TT_TAKE(zb, (size_t)l * l * sizeof(W));
         ldz = l;
         tm.begin(s, TT_PH_SMALL);
         TT_CK(ttk::small_factor(gy.as<double>(), prm, small64, zb.p, W64, (int)ldz, ws2.p,
@@ -594,6 +786,9 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         r = hinfo->r;
         const double d2 = hinfo->delta2;
         const int64_t lmax = std::min<int64_t>(std::min<int64_t>(nb, no), ttk::kMaxSmall);
+        if (debug_trace())
+          fprintf(stderr, "[ttutv]   sketch attempt k=%d l=%lld r=%d mu2=%.3e s1=%.3e tail=%.3e delta2=%.3e x2=%.9e trace=%.9e\n",
+                  k, (long long)l, hinfo->r, hinfo->mu2, hinfo->s1, hinfo->tail, d2, hinfo->x2, hinfo->trace);
         if (!fixed && !cfg.svd && (r > l - p_over || hinfo->tail > d2)) {
           if (l < lmax) {
             l = std::min<int64_t>(2 * l, lmax);
@@ -631,6 +826,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     // a ~2^-22 relative error in the carry only adds ~2^-44 of its squared
     // norm to that tail.
     mm = mm_all;
+    if (precise) mm.tc = false;
     // The next step's ||C||^2 is this carry's sum of squares.  The tensor-core
     // epilogue sums each row's squares in FP32 (~u/sqrt(rows) relative); after
     // a tight step the carry's squares are summed again exactly (FP64).
@@ -649,16 +845,19 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
                        cfg.urv ? mm_ws<W>(mm, r, n, l, false) : mm_ws<W>(mm, m, r, l, false));
       }
       if (sq_pass) wsz = std::max(wsz, ttk::sumsq_ws_bytes(crow * ccol));
-      TT_ALLOC(ws, wsz);
+      if (wsz > ws_bytes) {
+        TT_ALLOC(ws_extra, wsz);
+        ws.p = ws_extra.p;
+      }
     }
     if (exact) {
       tm.begin(s, TT_PH_CARRY);
       if (cfg.urv)
         TT_CK(mm_run<W>(mm, {C, n, true}, {Zp, ldz, true}, m, r, n, carry.as<W>(), r, nullptr, false,
-                        carry_sq, ws.p, false, true, true, false), "carry C Z1");
+                        carry_sq, ws.p, precise, true, true, false), "carry C Z1");
       else
         TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {C, n, true}, r, n, m, carry.as<W>(), n, nullptr, false,
-                        carry_sq, ws.p, false, true, true, false), "carry Z1^T C");
+                        carry_sq, ws.p, precise, true, true, false), "carry Z1^T C");
       tm.end();
       tm.begin(s, TT_PH_CORE);
       if (cfg.urv)
@@ -672,22 +871,23 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       tm.begin(s, TT_PH_CARRY);
       if (cfg.urv)
         TT_CK(mm_run<W>(mm, {Bm, l, true}, {Zp, ldz, true}, m, r, l, carry.as<W>(), r, nullptr, false,
-                        carry_sq, ws.p, false, true, true, false), "carry B Z1");
+                        carry_sq, ws.p, precise, true, true, false), "carry B Z1");
       else
         TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {Bm, l, false}, r, n, l, carry.as<W>(), n, nullptr, false,
-                        carry_sq, ws.p, false, true, true, false), "carry (B Z1)^T");
+                        carry_sq, ws.p, precise, true, true, false), "carry (B Z1)^T");
       tm.end();
       tm.begin(s, TT_PH_CORE);
       if (cfg.urv)
         TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {Wm, l, false}, r, n, l, core.as<W>(), n, nullptr, false,
-                        nullptr, ws.p, false, true, true, false), "core (W Z1)^T");
+                        nullptr, ws.p, precise, true, true, false), "core (W Z1)^T");
       else
         TT_CK(mm_run<W>(mm, {Wm, l, true}, {Zp, ldz, true}, m, r, l, core.as<W>(), r, nullptr, false,
-                        nullptr, ws.p, false, true, true, false), "core W Z1");
+                        nullptr, ws.p, precise, true, true, false), "core W Z1");
       tm.end();
     }
     if (sq_pass)
       TT_CK(ttk::sumsq(carry.p, W64, crow * ccol, d_carry2 + s, ws.p, st), "carry sum of squares");
+    TT_RED(d_carry2 + s, 1);
     cores[k - 1] = core.release();
     if (cfg.urv)
       out->ranks[k - 1] = r;
@@ -704,7 +904,26 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     r_carry = r;
     r_prev = r;
   }
-  // last core: the final carry (Alg. 3 step 8 / Alg. 1 step 8)
+  // last core: the final carry (Alg. 3 step 8 / Alg. 1 step 8); a
+  // partitioned one is gathered, every rank returns the whole core
+  if (active) {
+    const int64_t rl = r_carry;  // r_1 (URV) or r_{d-1} (ULV)
+    const int64_t lb = (cfg.urv ? dl[0] : dl[d - 1]) * rl;
+    Buf whole(&al), parts(&al);
+    TT_ALLOC(whole, (size_t)lb * sh->nranks * sizeof(W));
+    if (cfg.urv) {
+      const tt_status sg = gather(cbuf.p, whole.p, lb * (int64_t)sizeof(W));
+      if (sg != TT_OK) return sg;
+    } else {
+      TT_ALLOC(parts, (size_t)lb * sh->nranks * sizeof(W));
+      const tt_status sg = gather(cbuf.p, parts.p, lb * (int64_t)sizeof(W));
+      if (sg != TT_OK) return sg;
+      TT_CK(ttk::unshard_cols(parts.p, whole.p, W64, sh->nranks, rl, 1, dl[d - 1], st),
+            "interleave the gathered core");
+    }
+    cbuf.reset();
+    cbuf.p = whole.release();
+  }
   cores[cfg.urv ? 0 : d - 1] = cbuf.release();
   double h_carry2[TT_MAXD];
   TT_CK(cudaMemcpyAsync(h_carry2, d_carry2, sizeof(double) * (d - 1), cudaMemcpyDeviceToHost, st), "tails");
@@ -841,7 +1060,8 @@ tt_status run_reversed(const void* A, int32_t dtype, int32_t d, const int64_t* d
 
 tt_status sweep_entry(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
                       const int64_t* fixed, SweepCfg cfg, const tt_opts* opts, tt_alloc_fn alloc,
-                      tt_free_fn free_fn, void* ctx, void* stream, tt_result* out) {
+                      tt_free_fn free_fn, void* ctx, void* stream, tt_result* out,
+                      const tt_shard* sh = nullptr) {
   g_err.clear();
   tt_opts o;
   tt_opts_default(&o);
@@ -850,11 +1070,22 @@ tt_status sweep_entry(const void* A, int32_t dtype, int32_t d, const int64_t* di
   if (v != TT_OK) return v;
   if ((alloc == nullptr) != (free_fn == nullptr))
     return fail(TT_EINVAL, "alloc and free must both be given or both be NULL");
+  if (sh) {
+    if (sh->nranks < 1 || sh->rank < 0 || sh->rank >= sh->nranks)
+      return fail(TT_EINVAL, "shard: rank must be in [0, nranks)");
+    const int pm = cfg.urv ? 0 : d - 1;
+    if (dims[pm] % sh->nranks != 0)
+      return fail(TT_EINVAL, "shard: the partitioned mode must split into equal slabs");
+    if (sh->nranks > 1 && (!sh->allreduce || !sh->allgather))
+      return fail(TT_EINVAL, "shard: all-reduce and all-gather callbacks are required");
+    if (o.reverse) return fail(TT_EUNSUPPORTED, "shard: the reversed sweep is not partitioned");
+    if (cfg.svd) return fail(TT_EUNSUPPORTED, "shard: TT-SVD is not partitioned");
+  }
   Alloc al{alloc, free_fn, ctx, (cudaStream_t)stream};
   if (o.reverse) return run_reversed(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
   if (o.precision == TT_P_FP64)
-    return run_sweep<double>(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
-  return run_sweep<float>(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
+    return run_sweep<double>(A, dtype, d, dims, eps, fixed, cfg, o, al, out, sh);
+  return run_sweep<float>(A, dtype, d, dims, eps, fixed, cfg, o, al, out, sh);
 }
 
 }  // namespace
@@ -893,6 +1124,18 @@ tt_status tt_utv(const void* A, int32_t dtype, int32_t d, const int64_t* dims, d
   const SweepCfg cfg{direction == TT_RL, false};
   return sweep_entry(A, dtype, d, dims, eps, fixed_ranks, cfg, opts, alloc, free_fn, alloc_ctx,
                      stream, out);
+}
+
+tt_status tt_utv_sharded(const void* A_local, int32_t dtype, int32_t d, const int64_t* dims,
+                         double eps, const int64_t* fixed_ranks, int32_t variant, int32_t direction,
+                         const tt_opts* opts, tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx,
+                         void* stream, const tt_shard* shard, tt_result* out) {
+  if (!shard) return fail(TT_EINVAL, "NULL shard");
+  if (variant != TT_URV && variant != TT_ULV) return fail(TT_EINVAL, "bad variant");
+  if (direction != TT_RL && direction != TT_LR) return fail(TT_EINVAL, "bad direction");
+  const SweepCfg cfg{direction == TT_RL, false};
+  return sweep_entry(A_local, dtype, d, dims, eps, fixed_ranks, cfg, opts, alloc, free_fn, alloc_ctx,
+                     stream, out, shard);
 }
 
 tt_status tt_svd(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
@@ -986,7 +1229,6 @@ int64_t rse_slab_rows(int32_t d, const int64_t* dims) {
   for (int k = 1; k < d; ++k) p *= dims[k];
   return std::max<int64_t>(1, std::min<int64_t>(dims[0], ((int64_t)1 << 24) / std::max<int64_t>(1, p)));
 }
-size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // Contraction scratch of tt_rse: the larger of a full slab's and the last
 // (ragged) slab's -- a smaller product may split its inner dimension and so
 // need more scratch.

@@ -97,9 +97,17 @@ cudaError_t small_factor(const double* G, SmallParams prm, bool fp64_math, void*
                          int ldz, void* ws, StepInfo* info, cudaStream_t st);
 
 // Elementwise helpers.
+// Rows of the sketch: local row i is global row (i / blk) * stride + off + i % blk
+// (blk <= 0: the identity mapping), the rows a slab of a partitioned unfolding owns.
 cudaError_t fill_sketch(void* out, bool fp64, int64_t rows, int64_t cols, uint64_t seed,
-                        uint32_t step, bool identity, cudaStream_t st);
+                        uint32_t step, bool identity, cudaStream_t st, int64_t blk = 0,
+                        int64_t stride = 0, int64_t off = 0);
 cudaError_t cast_copy(const void* in, bool in64, void* out, bool out64, int64_t n, cudaStream_t st);
+// Gathered column blocks [P][rows][outer * blk] of a partitioned unfolding
+// (rank p: blk consecutive columns of each outer group) back to
+// [rows][outer * P * blk] in column order.
+cudaError_t unshard_cols(const void* in, void* out, bool fp64, int P, int64_t rows, int64_t outer,
+                         int64_t blk, cudaStream_t st);
 cudaError_t copy2d(const void* in, int64_t ldi, bool trans, void* out, int64_t ldo, int64_t rows,
                    int64_t cols, bool fp64, cudaStream_t st);
 size_t sumsq_ws_bytes(int64_t n);

@@ -17,18 +17,23 @@ constexpr int kGrid = 152 * 8;
 constexpr int kMaxModes = 16;
 constexpr int TT_MAXD_INTERNAL = 18;
 
+// Row i of the local block is row (i / blk) * stride + off + i % blk of the
+// whole sketch (a slab of a partitioned unfolding draws the rows the whole
+// unfolding would: blk = rows, off = 0 for an unpartitioned one).
 template <typename T>
 __global__ void fill_sketch_kernel(T* __restrict__ out, int64_t rows, int64_t cols, uint64_t seed,
-                                   uint32_t step, bool identity) {
+                                   uint32_t step, bool identity, int64_t blk, int64_t stride,
+                                   int64_t off) {
   const int64_t total = rows * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / cols, j = e % cols;
+    const int64_t gi = (i / blk) * stride + off + i % blk;
     T v;
     if (identity)
-      v = (i == j) ? T(1) : T(0);
+      v = (gi == j) ? T(1) : T(0);
     else
-      v = (T)sketch_sign((uint64_t)i, (uint64_t)j, seed, step);
+      v = (T)sketch_sign((uint64_t)gi, (uint64_t)j, seed, step);
     out[e] = v;
   }
 }
@@ -160,6 +165,21 @@ __global__ void eval_backward_kernel(EvalArgs a, const int64_t* __restrict__ idx
   }
 }
 
+// Columns of a partitioned unfolding back in order: `in` holds P rank blocks
+// [P][rows][outer * blk] (rank p's columns are its slab of the fastest mode:
+// blk of them per outer index), `out` is [rows][outer * P * blk] with column
+// (o, p, t) at o * P * blk + p * blk + t.
+template <typename T>
+__global__ void unshard_cols_kernel(const T* __restrict__ in, T* __restrict__ out, int P, int64_t rows,
+                                    int64_t outer, int64_t blk) {
+  const int64_t nl = outer * blk, total = (int64_t)P * rows * nl;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e % blk, o = (e / blk) % outer, i = (e / nl) % rows, p = e / (nl * rows);
+    out[i * (outer * P * blk) + o * P * blk + p * blk + t] = in[e];
+  }
+}
+
 // ---- mode reversal (the index-reversed tensor of the Remark after Thm 3.2)
 struct RevArgs {
   int nmid;                 // middle modes 1 .. d-2
@@ -286,13 +306,31 @@ bool fill_eval_args(EvalArgs& a, int d, const int64_t* dims, const int64_t* rank
 }  // namespace
 
 cudaError_t fill_sketch(void* out, bool fp64, int64_t rows, int64_t cols, uint64_t seed,
-                        uint32_t step, bool identity, cudaStream_t st) {
+                        uint32_t step, bool identity, cudaStream_t st, int64_t blk, int64_t stride,
+                        int64_t off) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  if (blk <= 0) blk = rows;
   count_launch(1);
   const int g = grid_for(rows * cols, 256);
   if (fp64)
-    fill_sketch_kernel<double><<<g, 256, 0, st>>>((double*)out, rows, cols, seed, step, identity);
+    fill_sketch_kernel<double><<<g, 256, 0, st>>>((double*)out, rows, cols, seed, step, identity, blk,
+                                                  stride, off);
   else
-    fill_sketch_kernel<float><<<g, 256, 0, st>>>((float*)out, rows, cols, seed, step, identity);
+    fill_sketch_kernel<float><<<g, 256, 0, st>>>((float*)out, rows, cols, seed, step, identity, blk,
+                                                 stride, off);
+  return cudaGetLastError();
+}
+
+cudaError_t unshard_cols(const void* in, void* out, bool fp64, int P, int64_t rows, int64_t outer,
+                         int64_t blk, cudaStream_t st) {
+  const int64_t total = (int64_t)P * rows * outer * blk;
+  if (total <= 0) return cudaSuccess;
+  count_launch();
+  const int g = grid_for(total, 256);
+  if (fp64)
+    unshard_cols_kernel<double><<<g, 256, 0, st>>>((const double*)in, (double*)out, P, rows, outer, blk);
+  else
+    unshard_cols_kernel<float><<<g, 256, 0, st>>>((const float*)in, (float*)out, P, rows, outer, blk);
   return cudaGetLastError();
 }
 

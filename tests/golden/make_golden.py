@@ -5,8 +5,9 @@ the seeded generators in ``synth``; run from the repository root:
     python tests/golden/make_golden.py [c2 c3 c5]
 
 Outputs tests/golden/<cfg>_<method>.npz with ranks, per-unfolding tails,
-||A||^2, RSE, the cores (c2, c3: small) or the oracle's values at 4096 seeded
-sample indices (c5: its cores are 8 MB).
+||A||^2, RSE, the oracle's values at 4096 seeded sample indices and its cores
+(c2, c3: FP64; c5: rounded once to FP32 to halve the file, 4.2 MB, which
+moves the represented tensor by about 1e-7 of its norm).
 """
 import os
 import sys
@@ -25,7 +26,7 @@ N_SAMPLES = 4096
 SAMPLE_SEED = 12345
 
 
-def save(name, A, res, keep_cores):
+def save(name, A, res, keep_cores, core_dtype=np.float64):
     cfg = name.split("_")[0]
     dims = A.shape
     out = dict(ranks=np.array(res["ranks"]), tails=np.array(res["tails"]),
@@ -42,6 +43,8 @@ def save(name, A, res, keep_cores):
     else:
         # RSE from the error equality of Thm 3.1 / 3.2 (pinned in test_oracle_tt.py)
         out["rse"] = float(np.sqrt(sum(res["tails"]) / res["normA2"]))
+        for k, g in enumerate(res["cores"]):
+            out[f"core{k}"] = g.astype(core_dtype)
     np.savez_compressed(os.path.join(OUT, name + ".npz"), **out)
     print(name, res["ranks"], "rse", out["rse"], flush=True)
 
@@ -63,7 +66,7 @@ def main(which):
     if "c5" in which:
         A = synth.make_config("c5")
         t = time.time()
-        save("c5_URV", A, tt.tt_utv(A, eps=1e-2, variant="URV"), False)
+        save("c5_URV", A, tt.tt_utv(A, eps=1e-2, variant="URV"), False, np.float32)
         print("  ", round(time.time() - t, 1), "s")
 
 

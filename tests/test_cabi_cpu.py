@@ -181,7 +181,7 @@ def test_binding_structs_match_the_header(tmp_path):
     if gcc is None:
         pytest.skip("gcc not available")
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ttutv.h"', "int main(void) {"]
-    for st in (tu.tt_opts, tu.tt_result):
+    for st in (tu.tt_opts, tu.tt_result, tu.tt_shard):
         name = st.__name__
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
         for f, _ in st._fields_:
@@ -193,8 +193,31 @@ def test_binding_structs_match_the_header(tmp_path):
     subprocess.run([gcc, "-I", inc, str(src), "-o", str(tmp_path / "layout")], check=True)
     out = subprocess.run([str(tmp_path / "layout")], capture_output=True, text=True, check=True).stdout
     got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out.splitlines()}
-    for st in (tu.tt_opts, tu.tt_result):
+    for st in (tu.tt_opts, tu.tt_result, tu.tt_shard):
         name = st.__name__
         assert got[(name, "size")] == ctypes.sizeof(st)
         for f, _ in st._fields_:
             assert got[(name, f)] == getattr(st, f).offset, (name, f)
+
+
+def test_sharded_arguments_rejected(L):
+    # the partition is validated before any device work
+    dims = tu._i64([8, 6, 5])
+    res = tu.tt_result()
+
+    def call(shard, direction=tu.TT_RL, opts=None, variant=tu.TT_URV):
+        return L.tt_utv_sharded(ctypes.c_void_p(16), tu.TT_F32, 3, dims, 1e-2, None, variant,
+                                direction, opts, tu.ALLOC_FN(), tu.FREE_FN(), None, None,
+                                ctypes.byref(shard) if shard is not None else None, ctypes.byref(res))
+
+    assert call(None) == 1                                   # no shard
+    noop_r = tu.ALLREDUCE_FN(lambda *a: 0)
+    noop_g = tu.ALLGATHER_FN(lambda *a: 0)
+    assert call(tu.tt_shard(2, 2, noop_r, noop_g, None)) == 1    # rank out of range
+    assert call(tu.tt_shard(3, 0, noop_r, noop_g, None)) == 1    # mode 1 (8) not a multiple of 3
+    assert call(tu.tt_shard(2, 0, noop_r, noop_g, None), direction=tu.TT_LR, variant=tu.TT_ULV) == 1  # mode 3 (5)
+    assert call(tu.tt_shard(2, 0, tu.ALLREDUCE_FN(), tu.ALLGATHER_FN(), None)) == 1  # no callbacks
+    o = tu.tt_opts()
+    L.tt_opts_default(ctypes.byref(o))
+    o.reverse = 1
+    assert call(tu.tt_shard(2, 0, noop_r, noop_g, None), opts=ctypes.byref(o)) == 7   # reversed: unsupported

@@ -1,0 +1,70 @@
+"""Opt-in paths of the sweep against the FP64 oracle, through the C ABI.
+
+* power_iters (tt_opts.power_iters = q): q subspace iterations of every
+  sketched range, Y <- X^T X Q (the randomized range finder behind randUTV,
+  Sec. 2.2 and 3.3).  The GPU orthonormalizes Y by shifted Cholesky-QR, the
+  oracle by Householder QR: both keep the nested spans of Y's leading
+  columns, so the final range basis, the pivoted QLP and everything after it
+  agree up to rounding.  The tensor here has a slowly decaying spectrum in
+  its sketched unfoldings, so q changes the result (checked against q = 0).
+* small = "df" / orth = "df" (TT_SMALL_DF): the tight steps' small factors
+  in double-float arithmetic instead of FP64, on the 32^5 workload whose
+  every step is tight; held to the FP32 tolerance and the tight-tail checks.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import tt as otc
+from test_gpu_parity import check_gold, check_tight_tails, np_cores, rel_diff, tu  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def decaying_tensor(dtype):
+    """A 24 x 30 x 160 tensor with slowly (geometrically) decaying spectra: a
+    sum of 80 rank-one terms with weights 0.88^j.  At eps = 1e-2 and
+    l_full = 16 both sweeps sketch their steps (widths 64 and 24, or 24 and
+    96) and q = 1, 2 move the represented tensor by ~2e-3 of its norm."""
+    rng = np.random.default_rng(71)
+    dims = (24, 30, 160)
+    A = np.zeros(dims)
+    for j in range(80):
+        a, b, c = (rng.standard_normal(n) for n in dims)
+        A += 0.88 ** j * np.einsum("i,j,k->ijk", a / np.linalg.norm(a), b / np.linalg.norm(b),
+                                  c / np.linalg.norm(c))
+    return A.astype(dtype)
+
+
+@pytest.mark.parametrize("precision, tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("q", [1, 2])
+@pytest.mark.parametrize("method", ["URV", "ULV"])
+def test_power_iterations(tu, precision, tol, q, method):
+    A = decaying_tensor(np.float64 if precision == "fp64" else np.float32)
+    kw = dict(eps=1e-2, l_full=16)
+    res = tu.tt_utv(torch.from_numpy(A).cuda(), variant=method, precision=precision,
+                    power_iters=q, **kw)
+    ref = otc.tt_utv(np.asarray(A, np.float64), variant=method, q=q, **kw)
+    ref0 = otc.tt_utv(np.asarray(A, np.float64), variant=method, q=0, **kw)
+    assert any(l > 0 for l in res.sketch_l)
+    assert res.ranks == ref["ranks"], (res.ranks, ref["ranks"])
+    normA2 = ref["normA2"]
+    diff = rel_diff(np_cores(res), ref["cores"], normA2)
+    # q matters on this spectrum: the oracle's q and q = 0 results differ by
+    # far more than the tolerance, so agreeing with the q result is a check
+    moved = (rel_diff(ref["cores"], ref0["cores"], normA2) if ref0["ranks"] == ref["ranks"]
+             else np.inf)
+    print(f"POWER {method} {precision} q={q} ranks={res.ranks} diff={diff:.3e} q-vs-0={moved:.3e}")
+    assert diff <= tol, diff
+    assert moved > 10 * tol
+
+
+@pytest.mark.parametrize("method", ["URV", "ULV"])
+def test_double_float_small_factors_c3(tu, method):
+    A = synth.make_config("c3")
+    res = check_gold(tu, A, method, f"c3_{method}", 1e-5, 1e-3, precision="fp32", small="df",
+                     orth="df")
+    assert res.ranks == [1, 20, 20, 20, 20, 1]
+    assert all(res.small_fp64)
+    check_tight_tails(tu, A, res, method, "c3")

@@ -42,6 +42,25 @@ def rel_diff(cores_a, cores_b, normA2):
     return float(np.sqrt(np.sum(D * D) / normA2))
 
 
+def tt_inner(a, b):
+    """<X, Y> of two tensors in TT format (FP64), contracting core by core:
+    O(d I r^3), the full tensors are never formed."""
+    Z = np.ones((1, 1))
+    for ga, gb in zip(a, b):
+        T = np.einsum("xy,xip->yip", Z, np.asarray(ga, np.float64))
+        Z = np.einsum("yip,yiq->pq", T, np.asarray(gb, np.float64))
+    return float(Z[0, 0])
+
+
+def rel_diff_tt(cores_a, cores_b, normA2):
+    """||X - Y||_F / ||A||_F from TT inner products, ||X||^2 - 2<X,Y> + ||Y||^2:
+    gauge invariant (does not depend on how the cores split the tensor).  The
+    FP64 inner products carry ~1e-14 of ||X||^2, so differences below ~1e-7
+    of ||A|| are not resolved; the tolerances here are 1e-5 and above."""
+    d2 = tt_inner(cores_a, cores_a) - 2.0 * tt_inner(cores_a, cores_b) + tt_inner(cores_b, cores_b)
+    return float(np.sqrt(max(d2, 0.0) / normA2))
+
+
 def orth_err(res):
     errs = []
     if res.orth == "right":
@@ -257,9 +276,11 @@ def check_gold(tu, A, method, name, tol, eps, **kw):
     ref = g["sample_val"]
     samp = np.sqrt(np.sum((vals - ref) ** 2) / np.sum(g["sample_ref"] ** 2))
     assert samp <= 10 * tol, samp
-    if "core0" in g.files:
-        ocores = [g[f"core{k}"] for k in range(len(res.cores))]
-        assert rel_diff(np_cores(res), ocores, normA2) <= tol
+    # the whole represented tensor against the oracle's (S13's criterion)
+    ocores = [g[f"core{k}"].astype(np.float64) for k in range(len(res.cores))]
+    full = rel_diff_tt(np_cores(res), ocores, normA2)
+    print(f"GOLD {name} {kw} ranks={res.ranks} full_diff={full:.3e} sampled={samp:.3e}")
+    assert full <= tol, full
     rse = gpu_rse(tu, A_t, res)
     assert abs(rse - float(g["rse"])) <= tol + 1e-3 * float(g["rse"])
     assert rse <= eps * (1 + 1e-3)
@@ -268,10 +289,16 @@ def check_gold(tu, A, method, name, tol, eps, **kw):
     return res
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
 @pytest.mark.parametrize("method", ["URV", "ULV", "SVD"])
-def test_c2_hilbert_256(tu, method):
+def test_c2_hilbert_256(tu, method, precision):
+    # the FP32 input of 1/(i+j+k+1).  FP64 arithmetic widens it; FP32 and
+    # mixed arithmetic meet eps = 1e-6 (eps_k^2 = 5e-13 ||A||^2, every step
+    # tight, kept singular values down to ~1e-6 of ||C||) through compensated
+    # Grams, FP64 small factors and compensated sketches, projections, carries
+    # and cores
     A = synth.make_config("c2")
-    check_gold(tu, A, method, f"c2_{method}", 1e-5, 1e-6, precision="fp64")
+    check_gold(tu, A, method, f"c2_{method}", 1e-5, 1e-6, precision=precision)
 
 
 @pytest.mark.parametrize("method", ["URV", "ULV"])
