@@ -52,6 +52,10 @@ WORKLOADS = {
                desc="32^5 f32 tensor from Gaussian TT cores ranks (1,20,20,20,20,1) + 1e-4 relative "
                     "Gaussian noise, eps=1e-3, TT-URV right-to-left (precision study: every step "
                     "is tight)"),
+    "c4": dict(kind="masked", ranks=(1, 32, 16, 1),
+               desc="masked TT evaluation + core gradients of the completion workload: "
+                    "256x256x64 f32 volume of 20 Gaussian blobs, Bernoulli(0.3) observation "
+                    "set (1.26M entries), TT ranks (1,32,16,1) from the TT-URV initialisation"),
     "c5-half": dict(dims=(64, 128, 128, 128), ranks=(1, 64, 64, 64, 1), rel_noise=1e-3, seed=0,
                     eps=1e-2, variant="URV",
                     desc="64x128^3 f32 (512 MiB) slab of the 128^4 workload's generator, for "
@@ -488,6 +492,241 @@ def run_reference(args, wl, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------- masked evaluation (c4)
+
+MASKED_METRIC = "masked TT eval + gradient TFLOP/s"
+
+
+def masked_flops_per_entry(ranks):
+    """Algorithmic FLOPs of one entry of x = G_1[i_1]..G_d[i_d] and of its core
+    gradients with the interfaces recomputed: forward sum_{k>=2} 2 r_{k-1} r_k
+    (the first core is a copy); per core k, the left interface
+    sum_{2<=j<k} 2 r_{j-1} r_j, the right one sum_{k<j<d} 2 r_{j-1} r_j (the
+    last core is a copy), the gout scaling r_k and the outer product
+    2 r_{k-1} r_k.  ranks = (r_0 = 1, ..., r_d = 1)."""
+    d = len(ranks) - 1
+    step = [2 * ranks[j] * ranks[j + 1] for j in range(d)]  # core j+1 (1-based) product
+    fwd = sum(step[1:])
+    bwd = 0
+    for k in range(d):                       # core k+1 (1-based)
+        left = sum(step[1:k])                # cores 2..k
+        right = sum(step[k + 1:d - 1])       # cores k+2..d-1
+        bwd += left + right + ranks[k + 1] + step[k]
+    return fwd, bwd
+
+
+def c4_problem(tu, torch, dev):
+    cfg = synth.CONFIGS["c4"]
+    shape, ranks = cfg["shape"], list(cfg["ranks"])
+    M = synth.make_config("c4")
+    idx = synth.observation_mask(shape, cfg["p_obs"], cfg["mask_seed"])
+    vals = np.ascontiguousarray(M.reshape(-1)[idx])
+    z = np.zeros(M.size, np.float32)
+    z[idx] = vals / (len(idx) / M.size)
+    cores = tu.tt_utv(torch.from_numpy(z.reshape(shape)).to(dev), ranks=ranks[1:-1]).cores
+    return shape, ranks, idx, vals, cores
+
+
+def run_c4(args, wl, rank, world):
+    import torch
+
+    import paper_2501_07904_gb300 as tu
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    shape, ranks, idx, vals, cores = c4_problem(tu, torch, dev)
+    n = len(idx)
+    i_t = torch.from_numpy(idx).to(dev)
+    v_t = torch.from_numpy(vals).to(dev)
+    plan = tu.EvalPlan(shape, ranks, i_t)
+    st = torch.cuda.current_stream()
+    gout = plan.at(cores) - v_t              # the residual of the initial cores
+    grads = [torch.zeros_like(c) for c in cores]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > the 129 MB L2
+
+    def step():
+        x = plan.at(cores)
+        for g in grads:
+            g.zero_()
+        plan.backward(cores, gout, out=grads)
+        return x
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    l0 = tu.kernel_launches()
+    with ClockSampler(dev.index, not args.no_clocks) as clk:
+        for e0, e1 in ev:
+            flush.fill_(1)                    # L2 flushed between timed steps
+            e0.record(st)
+            step()
+            e1.record(st)
+        torch.cuda.synchronize()
+    barrier()
+    launches = tu.kernel_launches() - l0
+    ms = slowest_ms(sum(a.elapsed_time(b) for a, b in ev) / args.steps, world, dev)
+    fwd_f, bwd_f = masked_flops_per_entry(ranks)
+    flops = (fwd_f + bwd_f) * n
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # forward and backward apart (same flush discipline), for the roofline line
+    def timed(fn, reps=20):
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+    ms_f = timed(lambda: plan.at(cores))
+    ms_b = timed(lambda: plan.backward(cores, gout, out=grads))
+    roof = {"bound": "alu", "achieved": round(flops / (ms * 1e-3) / 1e12, 2),
+            "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+            "frac": round(flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, 4),
+            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
+            "scope": "forward (1 launch) + backward (2d launches) of one step",
+            "flops_per_entry": {"forward": fwd_f, "backward": bwd_f}, "entries": n,
+            "forward": {"ms": round(ms_f, 4), "tflops": round(fwd_f * n / (ms_f * 1e-3) / 1e12, 2)},
+            "backward": {"ms": round(ms_b, 4), "tflops": round(bwd_f * n / (ms_b * 1e-3) / 1e12, 2)},
+            "traffic": None}
+
+    # determinism and accuracy of this run (untimed)
+    g1 = plan.backward(cores, gout)
+    g2 = plan.backward(cores, gout)
+    bitwise = all(torch.equal(a, b) for a, b in zip(g1, g2))
+    from oracle import tt as otc  # accuracy check against the FP64 oracle (sampled, untimed)
+    sub = np.random.default_rng(7).choice(n, 20000, replace=False)
+    c64 = [c.double().cpu().numpy() for c in cores]
+    xs = plan.at(cores).double().cpu().numpy()[sub]
+    ref = otc.tt_eval_at(c64, idx[sub])
+    acc = {"sampled_entries": len(sub),
+           "max_rel_err_vs_oracle": float(np.max(np.abs(xs - ref)) / np.max(np.abs(ref))),
+           "gradients_bitwise_reproducible": bool(bitwise)}
+
+    # end to end through the public API with host buffers: cores in, gradients and loss out
+    e2e = None
+    if not args.no_e2e:
+        h_cores = [c.cpu().pin_memory() for c in cores]
+        h_grads = [torch.empty(c.shape, dtype=c.dtype, pin_memory=True) for c in cores]
+        h_loss = torch.empty(1, dtype=torch.float32, pin_memory=True)
+        d_cores = [torch.empty_like(c) for c in cores]
+        in_bytes = sum(c.numel() * 4 for c in h_cores)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(st)
+        for _ in range(args.steps):
+            for dc, hc in zip(d_cores, h_cores):
+                dc.copy_(hc, non_blocking=True)
+            r = plan.at(d_cores) - v_t
+            loss = 0.5 * torch.dot(r, r)
+            gg = plan.backward(d_cores, r)
+            for hg, g in zip(h_grads, gg):
+                hg.copy_(g, non_blocking=True)
+            h_loss.copy_(loss.view(1), non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_e = slowest_ms(e0.elapsed_time(e1) / args.steps, world, dev)
+        e2e = {"value": round(world * flops / (ms_e * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
+               "ms_per_step": round(ms_e, 4), "h2d_bytes_per_step": int(in_bytes),
+               "d2h_bytes_per_step": int(in_bytes + 4),
+               "step": "cores H2D, x = P_Omega(TT), residual and loss, gradients, gradients and loss D2H"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = c4_cpu_baseline(cores, idx, ranks)
+
+    return {
+        "metric": MASKED_METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"c4: {wl['desc']}", "entries": n, "ranks": ranks,
+                   "l2": "flushed between timed steps (256 MiB write): the plan and operands "
+                         "(~80 MB) fit in the 129 MB L2",
+                   "parallelism": f"replicas x{world} (independent problems)",
+                   "entries_per_s": round(world * n / (ms * 1e-3), 1),
+                   "plan_device_bytes": plan.device_bytes},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk.summary(), "accuracy": acc,
+    }
+
+
+def c4_cpu_baseline(cores, idx, ranks, target_s=10.0, chunk=1 << 16):
+    """The oracle's masked evaluation and gradient (FP64, numpy on the host
+    cores) on successive blocks of the observation set for about target_s."""
+    from oracle import tt as otc  # the FP64 oracle: only this leg of bench.py runs it
+
+    c64 = [c.double().cpu().numpy() for c in cores]
+    rng = np.random.default_rng(3)
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < target_s and done < len(idx):
+        blk = idx[done:done + chunk]
+        otc.tt_eval_at(c64, blk)
+        otc.tt_eval_grad(c64, blk, rng.standard_normal(len(blk)))
+        done += len(blk)
+    dt = time.perf_counter() - t0
+    f, b = masked_flops_per_entry(ranks)
+    return {"value": round((f + b) * done / dt / 1e12, 6), "unit": "TFLOP/s",
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {done} of {len(idx)} observed entries in blocks of {chunk}, "
+                      f"forward + gradient; {dt:.1f} s",
+            "seconds": round(dt, 3)}
+
+
+def run_reference_c4(args, wl, rank, world):
+    if rank != 0:
+        return None
+    from oracle import tt as otc  # the FP64 oracle is this arm
+
+    cfg = synth.CONFIGS["c4"]
+    ranks = list(cfg["ranks"])
+    shape = cfg["shape"]
+    idx = synth.observation_mask(shape, cfg["p_obs"], cfg["mask_seed"])
+    cores = synth.gaussian_cores(shape, ranks, seed=0)     # the oracle's cost does not depend on values
+    budget = 150.0 / max(1, args.steps)                     # seconds per step: the loop stays near 2.5 min
+    chunk = 1 << 14
+    n = max(chunk, min(len(idx), int(budget * 3.5e4)) // chunk * chunk)  # ~3.5e4 entries/s
+    rng = np.random.default_rng(3)
+    gout = rng.standard_normal(n)
+
+    def one():
+        for s in range(0, n, chunk):
+            otc.tt_eval_at(cores, idx[s:s + chunk])
+            otc.tt_eval_grad(cores, idx[s:s + chunk], gout[s:s + chunk])
+    for _ in range(min(args.warmup, 1)):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = (time.perf_counter() - t0) / args.steps
+    f, b = masked_flops_per_entry(ranks)
+    value = (f + b) * n / dt / 1e12
+    sample = (f"first {n} of {len(idx)} observed entries in blocks of {chunk}, forward + gradient "
+              f"(Gaussian cores of the workload's ranks)")
+    return {"impl": "reference", "metric": MASKED_METRIC, "value": round(value, 6),
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"c4: {wl['desc']}", "precision": "fp64 oracle",
+                       "l2": "n/a (CPU)", "parallelism": "1 process, host cores"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
@@ -497,10 +736,11 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
+    masked = wl.get("kind") == "masked"
     if args.impl == "reference":
-        out = run_reference(args, wl, rank, world)
+        out = (run_reference_c4 if masked else run_reference)(args, wl, rank, world)
     else:
-        out = run_ours(args, wl, rank, world)
+        out = (run_c4 if masked else run_ours)(args, wl, rank, world)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if world > 1 and args.impl == "ours":

@@ -21,7 +21,9 @@
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *   All work is enqueued on it.  tt_utv / tt_svd synchronize that stream
  *   once per sweep step to read the chosen rank (the next step's shapes
- *   depend on it); the other calls are asynchronous.
+ *   depend on it), and tt_eval_plan_create (and the one-shot masked
+ *   evaluations built on it) once to read its index check; the other calls
+ *   are asynchronous.
  * - Every function returns a tt_status; on failure tt_last_error() returns a
  *   thread-local message.  No function aborts or traps.
  */
@@ -293,19 +295,58 @@ size_t tt_rse_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks, i
 tt_status tt_rse(int32_t d, const int64_t* dims, const int64_t* ranks, const void* const* cores,
                  int32_t dtype, const void* A, void* work, double* out, void* stream);
 
-/* Masked TT evaluation x_e = G_1[i_1] G_2[:, i_2, :] ... G_d[:, i_d] at n
- * row-major linear indices idx[e] (device int64, 0 <= idx < prod(dims)).
- * FP32 only.  out: device float[n]. */
+/* Masked TT evaluation (the observation operator P_Omega of the completion
+ * experiment, Sec. 4.2.2): x_e = G_1[i_1] G_2[:, i_2, :] ... G_d[:, i_d] at n
+ * row-major linear indices idx[e] of a tensor of shape dims, and the core
+ * gradients of sum_e gout_e x_e,
+ *   dG_k[:, i_k, :] += gout_e (G_1[i_1]..G_{k-1}[i_{k-1}])^T (G_{k+1}[i_{k+1}]..G_d[i_d])^T,
+ * the left and right interface products recomputed per entry (nothing is
+ * stored between calls).  FP32 cores, values and gradients; d in [1, 16],
+ * ranks in [1, 64] with r_0 = r_d = 1, dims in [1, 2^31), n in [0, 2^31).
+ *
+ * A plan holds what depends only on the index set: the decoded mode indices
+ * and, for every core, the entries ordered stably by that core's index (ties
+ * by a neighbouring core's).  Device bytes: 8 d n (indices and orders),
+ * d ceil(n/128) (chunk flags), 2 ceil(n/128) max_k(round4(r_{k-1}) round4(r_k)) * 4
+ * (per-chunk gradient partials), 4 n + 4 * 256 ceil(n/2048) (sort scratch).
+ *
+ * Gradients are summed in a fixed order with no floating-point atomics: a
+ * plan gives bitwise-equal results on every call (and two plans built from
+ * the same idx give the same results).  One call at a time per plan (the
+ * backward writes the plan's partials): calls on one stream are ordered. */
+typedef struct tt_eval_plan tt_eval_plan;
+
+/* Build a plan for idx (device int64[n]).  Device memory comes from `alloc`
+ * (or cudaMallocAsync on `stream` when alloc and free_fn are both NULL) and
+ * goes back through free_fn in tt_eval_plan_destroy.  Synchronizes `stream`
+ * once to read the index check: an index outside [0, prod(dims)) returns
+ * TT_EINVAL (the kernels read no core memory for it) and no plan.  *out is
+ * a host handle. */
+tt_status tt_eval_plan_create(int32_t d, const int64_t* dims, const int64_t* ranks,
+                              const int64_t* idx, int64_t n, tt_alloc_fn alloc, tt_free_fn free_fn,
+                              void* alloc_ctx, void* stream, tt_eval_plan** out);
+/* Release the plan (its device block is freed stream-ordered on `stream`). */
+void tt_eval_plan_destroy(tt_eval_plan* plan, void* stream);
+/* Bytes of the plan's device block. */
+size_t tt_eval_plan_device_bytes(const tt_eval_plan* plan);
+
+/* x_e for the plan's indices.  cores: host array of d device pointers, core
+ * k an FP32 array [r_{k-1}][I_k][r_k] with the plan's dims and ranks;
+ * out: device float[n].  Asynchronous; 1 kernel launch. */
+tt_status tt_eval_plan_at(const tt_eval_plan* plan, const float* const* cores, float* out,
+                          void* stream);
+/* Gradients of sum_e gout_e x_e (gout: device float[n]), ACCUMULATED into
+ * grads (host array of d device pointers shaped like the cores, distinct
+ * buffers; zero them first for a plain gradient).  Asynchronous; 2 d launches. */
+tt_status tt_eval_plan_backward(tt_eval_plan* plan, const float* const* cores, const float* gout,
+                                float* const* grads, void* stream);
+
+/* One-shot forms: build a plan (cudaMallocAsync), run, destroy.  Each
+ * synchronizes `stream` once (the index check); TT_EINVAL for an index
+ * outside [0, prod(dims)). */
 tt_status tt_eval_at(int32_t d, const int64_t* dims, const int64_t* ranks,
                      const float* const* cores, const int64_t* idx, int64_t n, float* out,
                      void* stream);
-
-/* Gradient of sum_e gout[e] x_e with respect to every core: for each entry,
- * dG_k[:, i_k, :] += gout_e * (G_1[i_1]..G_{k-1}[i_{k-1}])^T (G_{k+1}[i_{k+1}]..G_d[i_d])^T,
- * the left and right interface products recomputed per entry (nothing
- * stored).  grads: host array of d device pointers shaped like the cores;
- * they are ACCUMULATED into (zero them first for a plain gradient).
- * Accumulation uses FP32 atomics, so the summation order is unspecified. */
 tt_status tt_eval_at_backward(int32_t d, const int64_t* dims, const int64_t* ranks,
                               const float* const* cores, const int64_t* idx, int64_t n,
                               const float* gout, float* const* grads, void* stream);

@@ -27,6 +27,8 @@ TT_MAXD = 16
 
 STATUS = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENONFINITE", 3: "TT_ENOMEM", 4: "TT_ECUDA",
           5: "TT_ENOCONV", 6: "TT_ETIMEOUT", 7: "TT_EUNSUPPORTED"}
+for _code, _name in STATUS.items():
+    globals()[_name] = _code
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 SMALL = {"auto": 0, "fp32": 1, "fp64": 2, "df": 3}
 TT_F32, TT_F64 = 0, 1
@@ -37,7 +39,8 @@ TT_RL, TT_LR = 0, 1
 EXPORTS = ["tt_opts_default", "tt_utv", "tt_utv_sharded", "tt_svd", "tt_result_free",
            "tt_full_work_bytes",
            "tt_full", "tt_full_noalloc", "tt_full_noalloc_max_work_bytes", "tt_rse_work_bytes",
-           "tt_rse", "tt_eval_at",
+           "tt_rse", "tt_eval_plan_create", "tt_eval_plan_destroy", "tt_eval_plan_device_bytes",
+           "tt_eval_plan_at", "tt_eval_plan_backward", "tt_eval_at",
            "tt_eval_at_backward", "tt_sketch_matrix", "tt_kernel_launches", "tt_last_error",
            "tt_version"]
 PHASES = ["gram", "small", "carry", "core", "sketch", "orth", "project"]
@@ -121,6 +124,17 @@ def lib():
     L.tt_rse_work_bytes.restype = SZ
     L.tt_rse.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), I32, P, P, P, P]
     L.tt_rse.restype = I32
+    L.tt_eval_plan_create.argtypes = [I32, PI64, PI64, P, I64, ALLOC_FN, FREE_FN, P, P,
+                                      ctypes.POINTER(P)]
+    L.tt_eval_plan_create.restype = I32
+    L.tt_eval_plan_destroy.argtypes = [P, P]
+    L.tt_eval_plan_destroy.restype = None
+    L.tt_eval_plan_device_bytes.argtypes = [P]
+    L.tt_eval_plan_device_bytes.restype = SZ
+    L.tt_eval_plan_at.argtypes = [P, ctypes.POINTER(P), P, P]
+    L.tt_eval_plan_at.restype = I32
+    L.tt_eval_plan_backward.argtypes = [P, ctypes.POINTER(P), P, ctypes.POINTER(P), P]
+    L.tt_eval_plan_backward.restype = I32
     L.tt_eval_at.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P, P]
     L.tt_eval_at.restype = I32
     L.tt_eval_at_backward.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P,
@@ -492,10 +506,111 @@ def _eval_operands(cores, idx, gout=None):
     return dev, cores_c, idx_c, gout_c
 
 
+def _check_cores(cores, dims, ranks):
+    d = len(dims)
+    if len(cores) != d:
+        raise ValueError(f"expected {d} cores")
+    for k, g in enumerate(cores):
+        if tuple(g.shape) != (ranks[k], dims[k], ranks[k + 1]):
+            raise ValueError(f"core {k} has shape {tuple(g.shape)}, the plan wants "
+                             f"{(ranks[k], dims[k], ranks[k + 1])}")
+
+
+class EvalPlan:
+    """Plan of the masked evaluation for one index set (decoded indices, the
+    entries ordered by each core's index, chunk flags), built once on the
+    GPU and reused by every evaluation and gradient.  Its device block comes
+    from torch's caching allocator and is released by close() or garbage
+    collection.  An index outside [0, prod(dims)) raises TTError(TT_EINVAL)."""
+
+    def __init__(self, dims, ranks, idx, stream=None):
+        dims = [int(x) for x in dims]
+        ranks = [int(x) for x in ranks]
+        if not isinstance(idx, torch.Tensor) or idx.dtype != torch.int64 or not idx.is_cuda:
+            raise TypeError("idx must be an int64 CUDA tensor")
+        self.dims, self.ranks = dims, ranks
+        self.device = idx.device
+        self.shape = idx.shape
+        idx_c = idx.reshape(-1).contiguous()
+        self.n = idx_c.numel()
+        self._alloc = _TorchAllocator(self.device)
+        self._h = None
+        st, st_ptr = _stream(stream)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device), torch.cuda.stream(st):
+            _check(lib().tt_eval_plan_create(len(dims), _i64(dims), _i64(ranks),
+                                             ctypes.c_void_p(idx_c.data_ptr()), self.n,
+                                             self._alloc._alloc, self._alloc._free, None, st_ptr,
+                                             ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def device_bytes(self):
+        return int(lib().tt_eval_plan_device_bytes(self._h))
+
+    def _cores(self, cores):
+        _check_cores(cores, self.dims, self.ranks)
+        for g in cores:
+            if not g.is_cuda or g.dtype != torch.float32 or g.device != self.device:
+                raise TypeError("cores must be float32 CUDA tensors on the plan's device")
+        return [g.contiguous() for g in cores]
+
+    def at(self, cores, stream=None):
+        """x_e at the plan's indices (FP32, shaped like the plan's idx)."""
+        cores_c = self._cores(cores)
+        st, st_ptr = _stream(stream)
+        with torch.cuda.device(self.device), torch.cuda.stream(st):
+            out = torch.empty(self.n, dtype=torch.float32, device=self.device)
+            ptrs = (ctypes.c_void_p * len(cores_c))(*[g.data_ptr() for g in cores_c])
+            _check(lib().tt_eval_plan_at(self._h, ptrs, ctypes.c_void_p(out.data_ptr()), st_ptr))
+        return out.view(self.shape)
+
+    def backward(self, cores, gout, stream=None, out=None):
+        """Core gradients of sum_e gout_e x_e; accumulated into ``out`` (a list
+        of tensors shaped like the cores) if given, else into fresh zeros.
+        Bitwise reproducible for this plan."""
+        cores_c = self._cores(cores)
+        if not isinstance(gout, torch.Tensor) or gout.dtype != torch.float32 or not gout.is_cuda \
+                or gout.device != self.device or gout.numel() != self.n:
+            raise TypeError("gout must be a float32 CUDA tensor with one value per index")
+        gout_c = gout.reshape(-1).contiguous()
+        st, st_ptr = _stream(stream)
+        with torch.cuda.device(self.device), torch.cuda.stream(st):
+            if out is None:
+                grads = [torch.zeros_like(g) for g in cores_c]
+            else:
+                _check_cores(out, self.dims, self.ranks)
+                if any(not g.is_contiguous() or g.dtype != torch.float32 or g.device != self.device
+                       for g in out):
+                    raise TypeError("out must hold contiguous float32 tensors on the plan's device")
+                grads = list(out)
+            ptrs = (ctypes.c_void_p * len(cores_c))(*[g.data_ptr() for g in cores_c])
+            gptrs = (ctypes.c_void_p * len(grads))(*[g.data_ptr() for g in grads])
+            _check(lib().tt_eval_plan_backward(self._h, ptrs, ctypes.c_void_p(gout_c.data_ptr()),
+                                               gptrs, st_ptr))
+        return grads
+
+    def close(self, stream=None):
+        if getattr(self, "_h", None) is not None:
+            st, st_ptr = _stream(stream)
+            with torch.cuda.device(self.device):
+                lib().tt_eval_plan_destroy(self._h, st_ptr)
+            self._h = None
+            self._alloc.live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def tt_eval_at(cores, idx, stream=None):
     """x_e = G_1[i_1] ... G_d[i_d] at int64 row-major linear indices (FP32).
-    An index outside [0, prod(dims)) raises TTError(TT_EINVAL) (the kernel
-    skips it and reports it; nothing out of bounds is read)."""
+    ``idx`` may be an EvalPlan.  An index outside [0, prod(dims)) raises
+    TTError(TT_EINVAL) before any core memory is read for it."""
+    if isinstance(idx, EvalPlan):
+        return idx.at(cores, stream)
     d, dims, ranks = _core_meta(cores)
     dev, cores_c, idx_c, _ = _eval_operands(cores, idx)
     st, st_ptr = _stream(stream)
@@ -509,7 +624,10 @@ def tt_eval_at(cores, idx, stream=None):
 
 def tt_eval_at_backward(cores, idx, gout, stream=None):
     """Core gradients of sum_e gout_e x_e (FP32), fresh zeroed buffers.
-    Deterministic: the same inputs give bitwise-equal gradients."""
+    ``idx`` may be an EvalPlan.  Deterministic: the same inputs give
+    bitwise-equal gradients (no floating-point atomics)."""
+    if isinstance(idx, EvalPlan):
+        return idx.backward(cores, gout, stream)
     d, dims, ranks = _core_meta(cores)
     dev, cores_c, idx_c, gout_c = _eval_operands(cores, idx, gout)
     st, st_ptr = _stream(stream)
@@ -524,17 +642,28 @@ def tt_eval_at_backward(cores, idx, gout, stream=None):
 
 
 class TTEvalMasked(torch.autograd.Function):
-    """Masked TT evaluation with the library's hand-written backward kernel."""
+    """Masked TT evaluation with the library's hand-written backward kernels.
+    ``apply(idx, *cores)``: idx an int64 CUDA tensor or an EvalPlan (reused
+    across calls, as in an optimisation loop)."""
 
     @staticmethod
     def forward(ctx, idx, *cores):
-        ctx.save_for_backward(idx, *cores)
+        if isinstance(idx, EvalPlan):
+            ctx.plan = idx
+            ctx.save_for_backward(*cores)
+        else:
+            ctx.plan = None
+            ctx.save_for_backward(idx, *cores)
         return tt_eval_at(list(cores), idx)
 
     @staticmethod
     def backward(ctx, gout):
-        idx, *cores = ctx.saved_tensors
-        grads = tt_eval_at_backward(cores, idx, gout.to(torch.float32))
+        saved = ctx.saved_tensors
+        if ctx.plan is not None:
+            idx, cores = ctx.plan, list(saved)
+        else:
+            idx, cores = saved[0], list(saved[1:])
+        grads = tt_eval_at_backward(cores, idx, gout.to(torch.float32).contiguous())
         return (None, *grads)
 
 

@@ -6,7 +6,8 @@ i_e, the cores are initialised by a fixed-rank TT-URV sweep of the zero-filled
 observations scaled by the inverse sampling rate, then fitted to the loss
 f = 1/2 sum_e (x(i_e) - m_e)^2 by full-batch gradient descent: x and the core
 gradients come from the library's masked evaluation and its backward
-(interfaces recomputed per entry), and each step length is found by Armijo
+(interfaces recomputed per entry, one plan of the observation set reused
+by every call), and each step length is found by Armijo
 backtracking starting from twice the previous one, so the loss never
 increases.  The paper's own solver (Riemannian gradient with a TT retraction)
 is not reproduced; only its observation operator P_Omega and the TT-UTV
@@ -18,7 +19,7 @@ import math
 
 import torch
 
-from . import tt_eval_at, tt_eval_at_backward, tt_utv
+from . import EvalPlan, tt_utv
 
 
 def complete(values, idx, shape, ranks, p_obs=None, steps=200, c1=1e-4, alpha0=1.0,
@@ -47,15 +48,18 @@ def complete(values, idx, shape, ranks, p_obs=None, steps=200, c1=1e-4, alpha0=1
                    stream=stream).cores
     del z
 
+    # one plan for the fixed observation set: every evaluation and gradient reuses it
+    plan = EvalPlan(shape, [1, *ranks, 1], idx, stream)
+
     def loss_of(cs):
-        r = tt_eval_at(cs, idx, stream) - values
+        r = plan.at(cs, stream) - values
         return r, 0.5 * float(torch.dot(r, r))
 
     r, loss = loss_of(cores)
     losses = [loss]
     alpha = alpha0
     for _ in range(steps):
-        grads = tt_eval_at_backward(cores, idx, r, stream)
+        grads = plan.backward(cores, r, stream)
         gn2 = float(sum(torch.dot(g.reshape(-1), g.reshape(-1)) for g in grads))
         if gn2 == 0.0:
             break

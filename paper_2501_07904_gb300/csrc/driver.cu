@@ -1296,30 +1296,6 @@ tt_status tt_rse(int32_t d, const int64_t* dims, const int64_t* ranks, const voi
   return TT_OK;
 }
 
-tt_status tt_eval_at(int32_t d, const int64_t* dims, const int64_t* ranks,
-                     const float* const* cores, const int64_t* idx, int64_t n, float* out,
-                     void* stream) {
-  g_err.clear();
-  if (!dims || !ranks || !cores || (n > 0 && (!idx || !out)) || n < 0)
-    return fail(TT_EINVAL, "bad argument");
-  cudaError_t e = ttk::eval_at(d, dims, ranks, cores, idx, n, out, (cudaStream_t)stream);
-  if (e == cudaErrorInvalidValue) return fail(TT_EINVAL, "d in [1,16], ranks in [1,64], r_0 = r_d = 1");
-  if (e != cudaSuccess) return cuda_fail(e, "tt_eval_at");
-  return TT_OK;
-}
-
-tt_status tt_eval_at_backward(int32_t d, const int64_t* dims, const int64_t* ranks,
-                              const float* const* cores, const int64_t* idx, int64_t n,
-                              const float* gout, float* const* grads, void* stream) {
-  g_err.clear();
-  if (!dims || !ranks || !cores || !grads || (n > 0 && (!idx || !gout)) || n < 0)
-    return fail(TT_EINVAL, "bad argument");
-  cudaError_t e = ttk::eval_at_backward(d, dims, ranks, cores, idx, n, gout, grads, (cudaStream_t)stream);
-  if (e == cudaErrorInvalidValue) return fail(TT_EINVAL, "d in [1,16], ranks in [1,64], r_0 = r_d = 1");
-  if (e != cudaSuccess) return cuda_fail(e, "tt_eval_at_backward");
-  return TT_OK;
-}
-
 tt_status tt_sketch_matrix(int64_t rows, int64_t cols, uint64_t seed, int32_t step, int32_t dtype,
                            void* out, void* stream) {
   g_err.clear();

@@ -125,10 +125,5 @@ size_t diff_sumsq_parts_bytes();
 cudaError_t diff_sumsq(const void* a, const void* x, bool fp64, int64_t n, double* part,
                        bool first, cudaStream_t st);
 cudaError_t sum_pairs(const double* part, double* out, cudaStream_t st);
-cudaError_t eval_at(int d, const int64_t* dims, const int64_t* ranks, const float* const* cores,
-                    const int64_t* idx, int64_t n, float* out, cudaStream_t st);
-cudaError_t eval_at_backward(int d, const int64_t* dims, const int64_t* ranks,
-                             const float* const* cores, const int64_t* idx, int64_t n,
-                             const float* gout, float* const* grads, cudaStream_t st);
 
 }  // namespace ttk

@@ -1,5 +1,5 @@
 // Elementwise kernels of the sweep (sketch matrix, casts, core copies,
-// sums of squares) and the masked TT evaluation with its gradient.
+// sums of squares).
 #include <algorithm>
 #include <atomic>
 
@@ -75,94 +75,6 @@ __global__ void sum_parts_kernel(const double* __restrict__ v, int n, double* ou
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
   s = block_sum(s, red);
   if (threadIdx.x == 0) *out = s;
-}
-
-constexpr int kEvalMaxD = 16;
-constexpr int kEvalMaxR = 64;
-
-struct EvalArgs {
-  int d;
-  int64_t dims[kEvalMaxD];
-  int ranks[kEvalMaxD + 1];
-  const float* cores[kEvalMaxD];
-  float* grads[kEvalMaxD];
-};
-
-__device__ __forceinline__ void decode(const EvalArgs& a, int64_t lin, int* ix) {
-  for (int k = a.d - 1; k >= 0; --k) {
-    ix[k] = (int)(lin % a.dims[k]);
-    lin /= a.dims[k];
-  }
-}
-
-// x = G_1[i_1] ... G_d[i_d], left to right, one entry per thread.
-__global__ void eval_kernel(EvalArgs a, const int64_t* __restrict__ idx, int64_t n,
-                            float* __restrict__ out) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int ix[kEvalMaxD];
-    decode(a, idx[e], ix);
-    float v[kEvalMaxR], w[kEvalMaxR];
-    v[0] = 1.0f;
-    for (int k = 0; k < a.d; ++k) {
-      const int r0 = a.ranks[k], r1 = a.ranks[k + 1];
-      const float* g = a.cores[k] + (int64_t)ix[k] * r1;  // G_k[a, i_k, b] at (a*I_k + i_k)*r1 + b
-      const int64_t sa = a.dims[k] * r1;
-      for (int b = 0; b < r1; ++b) w[b] = 0.0f;
-      for (int q = 0; q < r0; ++q) {
-        const float vq = v[q];
-        const float* gr = g + q * sa;
-        for (int b = 0; b < r1; ++b) w[b] = fmaf(vq, gr[b], w[b]);
-      }
-      for (int b = 0; b < r1; ++b) v[b] = w[b];
-    }
-    out[e] = v[0];
-  }
-}
-
-// dG_k[:, i_k, :] += gout * left_k^T right_k^T, interfaces recomputed per core.
-__global__ void eval_backward_kernel(EvalArgs a, const int64_t* __restrict__ idx, int64_t n,
-                                     const float* __restrict__ gout) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int ix[kEvalMaxD];
-    decode(a, idx[e], ix);
-    const float g = gout[e];
-    for (int k = 0; k < a.d; ++k) {
-      float left[kEvalMaxR], right[kEvalMaxR], w[kEvalMaxR];
-      // left = G_1[i_1] ... G_{k-1}[i_{k-1}]  (1 x r_{k-1})
-      left[0] = 1.0f;
-      for (int t = 0; t < k; ++t) {
-        const int r0 = a.ranks[t], r1 = a.ranks[t + 1];
-        const float* gg = a.cores[t] + (int64_t)ix[t] * r1;
-        const int64_t sa = a.dims[t] * r1;
-        for (int b = 0; b < r1; ++b) w[b] = 0.0f;
-        for (int q = 0; q < r0; ++q)
-          for (int b = 0; b < r1; ++b) w[b] = fmaf(left[q], gg[q * sa + b], w[b]);
-        for (int b = 0; b < r1; ++b) left[b] = w[b];
-      }
-      // right = G_{k+1}[i_{k+1}] ... G_d[i_d]  (r_k x 1)
-      right[0] = 1.0f;
-      for (int t = a.d - 1; t > k; --t) {
-        const int r0 = a.ranks[t], r1 = a.ranks[t + 1];
-        const float* gg = a.cores[t] + (int64_t)ix[t] * r1;
-        const int64_t sa = a.dims[t] * r1;
-        for (int q = 0; q < r0; ++q) {
-          float s = 0.0f;
-          for (int b = 0; b < r1; ++b) s = fmaf(gg[q * sa + b], right[b], s);
-          w[q] = s;
-        }
-        for (int q = 0; q < r0; ++q) right[q] = w[q];
-      }
-      const int r0 = a.ranks[k], r1 = a.ranks[k + 1];
-      float* gk = a.grads[k] + (int64_t)ix[k] * r1;
-      const int64_t sa = a.dims[k] * r1;
-      for (int q = 0; q < r0; ++q) {
-        const float lq = g * left[q];
-        for (int b = 0; b < r1; ++b) atomicAdd(gk + q * sa + b, lq * right[b]);
-      }
-    }
-  }
 }
 
 // Columns of a partitioned unfolding back in order: `in` holds P rank blocks
@@ -287,22 +199,6 @@ int grid_for(int64_t n, int threads) {
   return (int)b;
 }
 
-bool fill_eval_args(EvalArgs& a, int d, const int64_t* dims, const int64_t* ranks,
-                    const float* const* cores, float* const* grads) {
-  if (d < 1 || d > kEvalMaxD) return false;
-  a.d = d;
-  for (int k = 0; k < d; ++k) {
-    a.dims[k] = dims[k];
-    a.cores[k] = cores[k];
-    a.grads[k] = grads ? grads[k] : nullptr;
-  }
-  for (int k = 0; k <= d; ++k) {
-    if (ranks[k] < 1 || ranks[k] > kEvalMaxR) return false;
-    a.ranks[k] = (int)ranks[k];
-  }
-  return a.ranks[0] == 1 && a.ranks[d] == 1;
-}
-
 }  // namespace
 
 cudaError_t fill_sketch(void* out, bool fp64, int64_t rows, int64_t cols, uint64_t seed,
@@ -372,27 +268,6 @@ cudaError_t sumsq(const void* x, bool fp64, int64_t n, double* out, void* ws, cu
   else
     sumsq_kernel<float><<<g, 256, 0, st>>>((const float*)x, n, part);
   sum_parts_kernel<<<1, 1024, 0, st>>>(part, g, out);
-  return cudaGetLastError();
-}
-
-cudaError_t eval_at(int d, const int64_t* dims, const int64_t* ranks, const float* const* cores,
-                    const int64_t* idx, int64_t n, float* out, cudaStream_t st) {
-  EvalArgs a;
-  if (!fill_eval_args(a, d, dims, ranks, cores, nullptr)) return cudaErrorInvalidValue;
-  if (n <= 0) return cudaSuccess;
-  count_launch();
-  eval_kernel<<<grid_for(n, 128), 128, 0, st>>>(a, idx, n, out);
-  return cudaGetLastError();
-}
-
-cudaError_t eval_at_backward(int d, const int64_t* dims, const int64_t* ranks,
-                             const float* const* cores, const int64_t* idx, int64_t n,
-                             const float* gout, float* const* grads, cudaStream_t st) {
-  EvalArgs a;
-  if (!fill_eval_args(a, d, dims, ranks, cores, grads)) return cudaErrorInvalidValue;
-  if (n <= 0) return cudaSuccess;
-  count_launch();
-  eval_backward_kernel<<<grid_for(n, 128), 128, 0, st>>>(a, idx, n, gout);
   return cudaGetLastError();
 }
 

@@ -221,3 +221,30 @@ def test_sharded_arguments_rejected(L):
     L.tt_opts_default(ctypes.byref(o))
     o.reverse = 1
     assert call(tu.tt_shard(2, 0, noop_r, noop_g, None), opts=ctypes.byref(o)) == 7   # reversed: unsupported
+
+
+def test_eval_plan_arguments_rejected(L):
+    """Plan creation validates its shape before any device work; the plan
+    calls reject a NULL plan; destroying NULL is a no-op."""
+    dims, ranks = tu._i64([3, 4]), tu._i64([1, 2, 1])
+    out = ctypes.c_void_p()
+    idx = ctypes.c_void_p(1)
+
+    def create(d=2, dm=dims, rk=ranks, n=4, alloc=None, free=None, o=True):
+        return L.tt_eval_plan_create(d, dm, rk, idx, n, alloc or tu.ALLOC_FN(0),
+                                     free or tu.FREE_FN(0), None, None,
+                                     ctypes.byref(out) if o else None)
+
+    assert create(o=False) == 1
+    assert create(d=0) == 1 and create(d=17, dm=tu._i64([2] * 17), rk=tu._i64([1] * 18)) == 1
+    assert create(rk=tu._i64([1, 65, 1])) == 1 and create(rk=tu._i64([2, 2, 1])) == 1
+    assert create(dm=tu._i64([3, 0])) == 1 and create(dm=tu._i64([3, 1 << 31])) == 1
+    assert create(n=-1) == 1 and create(n=1 << 31) == 1
+    assert create(alloc=tu.ALLOC_FN(lambda b, s, c: None)) == 1      # alloc without free
+    assert out.value is None
+    assert L.tt_last_error() != b""
+    ptrs = (ctypes.c_void_p * 2)(1, 1)
+    assert L.tt_eval_plan_at(None, ptrs, ctypes.c_void_p(1), None) == 1
+    assert L.tt_eval_plan_backward(None, ptrs, ctypes.c_void_p(1), ptrs, None) == 1
+    L.tt_eval_plan_destroy(None, None)
+    assert L.tt_eval_plan_device_bytes(None) == 0
