@@ -307,8 +307,9 @@ tt_status tt_rse(int32_t d, const int64_t* dims, const int64_t* ranks, const voi
  * A plan holds what depends only on the index set: the decoded mode indices
  * and, for every core, the entries ordered stably by that core's index (ties
  * by a neighbouring core's).  Device bytes: 8 d n (indices and orders),
- * d ceil(n/128) (chunk flags), 2 ceil(n/128) max_k(round4(r_{k-1}) round4(r_k)) * 4
- * (per-chunk gradient partials), 4 n + 4 * 256 ceil(n/2048) (sort scratch).
+ * 5 d ceil(n/128) (chunk flags and slice ends), 2 ceil(n/128)
+ * max_k(round4(r_{k-1}) round4(r_k)) * 4 (per-chunk gradient partials),
+ * 4 n + 4 * 256 ceil(n/2048) (sort scratch).
  *
  * Gradients are summed in a fixed order with no floating-point atomics: a
  * plan gives bitwise-equal results on every call (and two plans built from

@@ -49,6 +49,10 @@ constexpr int kSortTile = 2048;    // entries per radix tile (256 threads x 8 ro
 static_assert(kChunk == kEvalThreads, "the forward contraction runs one thread per entry");
 
 __device__ __forceinline__ int round4_dev(int x) { return (x + 3) & ~3; }
+
+// Two FP32 fused multiply-adds in one packed instruction (each lane rounded
+// to nearest, as fmaf).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 // smallest power of two >= x, and >= 4 (the width of a chain-step lane group)
 __device__ __forceinline__ int group_width(int x) {
   const int p = x <= 1 ? 1 : 1 << (32 - __clz(x - 1));
@@ -186,8 +190,12 @@ __global__ void __launch_bounds__(1024) scan_kernel(int32_t* __restrict__ a, int
 // Chunk bits of core k's order: 1 = the first slice continues from the
 // previous chunk, 2 = the last slice continues into the next chunk, 4 = one
 // slice only.
+// A chunk holding the start of a slice that continues past it (its "head")
+// also gets the last chunk of that slice in head_end (found by binary search
+// on the sorted keys); other chunks get -1.
 __global__ void chunk_info_kernel(const int32_t* __restrict__ keyk, const int32_t* __restrict__ perm,
-                                  int64_t n, int64_t nchunks, uint8_t* __restrict__ info) {
+                                  int64_t n, int64_t nchunks, uint8_t* __restrict__ info,
+                                  int32_t* __restrict__ head_end) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t first = c * kChunk, last = min(n, first + kChunk) - 1;
@@ -197,7 +205,28 @@ __global__ void chunk_info_kernel(const int32_t* __restrict__ keyk, const int32_
     if (last + 1 < n && keyk[perm[last + 1]] == kl) b |= 2;
     if (kf == kl) b |= 4;
     info[c] = b;
+    int32_t he = -1;
+    if ((b & 2) && !((b & 4) && (b & 1))) {
+      int64_t lo = last + 1, hi = n;  // first position past the slice lies in (last, n]
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (keyk[perm[mid]] == kl)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      he = (int32_t)((lo - 1) / kChunk);
+    }
+    head_end[c] = he;
   }
+}
+
+// pos[perm[p]] = p: an entry's position in an order.
+__global__ void inverse_perm_kernel(const int32_t* __restrict__ perm, int64_t n,
+                                    int32_t* __restrict__ pos) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x)
+    pos[perm[p]] = (int32_t)p;
 }
 
 // ------------------------------------------------------------------ evaluation
@@ -212,11 +241,23 @@ struct PassArgs {
   const int32_t* ix;   // [d][n]
   const int32_t* perm; // [n] order of core k
   const uint8_t* info; // [nchunks]
+  const int32_t* head_end;  // [nchunks]
   const float* gout;   // [n] (backward)
   float* grad;         // core k's gradient (backward)
   float* slots;        // [2 * nchunks][slot_elems] (backward)
   int slot_elems;
   float* out;          // [n] (forward)
+  // d = 3 backward: the middle core's pass (mode 1) writes, per entry,
+  // gout (G_2[:, i_2, :] G_3[:, i_3, 0]) at the entry's position in core 1's
+  // order (rows1, r_1 wide) and gout G_1[0, i_1, :] G_2[:, i_2, :] at its
+  // position in core 3's order (rows3, r_2 wide); the outer cores' passes
+  // read those rows as their interface (mode 2: right side given, core 1;
+  // mode 3: left side given, core 3).  Mode 0: interfaces from chains.
+  int mode;
+  const int32_t* pos1;  // [n] entry -> position in core 1's order (mode 1)
+  const int32_t* pos3;  // [n] entry -> position in core 3's order (mode 1)
+  float* rows1;         // [n][r_1]
+  float* rows3;         // [n][r_2]
   // shared-memory carve-up (in 4-byte words)
   int sL, sR, sT;      // row strides of the L, R and scratch buffers (0: buffer unused)
   int off_L, off_R, off_T, off_U;
@@ -236,9 +277,9 @@ __device__ void left_step(const float* __restrict__ G, int I, int r0, int r1,
   const int t = threadIdx.x, g = t / W, o = t % W;
   if (o >= round4_dev(r1)) return;
   const bool live = o < r1;
-  float col[NI];
+  float2 col[NI / 2];  // (col[2h], col[2h+1]) = rows 2h, 2h+1 of column o
 #pragma unroll
-  for (int q = 0; q < NI; ++q) col[q] = 0.0f;
+  for (int h = 0; h < NI / 2; ++h) col[h] = make_float2(0.0f, 0.0f);
   int cur = -1;
   const int p1 = min(cnt, (g + 1) * E);
   for (int p = g * E; p < p1; ++p) {
@@ -246,47 +287,45 @@ __device__ void left_step(const float* __restrict__ G, int I, int r0, int r1,
     if (live && i != cur) {
       cur = i;
       const float* gp = G + (int64_t)i * r1 + o;
+      const int64_t rs = (int64_t)I * r1;
 #pragma unroll
-      for (int q = 0; q < NI; ++q)
-        if (q < r0) col[q] = __ldg(gp + (int64_t)q * I * r1);
+      for (int h = 0; h < NI / 2; ++h) {
+        if (2 * h < r0) col[h].x = __ldg(gp + 2 * h * rs);
+        if (2 * h + 1 < r0) col[h].y = __ldg(gp + (2 * h + 1) * rs);
+      }
     }
-    float acc = 0.0f;
+    // rows 4h, 4h+1, 4h+2, 4h+3 go to four running sums, added at the end
+    float2 acc = make_float2(0.0f, 0.0f), acc2 = make_float2(0.0f, 0.0f);
     if (live) {
-      if (in == nullptr) {
-        acc = col[0];
-      } else {
-        const float* vp = in + p * sin;
+      const float* vp = in + p * sin;
 #pragma unroll
-        for (int q4 = 0; q4 < NI; q4 += 4) {
-          if (q4 < r0) {
-            const float4 v = *reinterpret_cast<const float4*>(vp + q4);
-            acc = fmaf(v.x, col[q4], acc);
-            acc = fmaf(v.y, col[q4 + 1], acc);
-            acc = fmaf(v.z, col[q4 + 2], acc);
-            acc = fmaf(v.w, col[q4 + 3], acc);
-          }
+      for (int q4 = 0; q4 < NI; q4 += 4) {
+        if (q4 < r0) {
+          const float4 v = *reinterpret_cast<const float4*>(vp + q4);
+          acc = ffma2(make_float2(v.x, v.y), col[q4 / 2], acc);
+          acc2 = ffma2(make_float2(v.z, v.w), col[q4 / 2 + 1], acc2);
         }
       }
     }
-    out[p * sout + o] = acc;
+    out[p * sout + o] = (acc.x + acc.y) + (acc2.x + acc2.y);
   }
 }
 
-// Right chain step: out[p][q] = sum_b G[(q*I + i_p) r1 + b] in[p][b] for
-// q < r0 (in == null: the vector [1], so out is the slice's column).  Lane o
-// keeps row o of the current slice (NI >= round4(r1) values).
+// Right chain step: out[p][q] = s_p sum_b G[(q*I + i_p) r1 + b] in[p][b] for
+// q < r0, s_p = scale[p] (1 when scale is null).  Lane o keeps row o of the
+// current slice (NI >= round4(r1) values).
 template <int NI>
 __device__ void right_step(const float* __restrict__ G, int I, int r0, int r1,
                            const int32_t* __restrict__ iv, const float* in, int sin, float* out,
-                           int sout, int cnt) {
+                           int sout, int cnt, const float* scale) {
   const int W = group_width(r0);
   const int groups = kEvalThreads / W, E = kChunk / groups;
   const int t = threadIdx.x, g = t / W, o = t % W;
   if (o >= round4_dev(r0)) return;
   const bool live = o < r0;
-  float row[NI];
+  float2 row[NI / 2];  // (row[2h], row[2h+1]) = columns 2h, 2h+1 of row o
 #pragma unroll
-  for (int b = 0; b < NI; ++b) row[b] = 0.0f;
+  for (int h = 0; h < NI / 2; ++h) row[h] = make_float2(0.0f, 0.0f);
   int cur = -1;
   const int p1 = min(cnt, (g + 1) * E);
   for (int p = g * E; p < p1; ++p) {
@@ -295,60 +334,222 @@ __device__ void right_step(const float* __restrict__ G, int I, int r0, int r1,
       cur = i;
       const float* gp = G + ((int64_t)o * I + i) * r1;
 #pragma unroll
-      for (int b = 0; b < NI; ++b)
-        if (b < r1) row[b] = __ldg(gp + b);
+      for (int h = 0; h < NI / 2; ++h) {
+        if (2 * h < r1) row[h].x = __ldg(gp + 2 * h);
+        if (2 * h + 1 < r1) row[h].y = __ldg(gp + 2 * h + 1);
+      }
     }
-    float acc = 0.0f;
+    float2 acc = make_float2(0.0f, 0.0f), acc2 = make_float2(0.0f, 0.0f);
     if (live) {
-      if (in == nullptr) {
-        acc = row[0];
-      } else {
-        const float* vp = in + p * sin;
+      const float* vp = in + p * sin;
 #pragma unroll
-        for (int b4 = 0; b4 < NI; b4 += 4) {
-          if (b4 < r1) {
-            const float4 v = *reinterpret_cast<const float4*>(vp + b4);
-            acc = fmaf(row[b4], v.x, acc);
-            acc = fmaf(row[b4 + 1], v.y, acc);
-            acc = fmaf(row[b4 + 2], v.z, acc);
-            acc = fmaf(row[b4 + 3], v.w, acc);
-          }
+      for (int b4 = 0; b4 < NI; b4 += 4) {
+        if (b4 < r1) {
+          const float4 v = *reinterpret_cast<const float4*>(vp + b4);
+          acc = ffma2(row[b4 / 2], make_float2(v.x, v.y), acc);
+          acc2 = ffma2(row[b4 / 2 + 1], make_float2(v.z, v.w), acc2);
         }
       }
     }
-    out[p * sout + o] = acc;
+    const float y = (acc.x + acc.y) + (acc2.x + acc2.y);
+    out[p * sout + o] = scale ? y * scale[p] : y;
   }
 }
 
+// First step of a chain (the input is the vector [1]): a gather, spread over
+// (entry, element) so every load is independent.  Left: the row
+// G_1[0, i_p, :]; right: the column G_d[:, i_p, 0]; times scale[p] when
+// scale is set.  Padding is zeroed.
+template <bool LEFT>
+__device__ void copy_step(const float* __restrict__ G, int I, int r, const int32_t* __restrict__ iv,
+                          float* out, int sout, int cnt, const float* scale) {
+  const int W = group_width(r), lw = __ffs(W) - 1, groups = kEvalThreads >> lw;
+  const int t = threadIdx.x, o = t & (W - 1);
+  if (o >= round4_dev(r)) return;
+  const bool live = o < r;
+  // eight gathers in flight per thread before their stores
+  for (int pb = t >> lw; pb < cnt; pb += 8 * groups) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int p = pb + u * groups;
+      v[u] = 0.0f;
+      if (live && p < cnt) {
+        const int64_t i = iv[p];
+        v[u] = __ldg(LEFT ? G + i * r + o : G + (int64_t)o * I + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int p = pb + u * groups;
+      if (p < cnt) out[p * sout + o] = scale ? v[u] * scale[p] : v[u];
+    }
+  }
+}
+
+// Stage the zero-padded slice G[:, i, :] (r0 x r1) as U[rLp][rRp], eight
+// loads in flight per thread.
+__device__ __forceinline__ void stage_slice(const float* __restrict__ G, int I, int i, int r0,
+                                            int r1, float* U) {
+  const int rLp = round4_dev(r0), rRp = round4_dev(r1), m = rLp * rRp;
+  for (int eb = threadIdx.x; eb < m; eb += 8 * kEvalThreads) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = eb + u * kEvalThreads;
+      const int q = e / rRp, b = e - q * rRp;
+      v[u] = (e < m && q < r0 && b < r1) ? __ldg(G + ((int64_t)q * I + i) * r1 + b) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = eb + u * kEvalThreads;
+      if (e < m) U[e] = v[u];
+    }
+  }
+}
+
+// Stage cnt given rows (rows[p][0..r), contiguous) as dst[p][0..round4(r)),
+// zero padded; vector loads when r is a multiple of 4.
+__device__ __forceinline__ void stage_rows(const float* __restrict__ rows, int r, int cnt,
+                                           float* dst, int sd) {
+  const int t = threadIdx.x;
+  if ((r & 3) == 0) {
+    const int r4 = r >> 2, m = cnt * r4;
+    const float4* src = reinterpret_cast<const float4*>(rows);
+    for (int fb = t; fb < m; fb += 8 * kEvalThreads) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int f = fb + u * kEvalThreads;
+        v[u] = f < m ? __ldg(src + f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int f = fb + u * kEvalThreads;
+        if (f < m) {
+          const int p = f / r4, o = (f - p * r4) * 4;
+          *reinterpret_cast<float4*>(dst + p * sd + o) = v[u];
+        }
+      }
+    }
+  } else {
+    const int rp = round4_dev(r), m = cnt * rp;
+    for (int eb = t; eb < m; eb += 8 * kEvalThreads) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = eb + u * kEvalThreads;
+        const int p = e / rp, o = e - p * rp;
+        v[u] = (e < m && o < r) ? __ldg(rows + (int64_t)p * r + o) : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = eb + u * kEvalThreads;
+        if (e < m) {
+          const int p = e / rp, o = e - p * rp;
+          dst[p * sd + o] = v[u];
+        }
+      }
+    }
+  }
+}
+
+// scale: per-entry factor applied to the step's output (null: none; left
+// chains take it on their first copy only).
 template <bool LEFT>
 __device__ __forceinline__ void chain_step(const float* G, int I, int r0, int r1, const int32_t* iv,
                                            const float* in, int sin, float* out, int sout,
-                                           int cnt) {
+                                           int cnt, const float* scale) {
+  if (in == nullptr) {
+    if (LEFT)
+      copy_step<true>(G, I, r1, iv, out, sout, cnt, scale);
+    else
+      copy_step<false>(G, I, r0, iv, out, sout, cnt, scale);
+    return;
+  }
   const int nin = LEFT ? r0 : r1;
   if (nin <= 4) {
     LEFT ? left_step<4>(G, I, r0, r1, iv, in, sin, out, sout, cnt)
-         : right_step<4>(G, I, r0, r1, iv, in, sin, out, sout, cnt);
+         : right_step<4>(G, I, r0, r1, iv, in, sin, out, sout, cnt, scale);
   } else if (nin <= 8) {
     LEFT ? left_step<8>(G, I, r0, r1, iv, in, sin, out, sout, cnt)
-         : right_step<8>(G, I, r0, r1, iv, in, sin, out, sout, cnt);
+         : right_step<8>(G, I, r0, r1, iv, in, sin, out, sout, cnt, scale);
   } else if (nin <= 16) {
     LEFT ? left_step<16>(G, I, r0, r1, iv, in, sin, out, sout, cnt)
-         : right_step<16>(G, I, r0, r1, iv, in, sin, out, sout, cnt);
+         : right_step<16>(G, I, r0, r1, iv, in, sin, out, sout, cnt, scale);
   } else if (nin <= 32) {
     LEFT ? left_step<32>(G, I, r0, r1, iv, in, sin, out, sout, cnt)
-         : right_step<32>(G, I, r0, r1, iv, in, sin, out, sout, cnt);
+         : right_step<32>(G, I, r0, r1, iv, in, sin, out, sout, cnt, scale);
   } else {
     LEFT ? left_step<64>(G, I, r0, r1, iv, in, sin, out, sout, cnt)
-         : right_step<64>(G, I, r0, r1, iv, in, sin, out, sout, cnt);
+         : right_step<64>(G, I, r0, r1, iv, in, sin, out, sout, cnt, scale);
+  }
+}
+
+// Mode 1 (d = 3, middle core, backward) for entry p: with L = gout a (Ls),
+// c (Rs) and M staged in U (rLp x rRp, zero padded),
+//   T[q][p] = gout sum_b M[q][b] c[b]       (core 1's row; row stride kChunk + 1)
+//   rows3[pos3] = sum_q L[q] M[q][:]        (core 3's row)
+// c and the running w stay in registers (NB >= round4(rR)).
+template <int NB>
+__device__ void emit_entry(const PassArgs& a, int p, const float* Ls, const float* Rs, float* Ts,
+                           const float* U, float g, int pos3, int rL, int rR) {
+  const int rLp = round4_dev(rL), rRp = round4_dev(rR);
+  float2 cr[NB / 2], w[NB / 2];
+  const float* rp = Rs + p * a.sR;
+#pragma unroll
+  for (int b4 = 0; b4 < NB; b4 += 4) {
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (b4 < rRp) v = *reinterpret_cast<const float4*>(rp + b4);
+    cr[b4 / 2] = make_float2(v.x, v.y);
+    cr[b4 / 2 + 1] = make_float2(v.z, v.w);
+    w[b4 / 2] = w[b4 / 2 + 1] = make_float2(0.0f, 0.0f);
+  }
+  const float* lp = Ls + p * a.sL;
+  float* tp = Ts + p;  // u of entry p at Ts[q * (kChunk + 1) + p]
+  for (int q4 = 0; q4 < rLp; q4 += 4) {
+    const float4 l = *reinterpret_cast<const float4*>(lp + q4);
+    const float lq[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      const float* mrow = U + (q4 + qq) * rRp;
+      const float2 ll = make_float2(lq[qq], lq[qq]);
+      float2 ua = make_float2(0.0f, 0.0f), ub = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int b4 = 0; b4 < NB; b4 += 4) {
+        if (b4 < rRp) {
+          const float4 m = *reinterpret_cast<const float4*>(mrow + b4);
+          const float2 m01 = make_float2(m.x, m.y), m23 = make_float2(m.z, m.w);
+          ua = ffma2(m01, cr[b4 / 2], ua);
+          ub = ffma2(m23, cr[b4 / 2 + 1], ub);
+          w[b4 / 2] = ffma2(ll, m01, w[b4 / 2]);
+          w[b4 / 2 + 1] = ffma2(ll, m23, w[b4 / 2 + 1]);
+        }
+      }
+      tp[(q4 + qq) * (kChunk + 1)] = ((ua.x + ua.y) + (ub.x + ub.y)) * g;
+    }
+  }
+  float* dst = a.rows3 + (int64_t)pos3 * rR;
+  if ((rR & 3) == 0) {
+#pragma unroll
+    for (int b4 = 0; b4 < NB; b4 += 4)
+      if (b4 < rR)
+        *reinterpret_cast<float4*>(dst + b4) =
+            make_float4(w[b4 / 2].x, w[b4 / 2].y, w[b4 / 2 + 1].x, w[b4 / 2 + 1].y);
+  } else {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (b < rR) dst[b] = (b & 1) ? w[b / 2].y : w[b / 2].x;
   }
 }
 
 // One chunk of core k's order: interfaces, then the forward contraction or
 // the gradient accumulation of core k.
-__global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(kEvalThreads, 5) eval_pass_kernel(PassArgs a) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int segs[kChunk + 1];
   __shared__ int nseg;
+  __shared__ int wstarts[kEvalThreads / 32];
   int32_t* ixs = reinterpret_cast<int32_t*>(sm);  // [d][kChunk] mode indices
   float* gs = sm + a.d * kChunk;                   // [kChunk] gout (backward)
   float* Ls = sm + a.off_L;
@@ -358,40 +559,75 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
   const int t = threadIdx.x, k = a.k, d = a.d;
   const int64_t c = blockIdx.x, p0 = c * kChunk;
   const int cnt = (int)min((int64_t)kChunk, a.n - p0);
+  int32_t* posA = reinterpret_cast<int32_t*>(gs + kChunk);  // [kChunk] (mode 1)
+  int32_t* posB = posA + kChunk;                              // [kChunk] (mode 1)
   for (int p = t; p < cnt; p += kEvalThreads) {
     const int e = a.perm[p0 + p];
-    for (int j = 0; j < d; ++j) ixs[j * kChunk + p] = a.ix[(int64_t)j * a.n + e];
-    if (a.backward) gs[p] = a.gout[e];
+    if (a.mode >= 2) {  // the given rows replace the chains: only i_k is needed
+      ixs[k * kChunk + p] = a.ix[(int64_t)k * a.n + e];
+    } else {
+      for (int j = 0; j < d; ++j) ixs[j * kChunk + p] = a.ix[(int64_t)j * a.n + e];
+      if (a.backward) gs[p] = a.gout[e];
+      if (a.mode == 1) {
+        posA[p] = a.pos1[e];
+        posB[p] = a.pos3[e];
+      }
+    }
   }
   __syncthreads();
-  if (t == 0) {  // runs of equal i_k
+  {  // runs of equal i_k: starts found by warp ballots, listed in order
     const int32_t* key = ixs + k * kChunk;
-    int m = 0;
-    for (int p = 0; p < cnt; ++p)
-      if (p == 0 || key[p] != key[p - 1]) segs[m++] = p;
-    segs[m] = cnt;
-    nseg = m;
+    const bool start = t < cnt && (t == 0 || key[t] != key[t - 1]);
+    const unsigned m = __ballot_sync(0xffffffffu, start);
+    if ((t & 31) == 0) wstarts[t >> 5] = __popc(m);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < kEvalThreads / 32; ++w) {
+      off += w < (t >> 5) ? wstarts[w] : 0;
+      tot += wstarts[w];
+    }
+    if (start) segs[off + __popc(m & ((1u << (t & 31)) - 1u))] = t;
+    if (t == 0) {
+      segs[tot] = cnt;
+      nseg = tot;
+    }
+  }
+  if (a.mode >= 2) {
+    // interfaces given: the stored rows of this order on one side, [1] on the other
+    const bool right = a.mode == 2;
+    const float* rows = right ? a.rows1 : a.rows3;
+    const int r = right ? a.ranks[1] : a.ranks[d - 1];
+    float* dst = right ? Rs : Ls;
+    float* one = right ? Ls : Rs;
+    const int sd = right ? a.sR : a.sL, so = right ? a.sL : a.sR;
+    stage_rows(rows + p0 * r, r, cnt, dst, sd);
+    for (int p = t; p < cnt; p += kEvalThreads) {
+      one[p * so] = 1.0f;
+      one[p * so + 1] = one[p * so + 2] = one[p * so + 3] = 0.0f;
+    }
   }
   // left interface over cores 0 .. k-1; step j writes Ls when k-1-j is even
-  if (k == 0) {
+  // (mode 1 scales it by gout)
+  if (a.mode < 2 && k == 0) {
     for (int p = t; p < cnt; p += kEvalThreads) {
       Ls[p * a.sL] = 1.0f;
       Ls[p * a.sL + 1] = Ls[p * a.sL + 2] = Ls[p * a.sL + 3] = 0.0f;
     }
   }
-  for (int j = 0; j < k; ++j) {
+  for (int j = 0; a.mode < 2 && j < k; ++j) {
     const bool toL = ((k - 1 - j) & 1) == 0;
     float* dst = toL ? Ls : Ts;
     const float* src = j == 0 ? nullptr : (toL ? Ts : Ls);
     chain_step<true>(a.cores[j], a.dims[j], a.ranks[j], a.ranks[j + 1], ixs + j * kChunk, src,
-                     toL ? a.sT : a.sL, dst, toL ? a.sL : a.sT, cnt);
+                     toL ? a.sT : a.sL, dst, toL ? a.sL : a.sT, cnt,
+                     (a.mode == 1 && j == k - 1) ? gs : nullptr);
     __syncthreads();
   }
   // right interface over cores d-1 .. k+1; step s (core d-1-s) writes Rs when nR-1-s is even
-  const int nR = d - 1 - k;
-  if (nR == 0) {
+  const int nR = a.mode < 2 ? d - 1 - k : 0;
+  if (a.mode < 2 && nR == 0) {  // R = [1] (times gout in the backward)
     for (int p = t; p < cnt; p += kEvalThreads) {
-      Rs[p * a.sR] = 1.0f;
+      Rs[p * a.sR] = a.backward ? gs[p] : 1.0f;
       Rs[p * a.sR + 1] = Rs[p * a.sR + 2] = Rs[p * a.sR + 3] = 0.0f;
     }
   }
@@ -400,8 +636,10 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
     const bool toR = ((nR - 1 - s) & 1) == 0;
     float* dst = toR ? Rs : Ts;
     const float* src = s == 0 ? nullptr : (toR ? Ts : Rs);
+    // the backward's last right step folds in gout (mode 1: the left side has it)
     chain_step<false>(a.cores[j], a.dims[j], a.ranks[j], a.ranks[j + 1], ixs + j * kChunk, src,
-                      toR ? a.sT : a.sR, dst, toR ? a.sR : a.sT, cnt);
+                      toR ? a.sT : a.sR, dst, toR ? a.sR : a.sT, cnt,
+                      (a.backward && a.mode == 0 && s == nR - 1) ? gs : nullptr);
     __syncthreads();
   }
   const int rL = a.ranks[k], rR = a.ranks[k + 1], rLp = round4_dev(rL), rRp = round4_dev(rR);
@@ -414,10 +652,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
     for (int s = 0; s < nseg; ++s) {
       const int s0 = segs[s], s1 = segs[s + 1];
       const int i = ixs[k * kChunk + s0];
-      for (int e = t; e < rLp * rRp; e += kEvalThreads) {
-        const int q = e / rRp, b = e % rRp;
-        U[e] = (q < rL && b < rR) ? __ldg(Gk + ((int64_t)q * I + i) * rR + b) : 0.0f;
-      }
+      stage_slice(Gk, I, i, rL, rR, U);
       __syncthreads();
       const int p = t;
       if (p >= s0 && p < s1) {
@@ -425,23 +660,22 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
         const float* rp = Rs + p * a.sR;
         float x = 0.0f;
         for (int bc = 0; bc < rRp; bc += 16) {
-          float u[16];
+          float2 u[8];  // u[b] = sum_q L[q] M[q][bc + b], pairs of b
 #pragma unroll
-          for (int j = 0; j < 16; ++j) u[j] = 0.0f;
+          for (int j = 0; j < 8; ++j) u[j] = make_float2(0.0f, 0.0f);
           for (int q4 = 0; q4 < rLp; q4 += 4) {
             const float4 l = *reinterpret_cast<const float4*>(lp + q4);
             const float lq[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
               const float* mrow = U + (q4 + qq) * rRp + bc;
+              const float2 ll = make_float2(lq[qq], lq[qq]);
 #pragma unroll
               for (int j4 = 0; j4 < 4; ++j4) {
                 if (bc + 4 * j4 < rRp) {
                   const float4 m = *reinterpret_cast<const float4*>(mrow + 4 * j4);
-                  u[4 * j4] = fmaf(lq[qq], m.x, u[4 * j4]);
-                  u[4 * j4 + 1] = fmaf(lq[qq], m.y, u[4 * j4 + 1]);
-                  u[4 * j4 + 2] = fmaf(lq[qq], m.z, u[4 * j4 + 2]);
-                  u[4 * j4 + 3] = fmaf(lq[qq], m.w, u[4 * j4 + 3]);
+                  u[2 * j4] = ffma2(ll, make_float2(m.x, m.y), u[2 * j4]);
+                  u[2 * j4 + 1] = ffma2(ll, make_float2(m.z, m.w), u[2 * j4 + 1]);
                 }
               }
             }
@@ -450,10 +684,10 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
           for (int j4 = 0; j4 < 4; ++j4) {
             if (bc + 4 * j4 < rRp) {
               const float4 r = *reinterpret_cast<const float4*>(rp + bc + 4 * j4);
-              x = fmaf(u[4 * j4], r.x, x);
-              x = fmaf(u[4 * j4 + 1], r.y, x);
-              x = fmaf(u[4 * j4 + 2], r.z, x);
-              x = fmaf(u[4 * j4 + 3], r.w, x);
+              x = fmaf(u[2 * j4].x, r.x, x);
+              x = fmaf(u[2 * j4].y, r.y, x);
+              x = fmaf(u[2 * j4 + 1].x, r.z, x);
+              x = fmaf(u[2 * j4 + 1].y, r.w, x);
             }
           }
         }
@@ -464,12 +698,38 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
     return;
   }
 
-  // backward: R_p <- gout_p R_p (padding stays zero)
-  for (int e = t; e < cnt * rRp; e += kEvalThreads) {
-    const int p = e / rRp, b = e % rRp;
-    Rs[p * a.sR + b] *= gs[p];
+  if (a.mode == 1) {
+    // per run of equal i_2: stage M = G_2[:, i_2, :]; per entry (L = gout a,
+    // R = c): u = M c -> gout u into the scratch rows, w = L^T M -> rows3
+    for (int s = 0; s < nseg; ++s) {
+      const int s0 = segs[s], s1 = segs[s + 1];
+      const int i = ixs[k * kChunk + s0];
+      stage_slice(Gk, I, i, rL, rR, U);
+      __syncthreads();
+      if (t >= s0 && t < s1) {
+        if (rRp <= 4)
+          emit_entry<4>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+        else if (rRp <= 8)
+          emit_entry<8>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+        else if (rRp <= 16)
+          emit_entry<16>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+        else
+          emit_entry<32>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+      }
+      __syncthreads();
+    }
+    // the u rows, coalesced, to their positions in core 1's order
+    {
+      const int W = group_width(rL), lw = __ffs(W) - 1, groups = kEvalThreads >> lw;
+      const int o = t & (W - 1);
+      if (o < rL)
+        for (int p = t >> lw; p < cnt; p += groups)
+          a.rows1[(int64_t)posA[p] * rL + o] = Ts[o * (kChunk + 1) + p];
+    }
+    __syncthreads();
   }
-  __syncthreads();
+
+  // backward (R_p already carries gout_p; mode 1: L_p does):
   // dG_k[:, i, :] += sum_p L_p R_p^T per run, in 4 x 4 tiles: group g of
   // ntiles threads takes entries s0 + g, s0 + g + G, ...; groups fold in order.
   const int tb = rRp / 4, ntiles = (rLp / 4) * tb;
@@ -486,6 +746,7 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
     tb0[u] = own[u] ? (tile % tb) * 4 : 0;
   }
   const uint8_t inf = a.info[c];
+  float* F = a.mode == 1 ? Ts : U;  // mode 1: the scratch rows are written out by now
   for (int s = 0; s < nseg; ++s) {
     const int s0 = segs[s], s1 = segs[s + 1];
     const int i = ixs[k * kChunk + s0];
@@ -501,34 +762,46 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
           if (own[u]) {
             const float4 l = *reinterpret_cast<const float4*>(Ls + p * a.sL + tq0[u]);
             const float4 r = *reinterpret_cast<const float4*>(Rs + p * a.sR + tb0[u]);
-            const float lv[4] = {l.x, l.y, l.z, l.w}, rv[4] = {r.x, r.y, r.z, r.w};
+            const float lv[4] = {l.x, l.y, l.z, l.w};
+            const float2 r01 = make_float2(r.x, r.y), r23 = make_float2(r.z, r.w);
 #pragma unroll
-            for (int qa = 0; qa < 4; ++qa)
-#pragma unroll
-              for (int bb = 0; bb < 4; ++bb)
-                acc[u][qa * 4 + bb] = fmaf(lv[qa], rv[bb], acc[u][qa * 4 + bb]);
+            for (int qa = 0; qa < 4; ++qa) {
+              const float2 ll = make_float2(lv[qa], lv[qa]);
+              float2 a01 = make_float2(acc[u][qa * 4], acc[u][qa * 4 + 1]);
+              float2 a23 = make_float2(acc[u][qa * 4 + 2], acc[u][qa * 4 + 3]);
+              a01 = ffma2(ll, r01, a01);
+              a23 = ffma2(ll, r23, a23);
+              acc[u][qa * 4] = a01.x;
+              acc[u][qa * 4 + 1] = a01.y;
+              acc[u][qa * 4 + 2] = a23.x;
+              acc[u][qa * 4 + 3] = a23.y;
+            }
           }
         }
       }
     }
+    const bool shared = (s == 0 && (inf & 1)) || (s == nseg - 1 && (inf & 2));
+    float* slot = a.slots + (2 * c + (s == 0 ? 0 : 1)) * (int64_t)a.slot_elems;
     if (G > 1) {
+      // fold the G group partials of every tile element in group order, one
+      // element per thread; F[j][group][tile] keeps both sides conflict-free
+      const int GN = G * ntiles;
       if (active) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) U[(grp * ntiles + t % ntiles) * 16 + j] = acc[0][j];
+        for (int j = 0; j < 16; ++j) F[j * GN + t] = acc[0][j];
       }
       __syncthreads();
-      if (active && grp == 0) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          float v = 0.0f;
-          for (int g = 0; g < G; ++g) v += U[(g * ntiles + t) * 16 + j];
-          acc[0][j] = v;
-        }
+      for (int e = t; e < ntiles * 16; e += kEvalThreads) {
+        const int tile = e % ntiles, j = e / ntiles;
+        float v = 0.0f;
+        for (int g = 0; g < G; ++g) v += F[j * GN + g * ntiles + tile];
+        const int q = (tile / tb) * 4 + (j >> 2), b = (tile % tb) * 4 + (j & 3);
+        if (shared)
+          slot[q * rRp + b] = v;
+        else if (q < rL && b < rR)
+          a.grad[((int64_t)q * I + i) * rR + b] += v;
       }
-    }
-    if (active && grp == 0) {
-      const bool shared = (s == 0 && (inf & 1)) || (s == nseg - 1 && (inf & 2));
-      float* slot = a.slots + (2 * c + (s == 0 ? 0 : 1)) * (int64_t)a.slot_elems;
+    } else {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         if (!own[u]) continue;
@@ -537,12 +810,10 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
 #pragma unroll
           for (int bb = 0; bb < 4; ++bb) {
             const int q = tq0[u] + qa, b = tb0[u] + bb;
-            if (shared) {
+            if (shared)
               slot[q * rRp + b] = acc[u][qa * 4 + bb];
-            } else if (q < rL && b < rR) {
-              float* gp = a.grad + ((int64_t)q * I + i) * rR + b;
-              *gp += acc[u][qa * 4 + bb];
-            }
+            else if (q < rL && b < rR)
+              a.grad[((int64_t)q * I + i) * rR + b] += acc[u][qa * 4 + bb];
           }
       }
     }
@@ -554,9 +825,9 @@ __global__ void __launch_bounds__(kEvalThreads) eval_pass_kernel(PassArgs a) {
 // slice's start (its "head") adds the slice's partials in chunk order.
 __global__ void eval_fixup_kernel(PassArgs a) {
   const int64_t c = blockIdx.x;
-  const uint8_t inf = a.info[c];
-  const bool cont_prev = inf & 1, cont_next = inf & 2, single = inf & 4;
-  if (!cont_next || (single && cont_prev)) return;
+  const int64_t cend = a.head_end[c];
+  if (cend < 0) return;
+  const bool single = a.info[c] & 4;
   const int k = a.k, rL = a.ranks[k], rR = a.ranks[k + 1], rRp = round4_dev(rR);
   const int rLp = round4_dev(rL), I = a.dims[k];
   const int64_t last = min(a.n, (c + 1) * kChunk) - 1;
@@ -565,11 +836,8 @@ __global__ void eval_fixup_kernel(PassArgs a) {
     const int q = e / rRp, b = e % rRp;
     if (q >= rL || b >= rR) continue;
     float v = a.slots[(2 * c + (single ? 0 : 1)) * (int64_t)a.slot_elems + e];
-    for (int64_t cc = c + 1; cc < a.nchunks; ++cc) {
-      v += a.slots[2 * cc * (int64_t)a.slot_elems + e];
-      const uint8_t f = a.info[cc];
-      if (!((f & 2) && (f & 4))) break;  // the slice ends in chunk cc
-    }
+#pragma unroll 8
+    for (int64_t cc = c + 1; cc <= cend; ++cc) v += a.slots[2 * cc * (int64_t)a.slot_elems + e];
     a.grad[((int64_t)q * I + i) * rR + b] += v;
   }
 }
@@ -582,8 +850,9 @@ struct Layout {
   int slot_elems = 0;
   int pivot = 0;
   int nb[kEvalMaxD];
-  size_t off_err = 0, off_ix = 0, off_perm = 0, off_info = 0, off_slots = 0, off_tmp = 0,
-         off_hist = 0, total = 0;
+  bool fast3 = false;  // d = 3 with round4(r_2) <= 32: the backward stores per-entry rows
+  size_t off_err = 0, off_ix = 0, off_perm = 0, off_info = 0, off_head = 0, off_slots = 0,
+         off_pos = 0, off_rows1 = 0, off_rows3 = 0, off_tmp = 0, off_hist = 0, total = 0;
 };
 
 bool valid_shape(int d, const int64_t* dims, const int64_t* ranks, int64_t n, const char** why) {
@@ -626,7 +895,14 @@ Layout layout_of(int d, const int64_t* dims, const int64_t* ranks, int64_t n) {
   L.off_ix = take((size_t)d * n * sizeof(int32_t));
   L.off_perm = take((size_t)d * n * sizeof(int32_t));
   L.off_info = take((size_t)d * L.nchunks);
+  L.off_head = take((size_t)d * L.nchunks * sizeof(int32_t));
   L.off_slots = take((size_t)2 * L.nchunks * L.slot_elems * sizeof(float));
+  L.fast3 = d == 3 && round4((int)ranks[2]) <= 32;
+  if (L.fast3) {
+    L.off_pos = take((size_t)2 * n * sizeof(int32_t));
+    L.off_rows1 = take((size_t)n * ranks[1] * sizeof(float));
+    L.off_rows3 = take((size_t)n * ranks[2] * sizeof(float));
+  }
   L.off_tmp = take((size_t)n * sizeof(int32_t));
   L.off_hist = take((size_t)256 * L.ntiles * sizeof(int32_t));
   L.total = o;
@@ -646,13 +922,22 @@ size_t pass_smem(PassArgs& a, const int64_t* ranks) {
   for (int j = a.k + 1; j < a.d; ++j) mR = std::max<int>(mR, (int)ranks[j]);
   a.sL = round4(mL) + 4;
   a.sR = round4(mR) + 4;
-  const bool needT = a.k >= 2 || a.d - 1 - a.k >= 2;
+  // scratch: chains of two or more steps; mode 1 keeps its u rows there
+  const bool needT = a.mode == 1 || (a.mode == 0 && (a.k >= 2 || a.d - 1 - a.k >= 2));
   a.sT = needT ? round4(rmax) + 4 : 0;
-  a.off_L = (a.d + 1) * kChunk;
+  if (a.mode == 1) a.sT = std::max(a.sT, 16);  // also the fold buffer (128 x 16 words)
+  a.off_L = (a.d + 3) * kChunk;  // mode indices, gout and two position lists first
   a.off_R = a.off_L + kChunk * a.sL;
   a.off_T = a.off_R + kChunk * a.sR;
+  const int usz = a.mode == 1 ? round4(rL) * round4(rR)
+                              : std::max(round4(rL) * round4(rR), kEvalThreads * 16);
+  // the staging / fold buffer is only used after the chains: it shares the
+  // scratch buffer when that is large enough
+  if (a.mode != 1 && a.sT > 0 && kChunk * a.sT >= usz) {
+    a.off_U = a.off_T;
+    return (size_t)(a.off_T + kChunk * a.sT) * sizeof(float);
+  }
   a.off_U = a.off_T + kChunk * a.sT;
-  const int usz = std::max(round4(rL) * round4(rR), kEvalThreads * 16);
   return (size_t)(a.off_U + usz) * sizeof(float);
 }
 
@@ -715,8 +1000,15 @@ ttk::PassArgs pass_args(const tt_eval_plan* P, const float* const* cores, int k,
   a.ix = reinterpret_cast<const int32_t*>(P->base + P->L.off_ix);
   a.perm = reinterpret_cast<const int32_t*>(P->base + P->L.off_perm) + (int64_t)k * P->n;
   a.info = reinterpret_cast<const uint8_t*>(P->base + P->L.off_info) + (int64_t)k * P->L.nchunks;
+  a.head_end = reinterpret_cast<const int32_t*>(P->base + P->L.off_head) + (int64_t)k * P->L.nchunks;
   a.slots = reinterpret_cast<float*>(P->base + P->L.off_slots);
   a.slot_elems = P->L.slot_elems;
+  if (P->L.fast3) {
+    a.pos1 = reinterpret_cast<const int32_t*>(P->base + P->L.off_pos);
+    a.pos3 = a.pos1 + P->n;
+    a.rows1 = reinterpret_cast<float*>(P->base + P->L.off_rows1);
+    a.rows3 = reinterpret_cast<float*>(P->base + P->L.off_rows3);
+  }
   return a;
 }
 
@@ -807,8 +1099,17 @@ tt_status tt_eval_plan_create(int32_t d, const int64_t* dims, const int64_t* ran
       }
       ttk::count_launch();
       ttk::chunk_info_kernel<<<(int)std::min<int64_t>((P->L.nchunks + 255) / 256, 4096), 256, 0, st>>>(
-          ix + (int64_t)k * n, pk, n, P->L.nchunks, info + (int64_t)k * P->L.nchunks);
+          ix + (int64_t)k * n, pk, n, P->L.nchunks, info + (int64_t)k * P->L.nchunks,
+          reinterpret_cast<int32_t*>(P->base + P->L.off_head) + (int64_t)k * P->L.nchunks);
       if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && P->L.fast3) {
+      int32_t* pos = reinterpret_cast<int32_t*>(P->base + P->L.off_pos);
+      const int g = (int)std::min<int64_t>((n + 255) / 256, 4096);
+      ttk::count_launch(2);
+      ttk::inverse_perm_kernel<<<g, 256, 0, st>>>(perm, n, pos);
+      ttk::inverse_perm_kernel<<<g, 256, 0, st>>>(perm + 2 * n, n, pos + n);
+      e = cudaGetLastError();
     }
     if (e != cudaSuccess) return bail(plan_cuda_fail(e, "plan build"));
   }
@@ -859,10 +1160,14 @@ tt_status tt_eval_plan_backward(tt_eval_plan* plan, const float* const* cores, c
     if (!cores[k] || !grads[k]) return plan_fail(TT_EINVAL, "NULL core or gradient");
   if (plan->n == 0) return TT_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  for (int k = 0; k < plan->d; ++k) {
+  // d = 3: the middle core's pass first (it writes the outer cores' rows)
+  const int order3[3] = {1, 0, 2};
+  for (int kk = 0; kk < plan->d; ++kk) {
+    const int k = plan->L.fast3 ? order3[kk] : kk;
     ttk::PassArgs a = pass_args(plan, cores, k, 1);
     a.gout = gout;
     a.grad = grads[k];
+    if (plan->L.fast3) a.mode = k == 1 ? 1 : (k == 0 ? 2 : 3);
     const size_t sm = ttk::pass_smem(a, plan->ranks);
     ttk::count_launch(2);
     ttk::eval_pass_kernel<<<(unsigned)plan->L.nchunks, ttk::kEvalThreads, sm, st>>>(a);

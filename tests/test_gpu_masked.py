@@ -1,6 +1,7 @@
 """Masked TT evaluation and its backward (the observation operator P_Omega of
 Sec. 4.2.2 and its core gradients) against the FP64 oracle, on shapes that
-exercise every path of the plan: d = 1 and 2, a mode of more than 256 slices
+exercise every path of the plan: d = 1, 2, 3 (stored per-entry rows for the
+outer cores, and the chained path when r_2 > 32), 4 and 5, a mode of more than 256 slices
 (two radix digits), ranks that are not multiples of 4, a 64 x 64 core (two
 accumulation tiles per thread), one index repeated across every chunk (the
 fix-up chain), all-distinct slices, ragged chunk tails and the empty set.
@@ -61,6 +62,7 @@ CASES = {
     "d2_two_digit_mode": ((300, 9), (1, 5, 1), 3000),
     "rank64": ((6, 5, 4, 3, 7), (1, 6, 64, 64, 7, 1), 2000),
     "ragged_ranks": ((9, 11, 13), (1, 3, 5, 1), 1283),
+    "d3_wide_last_rank": ((5, 6, 7), (1, 8, 40, 1), 1500),   # d = 3 on the chained path
     "distinct_slices": ((1000, 3), (1, 7, 1), 2500),
     "long_modes": ((70000, 2, 3), (1, 4, 2, 1), 5000),
 }
