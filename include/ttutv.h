@@ -239,7 +239,12 @@ tt_status tt_utv_sharded(const void* A_local, int32_t dtype, int32_t d, const in
  * factor is a Jacobi eigen-decomposition of the Gram matrix, so the kept
  * basis is the leading singular subspace and ||E_k||^2 = sum of the dropped
  * sigma_i^2.  direction TT_LR (left-orthogonal, as in the paper) or TT_RL.
- * A step whose two sides both exceed l_full returns TT_EUNSUPPORTED. */
+ * A step whose basis side exceeds l_full takes the sweep's sketch: the
+ * Jacobi SVD is then that of the projection C P_W onto the Rademacher
+ * sketch's range (the identity when the other side is at most 256), the
+ * range miss ||C||^2 - ||C P_W||^2 is part of ||E_k||^2, and the sketch is
+ * widened (up to 256 columns) until the kept rank leaves the oversampling
+ * margin and the tail meets the tolerance; beyond that, TT_EUNSUPPORTED. */
 tt_status tt_svd(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
                  const int64_t* fixed_ranks, int32_t direction, const tt_opts* opts,
                  tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx, void* stream,

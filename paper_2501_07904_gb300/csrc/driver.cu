@@ -446,19 +446,20 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     int64_t no = cfg.urv ? m : n;
     const double dscale = fixed ? 0.0 : (w[u - 1] * eps) * (w[u - 1] * eps);
     const int64_t rfix = fixed ? fixed[u - 1] : -1;
-    // A tolerance within a few hundred FP32 ulps of ||C||^2 (eps_k^2 below
-    // 1e-10 of ||A||^2) keeps directions whose singular values are ~1e-6 of
-    // ||C||: FP32 accumulation (or the tensor cores' drift) would bury them in
-    // the sketch, the range basis, the projection B = C W, the carry and the
-    // core, whose error energy of ~1e-12 of ||C||^2 already exceeds eps_k^2.
-    // Every product of such a step then uses compensated sums of exact
-    // products on the SIMT path.
-    const bool precise = !W64 && !fixed && dscale < 1e-10;
+    // A tolerance within a few FP32 ulps of ||C||^2 (eps_k^2 below 2e-7 of
+    // ||A||^2, about 3.4 u) cannot be resolved from FP32-summed products: the
+    // range miss mu^2 = ||C||^2 - ||C P_W||^2 of a sketched step comes out
+    // with an error of several 1e-9 of ||C||^2 whatever the sketch width, and
+    // at tighter tolerances FP32 accumulation (or the tensor cores' drift)
+    // buries the kept directions themselves in the sketch, the range basis,
+    // the projection, the carry and the core.  Every product of such a step
+    // uses compensated sums of exact products on the SIMT path, and the
+    // projection B = C W is kept in FP64 for its Gram: rounding B to FP32
+    // alone perturbs ||B||^2 by ~u ||C||^2 / sqrt(rows).
+    const bool precise = !W64 && !fixed && dscale < 2e-7;
     const int64_t rcap = std::min<int64_t>(std::min<int64_t>(nb, no_g), ttk::kMaxSmall);
     const bool exact = nb <= l_full;
     const bool first = (s == 0);
-    if (cfg.svd && !exact && no_g > ttk::kMaxSmall)
-      return fail(TT_EUNSUPPORTED, "TT-SVD step with both unfolding sides above 256");
 
     // A tolerance below ~n u_fp32 of ||C||^2 cannot be resolved from an
     // FP32-accumulated Gram or an FP32 factorization: such steps form the
@@ -545,8 +546,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       r = hinfo->r;
       Zp = zb.as<W>();
     } else {
-      l = cfg.svd ? std::min<int64_t>(no_g, ttk::kMaxSmall)
-                  : sketch_size(nb, no_g, r_prev, p_over, rfix);
+      l = sketch_size(nb, no_g, r_prev, p_over, rfix);
       const double* x2_dev = first ? d_x2first : (d_carry2 + (s - 1));
       if (first) {
         TT_RESERVE(scr, ttk::sumsq_ws_bytes(total));
@@ -598,12 +598,14 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
                                       : mm_ws<W>(mm_all, rmax, n, l, false));
           wsz = std::max(wsz, cfg.urv ? mm_ws<W>(mm_all, rmax, n, l, false)
                                       : mm_ws<W>(mm_all, m, rmax, l, false));
+          if (precise) wsz = std::max(wsz, mm_ws<double>(mm, l, l, no, true));
           ws_bytes = wsz;
           const size_t nl = align256((size_t)nb * l * sizeof(W)), ol = align256((size_t)no * l * sizeof(W));
           const size_t ll8 = align256((size_t)l * l * sizeof(double)), llw = align256((size_t)l * l * sizeof(W));
           size_t tot = (identity ? 0 : ol) + nl + align256(wsz) + align256(ttk::small_ws_bytes((int)l, true)) +
                        ll8 + llw + 2 * nl + ol + (whiten_l ? ll8 : 0) + llw;
           if (powered) tot += ol;
+          if (precise) tot += align256((size_t)no * l * sizeof(double));  // B in FP64
           if (active) {
             // a slab's partial sketch is formed in FP64 and summed over ranks
             wsz = std::max(wsz, mm_ws<W>(mm, nb, l, no, true));
@@ -741,17 +743,25 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         const W* Wm = src_pass;
         Wfin = Wm;
         TT_TAKE(bb, (size_t)no * l * sizeof(W));
+        Piece bb64;  // a precise step's projection in FP64, for its Gram
+        if (precise) TT_TAKE(bb64, (size_t)no * l * sizeof(double));
+        double* b64 = precise ? bb64.as<double>() : nullptr;
         acc_gram = !W64 && tight(l);
         tm.begin(s, TT_PH_PROJECT);
         if (cfg.urv)
-          TT_CK(mm_run<W>(mm, {C, n, true}, {Wm, l, true}, m, l, n, bb.as<W>(), l, nullptr, false,
+          TT_CK(mm_run<W>(mm, {C, n, true}, {Wm, l, true}, m, l, n, bb.as<W>(), l, b64, false,
                           nullptr, ws.p, precise, true, true, false), "project C W");
         else
-          TT_CK(mm_run<W>(mm, {C, n, false}, {Wm, l, true}, n, l, m, bb.as<W>(), l, nullptr, false,
+          TT_CK(mm_run<W>(mm, {C, n, false}, {Wm, l, true}, n, l, m, bb.as<W>(), l, b64, false,
                           nullptr, ws.p, precise, true, true, false), "project C^T W");
-        TT_CK(mm_run<W>(mm, {bb.as<W>(), l, false}, {bb.as<W>(), l, true}, l, l, no, nullptr, 0,
-                        gy.as<double>(), true, nullptr, ws.p, acc_gram, true, true, false),
-              "Gram B^T B");
+        if (precise)
+          TT_CK(mm_run<double>(mm, {b64, l, false}, {b64, l, true}, l, l, no, nullptr, 0,
+                               gy.as<double>(), true, nullptr, ws.p, false, false, false, false),
+                "Gram B^T B (FP64)");
+        else
+          TT_CK(mm_run<W>(mm, {bb.as<W>(), l, false}, {bb.as<W>(), l, true}, l, l, no, nullptr, 0,
+                          gy.as<double>(), true, nullptr, ws.p, acc_gram, true, true, false),
+                "Gram B^T B");
         TT_RED(gy.as<double>(), l * l);
         // FP32 W is orthonormal only to ~1e-7, which biases ||X W||^2 and so
         // the range miss mu^2; with a tight tolerance the small factor
@@ -789,7 +799,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         if (debug_trace())
           fprintf(stderr, "[ttutv]   sketch attempt k=%d l=%lld r=%d mu2=%.3e s1=%.3e tail=%.3e delta2=%.3e x2=%.9e trace=%.9e\n",
                   k, (long long)l, hinfo->r, hinfo->mu2, hinfo->s1, hinfo->tail, d2, hinfo->x2, hinfo->trace);
-        if (!fixed && !cfg.svd && (r > l - p_over || hinfo->tail > d2)) {
+        if (!fixed && (r > l - p_over || hinfo->tail > d2)) {
           if (l < lmax) {
             l = std::min<int64_t>(2 * l, lmax);
             continue;

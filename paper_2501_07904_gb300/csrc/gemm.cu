@@ -50,15 +50,18 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(const T* __restrict__ A, 
                                                        int64_t kchunk, bool sym,
                                                        T* __restrict__ out, int64_t ldo,
                                                        double* __restrict__ part,
-                                                       double* __restrict__ sq_part) {
+                                                       double* __restrict__ sq_part, bool swap) {
   constexpr int BM = BMX, BN = BMX, TM = BMX / 16, TN = BMX / 16;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   __shared__ double red[32];
-  // grid.x walks the (possibly huge) row-tile range, grid.y the column tiles
-  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  // grid.x walks the (possibly huge) row-tile range, grid.y the column tiles;
+  // swapped when the column tiles are the ones above grid.y's 65535 limit
+  const unsigned bx = swap ? blockIdx.y : blockIdx.x, by = swap ? blockIdx.x : blockIdx.y;
+  const unsigned gny = swap ? gridDim.x : gridDim.y;
+  const int64_t m0 = (int64_t)bx * BM, n0 = (int64_t)by * BN;
   // Gram: tiles strictly below the diagonal are mirrored, not computed.
-  const bool skip = sym && (blockIdx.y < blockIdx.x);
+  const bool skip = sym && (by < bx);
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int64_t kb = (int64_t)blockIdx.z * kchunk;
   const int64_t ke = min(K, kb + kchunk);
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(const T* __restrict__ A, 
   }
   if (sq_part) {
     sq = block_sum(sq, red);
-    if (threadIdx.x == 0) sq_part[(int64_t)blockIdx.x * gridDim.y + blockIdx.y] = sq;
+    if (threadIdx.x == 0) sq_part[(int64_t)bx * gny + by] = sq;
   }
 }
 
@@ -286,17 +289,17 @@ Plan make_plan(int64_t M, int64_t N, int64_t K, int bt) {
 template <typename T, bool AR, bool BR>
 void launch_tiles(dim3 grid, cudaStream_t st, Mat<T> A, Mat<T> B, int64_t M, int64_t N, int64_t K,
                   int64_t kchunk, bool sym, T* out, int64_t ldo, double* part, double* sqp,
-                  bool accurate) {
+                  bool accurate, bool swap) {
   if constexpr (std::is_same<T, double>::value) {
     gemm_tile_kernel<double, kF64, 64, AR, BR><<<grid, NT, 0, st>>>(A.p, A.ld, B.p, B.ld, M, N, K,
-                                                                   kchunk, sym, out, ldo, part, sqp);
+                                                                   kchunk, sym, out, ldo, part, sqp, swap);
   } else {
     if (accurate)
       gemm_tile_kernel<float, kDF, 32, AR, BR><<<grid, NT, 0, st>>>(A.p, A.ld, B.p, B.ld, M, N, K,
-                                                                   kchunk, sym, out, ldo, part, sqp);
+                                                                   kchunk, sym, out, ldo, part, sqp, swap);
     else
       gemm_tile_kernel<float, kF32, 64, AR, BR><<<grid, NT, 0, st>>>(A.p, A.ld, B.p, B.ld, M, N, K,
-                                                                    kchunk, sym, out, ldo, part, sqp);
+                                                                    kchunk, sym, out, ldo, part, sqp, swap);
   }
 }
 
@@ -341,22 +344,25 @@ cudaError_t gemm(Mat<T> A, Mat<T> B, int64_t M, int64_t N, int64_t K, T* out, in
     if (sumsq) return cudaMemsetAsync(sumsq, 0, sizeof(double), st);
     return cudaSuccess;
   }
-  if (p.gn > 65535) return cudaErrorInvalidConfiguration;
+  // grid.y holds at most 65535 tiles: a very wide product puts its column
+  // tiles on grid.x instead
+  const bool swap = p.gn > 65535;
+  if (swap && p.gm > 65535) return cudaErrorInvalidConfiguration;
   count_launch(1 + (use_part ? 1 : 0) + (sumsq ? 1 : 0));
-  dim3 grid((unsigned)p.gm, (unsigned)p.gn, (unsigned)p.S);
+  dim3 grid(swap ? (unsigned)p.gn : (unsigned)p.gm, swap ? (unsigned)p.gm : (unsigned)p.gn, (unsigned)p.S);
   double* sqp = (!use_part && sumsq) ? sq_part : nullptr;
 if (A.row && B.row)
     launch_tiles<T, true, true>(grid, st, A, B, M, N, K, p.kchunk, sym, out, ldo,
-                                use_part ? part : nullptr, sqp, accurate);
+                                use_part ? part : nullptr, sqp, accurate, swap);
   else if (A.row && !B.row)
     launch_tiles<T, true, false>(grid, st, A, B, M, N, K, p.kchunk, sym, out, ldo,
-                                 use_part ? part : nullptr, sqp, accurate);
+                                 use_part ? part : nullptr, sqp, accurate, swap);
   else if (!A.row && B.row)
     launch_tiles<T, false, true>(grid, st, A, B, M, N, K, p.kchunk, sym, out, ldo,
-                                 use_part ? part : nullptr, sqp, accurate);
+                                 use_part ? part : nullptr, sqp, accurate, swap);
   else
     launch_tiles<T, false, false>(grid, st, A, B, M, N, K, p.kchunk, sym, out, ldo,
-                                  use_part ? part : nullptr, sqp, accurate);
+                                  use_part ? part : nullptr, sqp, accurate, swap);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (use_part) {

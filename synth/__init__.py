@@ -78,6 +78,20 @@ def example2(I=160, d=4, dtype=np.float64):
     return np.sin(np.sqrt(s)).astype(dtype, copy=False)
 
 
+def example2_torch(I=160, d=4, device="cuda", dtype=None):
+    """example2 built on a torch device (FP64 arithmetic, then cast to dtype):
+    the 160^4 tensor is 5.2 GB in FP64, so the GPU tests form it in place."""
+    import torch
+    x2 = (torch.arange(I, dtype=torch.float64, device=device) / (I - 1)) ** 2
+    s = torch.zeros((1,) * d, dtype=torch.float64, device=device)
+    for k in range(d):
+        shape = [1] * d
+        shape[k] = I
+        s = s + x2.reshape(shape)
+    out = torch.sin(torch.sqrt(s))
+    return out if dtype is None else out.to(dtype)
+
+
 def blobs_volume(shape=(256, 256, 64), nblobs=20, seed=0, dtype=np.float32):
     """Sum of axis-aligned anisotropic Gaussian blobs: centres uniform over the
     volume, per-axis widths U[2,30] voxels, amplitudes U[0.2,1]."""

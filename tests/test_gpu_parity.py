@@ -222,10 +222,27 @@ def test_host_input_and_cast(tu):
     assert r64.ranks == dev.ranks and r64.cores[0].dtype == torch.float32
 
 
-def test_svd_unsupported_when_both_sides_large(tu):
-    A = torch.randn((300, 300, 2), device="cuda")
-    with pytest.raises(tu.TTError, match="EUNSUPPORTED"):
-        tu.tt_svd(A, eps=0.5, l_full=16, direction="LR")
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_svd_sketched_when_both_sides_large(tu, precision):
+    # both sides of the first unfolding above l_full: the Jacobi SVD runs on
+    # the projection onto the sketch's range, which holds the tensor's whole
+    # low-rank range here, so ranks match the exact TT-SVD's and the cores
+    # agree to the level of the 1e-7 noise that the two treat differently;
+    # FP32 resolves the range miss (a difference of squared norms) only to
+    # ~1e-8 of ||A||^2, which bounds its tail estimate
+    A = synth.gaussian_tt((300, 300, 2), (1, 5, 2, 1), 1e-7, seed=71, dtype=np.float64)
+    if precision == "fp32":
+        A = A.astype(np.float32)
+    res = tu.tt_svd(torch.from_numpy(A).cuda(), eps=1e-3, l_full=16, direction="LR",
+                    precision=precision)
+    ref = otc.tt_svd(np.asarray(A, np.float64), eps=1e-3, direction="LR")
+    assert res.ranks == ref["ranks"]
+    assert res.sketch_l[0] > 0
+    d = rel_diff_tt([c.double().cpu().numpy() for c in res.cores], ref["cores"], ref["normA2"])
+    assert d <= (1e-6 if precision == "fp64" else 1e-5), d
+    err2 = float(np.sum((otc.tt_full([c.double().cpu().numpy() for c in res.cores]) - A) ** 2))
+    floor = (1e-12 if precision == "fp64" else 1e-7) * ref["normA2"]
+    assert abs(sum(res.tail_sq) - err2) <= 0.1 * err2 + floor
 
 
 @pytest.mark.parametrize("precision, tol", [("fp64", 1e-10), ("fp32", 1e-5)])
