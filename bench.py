@@ -339,9 +339,25 @@ def run_ours(args, wl, rank, world):
         e1.record(st)
         torch.cuda.synchronize()
         ms_e2e = slowest_ms(e0.elapsed_time(e1) / args.steps, world, dev)
+        # the host-to-device copy alone (pinned source, the same bytes)
+        scratch = torch.empty_like(A)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(st)
+        for _ in range(args.steps):
+            scratch.copy_(A_host, non_blocking=True)
+        h1.record(st)
+        torch.cuda.synchronize()
+        ms_h2d = h0.elapsed_time(h1) / args.steps
+        del scratch
         e2e = {"value": round(job_gbs(nbytes, world, ms_e2e), 2), "unit": "GB/s",
                "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": int(nbytes),
-               "d2h_bytes_per_step": int(core_bytes)}
+               "d2h_bytes_per_step": int(core_bytes),
+               "h2d_ms": round(ms_h2d, 4), "h2d_gbs": round(nbytes / (ms_h2d * 1e-3) / 1e9, 1),
+               "sweep_ms": round(ms, 4),
+               "rest_ms": round(ms_e2e - ms_h2d - ms, 4),
+               "breakdown": "e2e = H2D copy (pinned, one cudaMemcpyAsync) + the sweep on the "
+                            "device copy + rest (core copies back, allocation of the device "
+                            "input, host work)"}
 
     # the same sweep in plain FP32 on the same input, for the mixed vs FP32 comparison
     compare = None

@@ -363,6 +363,14 @@ tt_status tt_eval_at_backward(int32_t d, const int64_t* dims, const int64_t* ran
 tt_status tt_sketch_matrix(int64_t rows, int64_t cols, uint64_t seed, int32_t step, int32_t dtype,
                            void* out, void* stream);
 
+/* Diagnostic used by the tests: run the bounded mbarrier wait of the
+ * tensor-core kernels, with the given limit (nanoseconds, at most 1e10), on a
+ * shared-memory barrier of one arrival that one thread completes
+ * (arrive != 0) or that nothing completes.  TT_OK when the wait returns,
+ * TT_ETIMEOUT when it ran out (the kernel then returns normally and the
+ * context stays usable).  Synchronizes `stream`. */
+tt_status tt_wait_selftest(int32_t arrive, int64_t limit_ns, void* stream);
+
 /* Number of kernels this library has launched in the process so far
  * (all threads); a diagnostic for counting launches per call. */
 uint64_t tt_kernel_launches(void);

@@ -41,7 +41,8 @@ EXPORTS = ["tt_opts_default", "tt_utv", "tt_utv_sharded", "tt_svd", "tt_result_f
            "tt_full", "tt_full_noalloc", "tt_full_noalloc_max_work_bytes", "tt_rse_work_bytes",
            "tt_rse", "tt_eval_plan_create", "tt_eval_plan_destroy", "tt_eval_plan_device_bytes",
            "tt_eval_plan_at", "tt_eval_plan_backward", "tt_eval_at",
-           "tt_eval_at_backward", "tt_sketch_matrix", "tt_kernel_launches", "tt_last_error",
+           "tt_eval_at_backward", "tt_sketch_matrix", "tt_wait_selftest", "tt_kernel_launches",
+           "tt_last_error",
            "tt_version"]
 PHASES = ["gram", "small", "carry", "core", "sketch", "orth", "project"]
 TT_NPHASES = 8
@@ -142,6 +143,8 @@ def lib():
     L.tt_eval_at_backward.restype = I32
     L.tt_sketch_matrix.argtypes = [I64, I64, U64, I32, I32, P, P]
     L.tt_sketch_matrix.restype = I32
+    L.tt_wait_selftest.argtypes = [I32, I64, P]
+    L.tt_wait_selftest.restype = I32
     L.tt_kernel_launches.argtypes = []
     L.tt_kernel_launches.restype = ctypes.c_uint64
     L.tt_last_error.argtypes = []
@@ -675,6 +678,13 @@ def sketch_matrix(rows, cols, seed=0, step=0, dtype=torch.float32, device="cuda"
     _check(lib().tt_sketch_matrix(rows, cols, seed, step, code, ctypes.c_void_p(out.data_ptr()),
                                   st_ptr))
     return out
+
+
+def wait_selftest(arrive, limit_ns=50_000_000, stream=None):
+    """Run the tensor-core kernels' bounded wait on a barrier that is (arrive)
+    or is not completed; raises TTError(TT_ETIMEOUT) when the wait runs out."""
+    st, st_ptr = _stream(stream)
+    _check(lib().tt_wait_selftest(1 if arrive else 0, int(limit_ns), st_ptr))
 
 
 def version():

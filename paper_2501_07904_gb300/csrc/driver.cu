@@ -1317,6 +1317,23 @@ tt_status tt_sketch_matrix(int64_t rows, int64_t cols, uint64_t seed, int32_t st
   return TT_OK;
 }
 
+tt_status tt_wait_selftest(int32_t arrive, int64_t limit_ns, void* stream) {
+  g_err.clear();
+  if (limit_ns <= 0 || limit_ns > 10000000000ll) return fail(TT_EINVAL, "limit_ns in (0, 1e10]");
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d_err = nullptr;
+  TT_CK(cudaMallocAsync((void**)&d_err, sizeof(int), st), "selftest word");
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = ttk::wait_selftest(arrive != 0, (uint64_t)limit_ns, d_err, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(d_err, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "tt_wait_selftest");
+  if (h) return fail(TT_ETIMEOUT, "the bounded wait ran out");
+  return TT_OK;
+}
+
 uint64_t tt_kernel_launches(void) { return ttk::launches(); }
 
 const char* tt_last_error(void) { return g_err.c_str(); }

@@ -67,6 +67,11 @@ cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K,
                     int64_t ldo, double* out64, bool sym, double* sumsq, void* ws, cudaStream_t st,
                     TcOpts o);
 
+// Diagnostic: the tensor-core kernels' bounded mbarrier wait on a barrier
+// that is (arrive) or is not completed; err (device int) is set to 1 when the
+// wait runs out after limit_ns.
+cudaError_t wait_selftest(bool arrive, uint64_t limit_ns, int* err, cudaStream_t st);
+
 // Small single-CTA factorizations of an n x n FP64 Gram matrix (n <= 256).
 enum SmallMode { SM_QLP = 0, SM_JACOBI = 1, SM_ORTH = 2 };
 struct SmallParams {

@@ -975,4 +975,27 @@ cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K,
   return cudaSuccess;
 }
 
+
+namespace {
+// The bounded wait of the tensor-core kernels on an mbarrier of one arrival,
+// which lane 0 completes (arrive) or nothing does; the wait then runs out
+// after limit_ns and sets the error word.
+__global__ void wait_selftest_kernel(int arrive, uint64_t limit_ns, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) mbar_arrive(&bar);
+  mbar_wait(&bar, 0, err, limit_ns);
+}
+}  // namespace
+
+cudaError_t wait_selftest(bool arrive, uint64_t limit_ns, int* err, cudaStream_t st) {
+  count_launch();
+  wait_selftest_kernel<<<1, 32, 0, st>>>(arrive ? 1 : 0, limit_ns, err);
+  return cudaGetLastError();
+}
+
 }  // namespace ttk

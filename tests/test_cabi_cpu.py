@@ -248,3 +248,9 @@ def test_eval_plan_arguments_rejected(L):
     assert L.tt_eval_plan_backward(None, ptrs, ctypes.c_void_p(1), ptrs, None) == 1
     L.tt_eval_plan_destroy(None, None)
     assert L.tt_eval_plan_device_bytes(None) == 0
+
+
+def test_wait_selftest_arguments_rejected(L):
+    assert L.tt_wait_selftest(0, 0, None) == 1
+    assert L.tt_wait_selftest(1, -5, None) == 1
+    assert L.tt_wait_selftest(0, 20_000_000_000, None) == 1

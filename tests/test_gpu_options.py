@@ -68,3 +68,17 @@ def test_double_float_small_factors_c3(tu, method):
     assert res.ranks == [1, 20, 20, 20, 20, 1]
     assert all(res.small_fp64)
     check_tight_tails(tu, A, res, method, "c3")
+
+
+def test_bounded_wait_runs_out_and_the_context_survives(tu):
+    """The tensor-core kernels' bounded mbarrier wait, on a barrier that is
+    completed and on one that nothing completes (a 50 ms limit instead of
+    the kernels' 2 s): TT_OK, then TT_ETIMEOUT, and the GPU keeps working."""
+    tu.wait_selftest(True, 50_000_000)
+    with pytest.raises(tu.TTError) as ei:
+        tu.wait_selftest(False, 50_000_000)
+    assert ei.value.status == tu.TT_ETIMEOUT
+    A = torch.from_numpy(synth.gaussian_tt((8, 9, 10), (1, 3, 4, 1), 1e-6, seed=81,
+                                           dtype=np.float32)).cuda()
+    res = tu.tt_utv(A, eps=1e-3, precision="mixed")
+    assert res.ranks == [1, 3, 4, 1]
