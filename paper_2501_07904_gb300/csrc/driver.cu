@@ -18,6 +18,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <chrono>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -44,12 +46,26 @@ tt_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
+// Host-time accounting of a sweep (printed with TTUTV_DEBUG=2): wall time,
+// time blocked in the per-step synchronizations, time inside the caller's
+// allocator, and the number of allocator calls.
+double host_us() {
+  return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+struct HostProf {
+  double alloc_us = 0.0, sync_us = 0.0;
+  int nalloc = 0;
+};
+thread_local HostProf g_hprof;
+
 struct Alloc {
   tt_alloc_fn al;
   tt_free_fn fr;
   void* ctx;
   cudaStream_t st;
   void* get(size_t bytes) {
+    const double t0 = host_us();
     bytes = ((bytes ? bytes : 1) + 255) & ~(size_t)255;
     void* p = nullptr;
     if (al) {
@@ -58,14 +74,19 @@ struct Alloc {
       cudaGetLastError();
       p = nullptr;
     }
+    g_hprof.alloc_us += host_us() - t0;
+    ++g_hprof.nalloc;
     return p;
   }
   void put(void* p) {
     if (!p) return;
+    const double t0 = host_us();
     if (fr)
       fr(p, (void*)st, ctx);
     else
       cudaFreeAsync(p, st);
+    g_hprof.alloc_us += host_us() - t0;
+    ++g_hprof.nalloc;
   }
 };
 
@@ -182,6 +203,14 @@ int* pinned_err() {
 int64_t roundup(int64_t x, int64_t m) { return ((x + m - 1) / m) * m; }
 
 // TTUTV_DEBUG=1 prints one line per sweep step to stderr.
+bool host_prof() {
+  static const bool on = [] {
+    const char* v = getenv("TTUTV_DEBUG");
+    return v && v[0] == '2';
+  }();
+  return on;
+}
+
 bool debug_trace() {
   static const bool on = [] {
     const char* v = getenv("TTUTV_DEBUG");
@@ -538,7 +567,11 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       tm.end();
       TT_CK(cudaMemcpyAsync(hinfo, dinfo.p, sizeof(ttk::StepInfo), cudaMemcpyDeviceToHost, st), "info");
       TT_CK(cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error word");
-      TT_CK(cudaStreamSynchronize(st), "step sync");
+      {
+        const double t0 = host_us();
+        TT_CK(cudaStreamSynchronize(st), "step sync");
+        g_hprof.sync_us += host_us() - t0;
+      }
       tm.collect();
       if (*herr) return fail(TT_ETIMEOUT, "a bounded wait in a tensor-core kernel ran out");
       if (hinfo->status & 1) return fail(TT_ENONFINITE, "input holds NaN or Inf");
@@ -788,7 +821,11 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         tm.end();
         TT_CK(cudaMemcpyAsync(hinfo, dinfo.p, sizeof(ttk::StepInfo), cudaMemcpyDeviceToHost, st), "info");
         TT_CK(cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error word");
-        TT_CK(cudaStreamSynchronize(st), "step sync");
+        {
+          const double t0 = host_us();
+          TT_CK(cudaStreamSynchronize(st), "step sync");
+          g_hprof.sync_us += host_us() - t0;
+        }
         tm.collect();
         if (*herr) return fail(TT_ETIMEOUT, "a bounded wait in a tensor-core kernel ran out");
         if (hinfo->status & 1) return fail(TT_ENONFINITE, "input holds NaN or Inf");
@@ -938,7 +975,11 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   double h_carry2[TT_MAXD];
   TT_CK(cudaMemcpyAsync(h_carry2, d_carry2, sizeof(double) * (d - 1), cudaMemcpyDeviceToHost, st), "tails");
   TT_CK(cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error word");
-  TT_CK(cudaStreamSynchronize(st), "final sync");
+  {
+    const double t0 = host_us();
+    TT_CK(cudaStreamSynchronize(st), "final sync");
+    g_hprof.sync_us += host_us() - t0;
+  }
   tm.collect();
   if (*herr) return fail(TT_ETIMEOUT, "a bounded wait in a tensor-core kernel ran out");
   for (int s = 0; s < d - 1; ++s) {
@@ -1092,10 +1133,21 @@ tt_status sweep_entry(const void* A, int32_t dtype, int32_t d, const int64_t* di
     if (cfg.svd) return fail(TT_EUNSUPPORTED, "shard: TT-SVD is not partitioned");
   }
   Alloc al{alloc, free_fn, ctx, (cudaStream_t)stream};
-  if (o.reverse) return run_reversed(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
-  if (o.precision == TT_P_FP64)
-    return run_sweep<double>(A, dtype, d, dims, eps, fixed, cfg, o, al, out, sh);
-  return run_sweep<float>(A, dtype, d, dims, eps, fixed, cfg, o, al, out, sh);
+  g_hprof = HostProf();
+  const double t0 = host_us();
+  const uint64_t l0 = ttk::launches();
+  tt_status st;
+  if (o.reverse)
+    st = run_reversed(A, dtype, d, dims, eps, fixed, cfg, o, al, out);
+  else if (o.precision == TT_P_FP64)
+    st = run_sweep<double>(A, dtype, d, dims, eps, fixed, cfg, o, al, out, sh);
+  else
+    st = run_sweep<float>(A, dtype, d, dims, eps, fixed, cfg, o, al, out, sh);
+  if (host_prof())
+    fprintf(stderr, "[ttutv] host: wall %.1f us, blocked in syncs %.1f us, allocator %.1f us (%d calls), %llu launches\n",
+            host_us() - t0, g_hprof.sync_us, g_hprof.alloc_us, g_hprof.nalloc,
+            (unsigned long long)(ttk::launches() - l0));
+  return st;
 }
 
 }  // namespace
