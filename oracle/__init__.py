@@ -16,6 +16,9 @@ tt      TT format (Eq. TT), TT-ULV (Alg. 1/2), TT-URV (Alg. 3 and its
         prescribed-accuracy analogue), TT-ULV right-to-left (the appendix's
         Alg. 4, both middle blocks), TT-SVD, the range step with optional
         power iterations, masked evaluation and gradients.
+rgrad   Riemannian gradient completion (Sec. 4.2.2): tangent-space
+        projection at a fixed-rank TT, the exact line-search step, the
+        fixed-rank TT-UTV / TT-SVD retraction and spectral initialisation.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, LAPACK, brute force or the paper's Table (tab: Beps);
@@ -23,4 +26,4 @@ against closed forms, LAPACK, brute force or the paper's Table (tab: Beps);
 Philox4x32-10 engine (ATen/core/PhiloxRNGEngine.h, compiled on the host by
 ``tests/test_oracle_philox_pin.py``) and by statistical properties.
 """
-from . import linalg, philox, tt  # noqa: F401
+from . import linalg, philox, rgrad, tt  # noqa: F401
