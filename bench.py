@@ -56,6 +56,11 @@ WORKLOADS = {
                desc="masked TT evaluation + core gradients of the completion workload: "
                     "256x256x64 f32 volume of 20 Gaussian blobs, Bernoulli(0.3) observation "
                     "set (1.26M entries), TT ranks (1,32,16,1) from the TT-URV initialisation"),
+    "c4-rgrad": dict(kind="rgrad", ranks=(1, 32, 16, 1),
+                     desc="Riemannian gradient completion (Sec. 4.2.2) of the 256x256x64 f32 "
+                          "blob volume from its Bernoulli(0.3) observation set, TT ranks "
+                          "(1,32,16,1): tangent projection, exact line-search step, fixed-rank "
+                          "TT-URV retraction of the full 4.2M-entry iterate"),
     "c5-half": dict(dims=(64, 128, 128, 128), ranks=(1, 64, 64, 64, 1), rel_noise=1e-3, seed=0,
                     eps=1e-2, variant="URV",
                     desc="64x128^3 f32 (512 MiB) slab of the 128^4 workload's generator, for "
@@ -743,6 +748,183 @@ def run_reference_c4(args, wl, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+RGRAD_METRIC = "RGrad completion iterations/s"
+
+
+def rgrad_problem():
+    cfg = synth.CONFIGS["c4"]
+    shape = cfg["shape"]
+    M = synth.make_config("c4")
+    idx = synth.observation_mask(shape, cfg["p_obs"], cfg["mask_seed"])
+    return cfg, shape, M, idx, np.ascontiguousarray(M.reshape(-1)[idx])
+
+
+def run_rgrad(args, wl, rank, world):
+    """RGrad iterations of the completion workload.  Timed: args.steps
+    iterations with the TT-URV retraction after args.warmup untimed ones, in
+    one call (the iterate, its frames and the plans stay resident).  Also
+    reported: the RSE / PSNR curves of the three retractions (the paper's
+    comparison, Sec. 4.2.2) and their time per iteration."""
+    import torch
+
+    import paper_2501_07904_gb300 as tu
+    from paper_2501_07904_gb300.completion import rgrad
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg, shape, M, idx, vals = rgrad_problem()
+    ranks = list(cfg["ranks"][1:-1])
+    i_t = torch.from_numpy(idx).to(dev)
+    v_t = torch.from_numpy(vals).to(dev)
+    truth = torch.from_numpy(M).to(dev).double()
+    held = torch.ones(M.size, dtype=torch.bool, device=dev)
+    held[i_t] = False
+    st = torch.cuda.current_stream()
+    W, K = args.warmup, args.steps
+
+    def run(method, keep):
+        marks, iters = {}, []
+
+        def cb(t, cores):
+            if t in (W, W + K):
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(st)
+                marks[t] = (e, tu.kernel_launches())
+            if keep:
+                iters.append([c.clone() for c in cores])
+        torch.cuda.synchronize()
+        cores, losses, alphas = rgrad(v_t, i_t, shape, ranks, steps=W + K, retraction=method,
+                                      callback=cb)
+        torch.cuda.synchronize()
+        ms = marks[W][0].elapsed_time(marks[W + K][0]) / K
+        return cores, losses, alphas, ms, marks[W + K][1] - marks[W][1], iters
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    barrier()
+    with ClockSampler(dev.index, not args.no_clocks) as clk:
+        cores, losses, alphas, ms, launches, _ = run("URV", False)
+    ms = slowest_ms(ms, world, dev)
+    value = world * 1e3 / ms
+
+    def metrics(cs):
+        x = tu.tt_full(cs).double().reshape(-1)
+        t = truth.reshape(-1)
+        rse = float(torch.linalg.vector_norm(x - t) / torch.linalg.vector_norm(t))
+        rse_u = float(torch.linalg.vector_norm((x - t)[held]) / torch.linalg.vector_norm(t[held]))
+        psnr = 10.0 * np.log10(float(t.abs().max()) ** 2 / float(((x - t) ** 2).mean()))
+        return round(rse, 5), round(rse_u, 5), round(psnr, 2)
+
+    curves = {}
+    show = sorted({0, 1, 2, 5, 10, 20, 40, W + K} & set(range(W + K + 1)))
+    for method in ("URV", "ULV", "SVD"):
+        _, ls, al, ms_m, _, iters = run(method, True)
+        m = [metrics(c) for c in iters]
+        curves[method] = {"ms_per_iter": round(ms_m, 3),
+                          "iters": show,
+                          "rse": [m[t][0] for t in show],
+                          "rse_unobserved": [m[t][1] for t in show],
+                          "psnr_db": [m[t][2] for t in show],
+                          "loss": [float(f"{ls[t]:.5g}") for t in show]}
+
+    e2e = None
+    if not args.no_e2e:
+        h_vals = torch.from_numpy(vals).pin_memory()
+        h_idx = torch.from_numpy(idx).pin_memory()
+        h_out = None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        dv, di = h_vals.to(dev, non_blocking=True), h_idx.to(dev, non_blocking=True)
+        out, _, _ = rgrad(dv, di, shape, ranks, steps=K, retraction="URV")
+        h_out = [c.to("cpu", non_blocking=True) for c in out]
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_e = slowest_ms(e0.elapsed_time(e1) / K, world, dev)
+        e2e = {"value": round(world * 1e3 / ms_e, 3), "unit": "iterations/s",
+               "ms_per_step": round(ms_e, 3),
+               "h2d_bytes_per_step": int((h_vals.numel() * 4 + h_idx.numel() * 8) / K),
+               "d2h_bytes_per_step": int(sum(c.numel() * 4 for c in h_out) / K),
+               "step": f"one rgrad() call of {K} iterations from host values and indices "
+                       f"(plan builds and the spectral initialisation included), cores back to "
+                       f"the host; per iteration"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = rgrad_cpu_baseline(shape, idx, vals, ranks)
+
+    return {
+        "metric": RGRAD_METRIC, "value": round(value, 3), "unit": "iterations/s", "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"c4-rgrad: {wl['desc']}", "entries": len(idx), "ranks": ranks,
+                   "l2": "inputs larger than L2 (the 4.2M-entry full iterate and its sweeps, "
+                         "the 1.26M-entry plans)",
+                   "parallelism": f"replicas x{world} (independent problems)"},
+        "roofline": None, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "accuracy": {"loss_first_last": [losses[0], losses[-1]], "alphas_positive": all(a > 0 for a in alphas)},
+        "curves": curves,
+    }
+
+
+def rgrad_iteration_oracle(shape, idx, vals, cores, ranks):
+    """One oracle RGrad iteration from the given cores (FP64, host)."""
+    from oracle import rgrad as org  # the FP64 oracle: only the baseline legs run it
+    from oracle import tt as otc
+
+    ntot = int(np.prod(shape))
+    full = otc.tt_full(cores).reshape(-1)
+    z = full[idx] - vals
+    U, V = org.left_orthogonal(cores), org.right_orthogonal(cores)
+    G = np.zeros(ntot)
+    G[idx] = z
+    dU = org.tangent_project(U, V, G.reshape(shape))
+    xi = otc.tt_full(org.tangent_cores(U, V, dU)).reshape(-1)
+    alpha = org.step_size(xi[idx], z)
+    return org.retract((full - alpha * xi).reshape(shape), [1, *ranks, 1], "URV")
+
+
+def rgrad_cpu_baseline(shape, idx, vals, ranks):
+    cores = synth.gaussian_cores(shape, [1, *ranks, 1], seed=0)
+    v64 = vals.astype(np.float64)
+    t0 = time.perf_counter()
+    rgrad_iteration_oracle(shape, idx, v64, cores, ranks)
+    dt = time.perf_counter() - t0
+    return {"value": round(1.0 / dt, 5), "unit": "iterations/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"one full RGrad iteration of the oracle (FP64, dense tangent projection, "
+                      f"oracle TT-URV retraction) on the workload; {dt:.1f} s"}
+
+
+def run_reference_rgrad(args, wl, rank, world):
+    if rank != 0:
+        return None
+    cfg, shape, M, idx, vals = rgrad_problem()
+    ranks = list(cfg["ranks"][1:-1])
+    cores = synth.gaussian_cores(shape, [1, *ranks, 1], seed=0)
+    v64 = vals.astype(np.float64)
+    steps = max(1, min(args.steps, 3))           # a bounded sample: a few iterations
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        cores = rgrad_iteration_oracle(shape, idx, v64, cores, ranks)
+    dt = (time.perf_counter() - t0) / steps
+    value = 1.0 / dt
+    sample = f"{steps} oracle RGrad iterations (FP64, host) of the workload"
+    return {"impl": "reference", "metric": RGRAD_METRIC, "value": round(value, 5),
+            "unit": "iterations/s", "n_gpus": world, "steps": steps, "warmup": 0,
+            "ms_per_step": round(dt * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"c4-rgrad: {wl['desc']}", "precision": "fp64 oracle",
+                       "l2": "n/a (CPU)", "parallelism": "1 process, host cores"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "iterations/s",
+                             "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
@@ -752,11 +934,12 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         torch.distributed.init_process_group("nccl")
-    masked = wl.get("kind") == "masked"
+    kind = wl.get("kind", "sweep")
     if args.impl == "reference":
-        out = (run_reference_c4 if masked else run_reference)(args, wl, rank, world)
+        fn = {"masked": run_reference_c4, "rgrad": run_reference_rgrad}.get(kind, run_reference)
     else:
-        out = (run_c4 if masked else run_ours)(args, wl, rank, world)
+        fn = {"masked": run_c4, "rgrad": run_rgrad}.get(kind, run_ours)
+    out = fn(args, wl, rank, world)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if world > 1 and args.impl == "ours":

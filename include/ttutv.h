@@ -346,6 +346,35 @@ tt_status tt_eval_plan_at(const tt_eval_plan* plan, const float* const* cores, f
  * buffers; zero them first for a plain gradient).  Asynchronous; 2 d launches. */
 tt_status tt_eval_plan_backward(tt_eval_plan* plan, const float* const* cores, const float* gout,
                                 float* const* grads, void* stream);
+/* The same gradients with the interfaces taken from two sets of cores:
+ *   grads_k[:, i, :] += sum_{e: i_k(e) = i} gout_e (L_1[i_1] .. L_{k-1}[i_{k-1}])^T
+ *                                                (R_{k+1}[i_{k+1}] .. R_d[i_d])^T
+ * with L = left and R = right (host arrays of d device pointers, shaped like
+ * the plan's cores).  left = right is tt_eval_plan_backward.  With left the
+ * left-orthogonal and right the right-orthogonal cores of one TT tensor X,
+ * grads_k is U_{<k}^T Z_(k) V_{>k}^T for the zero-filled tensor Z of gout on
+ * the index set: the first part of the tangent-space projection of the
+ * Riemannian gradient (Sec. 4.2.2).  Asynchronous; 2 d launches. */
+tt_status tt_eval_plan_backward_mixed(tt_eval_plan* plan, const float* const* left,
+                                      const float* const* right, const float* gout,
+                                      float* const* grads, void* stream);
+/* Projection of P_Omega Z onto the tangent space at X of the manifold of TT
+ * tensors of the plan's ranks (the Riemannian gradient of Sec. 4.2.2 when z
+ * is the residual X - M on the index set).  U: the left-orthogonal cores of X
+ * (U_1 .. U_{d-1} with orthonormal left unfoldings [r_{k-1} I_k] x [r_k], U_d
+ * carrying the norm); V: the right-orthogonal cores of the same X (V_2 .. V_d
+ * with orthonormal right unfoldings).  z: device float[n], the values of Z on
+ * the plan's indices.  dU (host array of d device pointers shaped like the
+ * cores, distinct buffers) is OVERWRITTEN with
+ *   Y_k  = tt_eval_plan_backward_mixed(U, V, z)_k,
+ *   dU_k = Y_k - U_k (U_k^T Y_k)   (left unfoldings, k < d; FP64 sums),
+ *   dU_d = Y_d,
+ * so that P_T(P_Omega Z) = sum_k U_1 .. U_{k-1} dU_k V_{k+1} .. V_d with the
+ * gauge U_k^T dU_k = 0.  The result is only meaningful when U and V are
+ * orthogonal frames of one tensor; that is not checked.  Asynchronous;
+ * d memsets and 2 d + 3 (d - 1) launches. */
+tt_status tt_tangent_project(tt_eval_plan* plan, const float* const* U, const float* const* V,
+                             const float* z, float* const* dU, void* stream);
 
 /* One-shot forms: build a plan (cudaMallocAsync), run, destroy.  Each
  * synchronizes `stream` once (the index check); TT_EINVAL for an index

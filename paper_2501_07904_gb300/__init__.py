@@ -40,7 +40,8 @@ EXPORTS = ["tt_opts_default", "tt_utv", "tt_utv_sharded", "tt_svd", "tt_result_f
            "tt_full_work_bytes",
            "tt_full", "tt_full_noalloc", "tt_full_noalloc_max_work_bytes", "tt_rse_work_bytes",
            "tt_rse", "tt_eval_plan_create", "tt_eval_plan_destroy", "tt_eval_plan_device_bytes",
-           "tt_eval_plan_at", "tt_eval_plan_backward", "tt_eval_at",
+           "tt_eval_plan_at", "tt_eval_plan_backward", "tt_eval_plan_backward_mixed",
+           "tt_tangent_project", "tt_eval_at",
            "tt_eval_at_backward", "tt_sketch_matrix", "tt_wait_selftest", "tt_kernel_launches",
            "tt_last_error",
            "tt_version"]
@@ -136,6 +137,11 @@ def lib():
     L.tt_eval_plan_at.restype = I32
     L.tt_eval_plan_backward.argtypes = [P, ctypes.POINTER(P), P, ctypes.POINTER(P), P]
     L.tt_eval_plan_backward.restype = I32
+    L.tt_eval_plan_backward_mixed.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), P,
+                                              ctypes.POINTER(P), P]
+    L.tt_eval_plan_backward_mixed.restype = I32
+    L.tt_tangent_project.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.POINTER(P), P]
+    L.tt_tangent_project.restype = I32
     L.tt_eval_at.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P, P]
     L.tt_eval_at.restype = I32
     L.tt_eval_at_backward.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P,
@@ -568,30 +574,63 @@ class EvalPlan:
             _check(lib().tt_eval_plan_at(self._h, ptrs, ctypes.c_void_p(out.data_ptr()), st_ptr))
         return out.view(self.shape)
 
-    def backward(self, cores, gout, stream=None, out=None):
-        """Core gradients of sum_e gout_e x_e; accumulated into ``out`` (a list
-        of tensors shaped like the cores) if given, else into fresh zeros.
-        Bitwise reproducible for this plan."""
-        cores_c = self._cores(cores)
+    def _gout(self, gout):
         if not isinstance(gout, torch.Tensor) or gout.dtype != torch.float32 or not gout.is_cuda \
                 or gout.device != self.device or gout.numel() != self.n:
             raise TypeError("gout must be a float32 CUDA tensor with one value per index")
-        gout_c = gout.reshape(-1).contiguous()
+        return gout.reshape(-1).contiguous()
+
+    def _out(self, out, like):
+        if out is None:
+            return [torch.zeros_like(g) for g in like]
+        _check_cores(out, self.dims, self.ranks)
+        if any(not g.is_contiguous() or g.dtype != torch.float32 or g.device != self.device
+               for g in out):
+            raise TypeError("out must hold contiguous float32 tensors on the plan's device")
+        return list(out)
+
+    @staticmethod
+    def _ptrs(ts):
+        return (ctypes.c_void_p * len(ts))(*[g.data_ptr() for g in ts])
+
+    def backward(self, cores, gout, stream=None, out=None, right=None):
+        """Core gradients of sum_e gout_e x_e; accumulated into ``out`` (a list
+        of tensors shaped like the cores) if given, else into fresh zeros.
+        With ``right``, the interfaces right of each core come from those
+        cores and the ones left of it from ``cores``.  Bitwise reproducible
+        for this plan."""
+        cores_c = self._cores(cores)
+        right_c = cores_c if right is None else self._cores(right)
+        gout_c = self._gout(gout)
         st, st_ptr = _stream(stream)
         with torch.cuda.device(self.device), torch.cuda.stream(st):
-            if out is None:
-                grads = [torch.zeros_like(g) for g in cores_c]
+            grads = self._out(out, cores_c)
+            if right is None:
+                _check(lib().tt_eval_plan_backward(self._h, self._ptrs(cores_c),
+                                                   ctypes.c_void_p(gout_c.data_ptr()),
+                                                   self._ptrs(grads), st_ptr))
             else:
-                _check_cores(out, self.dims, self.ranks)
-                if any(not g.is_contiguous() or g.dtype != torch.float32 or g.device != self.device
-                       for g in out):
-                    raise TypeError("out must hold contiguous float32 tensors on the plan's device")
-                grads = list(out)
-            ptrs = (ctypes.c_void_p * len(cores_c))(*[g.data_ptr() for g in cores_c])
-            gptrs = (ctypes.c_void_p * len(grads))(*[g.data_ptr() for g in grads])
-            _check(lib().tt_eval_plan_backward(self._h, ptrs, ctypes.c_void_p(gout_c.data_ptr()),
-                                               gptrs, st_ptr))
+                _check(lib().tt_eval_plan_backward_mixed(self._h, self._ptrs(cores_c),
+                                                         self._ptrs(right_c),
+                                                         ctypes.c_void_p(gout_c.data_ptr()),
+                                                         self._ptrs(grads), st_ptr))
         return grads
+
+    def tangent_project(self, U, V, z, stream=None, out=None):
+        """Increments dU_1..dU_d of the projection of P_Omega Z (z: its values
+        on the plan's indices) onto the tangent space at the TT tensor whose
+        left-orthogonal cores are U and right-orthogonal cores are V (see
+        tt_tangent_project).  ``out`` (tensors shaped like the cores) is
+        overwritten if given."""
+        U_c, V_c = self._cores(U), self._cores(V)
+        z_c = self._gout(z)
+        st, st_ptr = _stream(stream)
+        with torch.cuda.device(self.device), torch.cuda.stream(st):
+            dU = [torch.empty_like(g) for g in U_c] if out is None else self._out(out, U_c)
+            _check(lib().tt_tangent_project(self._h, self._ptrs(U_c), self._ptrs(V_c),
+                                            ctypes.c_void_p(z_c.data_ptr()), self._ptrs(dU),
+                                            st_ptr))
+        return dU
 
     def close(self, stream=None):
         if getattr(self, "_h", None) is not None:

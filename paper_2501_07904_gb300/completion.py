@@ -9,9 +9,19 @@ gradients come from the library's masked evaluation and its backward
 (interfaces recomputed per entry, one plan of the observation set reused
 by every call), and each step length is found by Armijo
 backtracking starting from twice the previous one, so the loss never
-increases.  The paper's own solver (Riemannian gradient with a TT retraction)
-is not reproduced; only its observation operator P_Omega and the TT-UTV
-initialisation are.
+increases (complete()).
+
+rgrad() is the paper's own solver: Riemannian gradient descent on the
+manifold of TT tensors of fixed ranks.  Each iteration projects the residual
+P_Omega(X_k - M) onto the tangent space at X_k (tt_tangent_project: one
+two-frame masked backward and an FP64 gauge), evaluates that Riemannian
+gradient xi on the observed entries through the rank-2r block TT of the
+tangent vector, takes the exact line-search step
+alpha_k = <P_Omega xi, P_Omega(X_k - M)> / <P_Omega xi, P_Omega xi>,
+forms X_k - alpha_k xi in full (a rank-2r block TT contracted by tt_full) and
+retracts it with a fixed-rank TT-URV, TT-ULV or TT-SVD sweep of the library.
+The other orthogonal frame of the new point comes from the opposite sweep of
+its full tensor (exact at its own ranks).
 """
 from __future__ import annotations
 
@@ -19,7 +29,7 @@ import math
 
 import torch
 
-from . import EvalPlan, tt_utv
+from . import EvalPlan, tt_full, tt_svd, tt_utv
 
 
 def complete(values, idx, shape, ranks, p_obs=None, steps=200, c1=1e-4, alpha0=1.0,
@@ -75,3 +85,98 @@ def complete(values, idx, shape, ranks, p_obs=None, steps=200, c1=1e-4, alpha0=1
         cores, r, loss = trial, rt, lt
         losses.append(loss)
     return cores, losses
+
+
+def _retract(full, ranks, method, precision, stream):
+    """Fixed-rank decomposition of the full tensor: (cores, "left"|"right")."""
+    if method == "SVD":
+        res = tt_svd(full, ranks=list(ranks), precision=precision, stream=stream)
+        return res.cores, res.orth
+    if method not in ("URV", "ULV"):
+        raise ValueError("retraction must be URV, ULV or SVD")
+    res = tt_utv(full, ranks=list(ranks), variant=method, precision=precision, stream=stream)
+    return res.cores, res.orth
+
+
+def _other_frame(cores, orth, ranks, precision, stream):
+    """The opposite orthogonal frame of the same tensor (its ranks are exact)."""
+    full = tt_full(cores, stream)
+    variant = "ULV" if orth == "right" else "URV"
+    return tt_utv(full, ranks=list(ranks), variant=variant, precision=precision,
+                  stream=stream).cores
+
+
+def tangent_block_cores(U, V, dU, alpha=None):
+    """Cores (ranks 2 r_k) of the tangent vector xi = sum_k U_<k dU_k V_>k,
+    or of X - alpha xi (X = U_1 .. U_d) when alpha is given."""
+    d = len(U)
+    c = 1.0 if alpha is None else -alpha
+    if d == 1:
+        return [dU[0] if alpha is None else U[0] - alpha * dU[0]]
+    out = []
+    for k in range(d):
+        if k == 0:
+            out.append(torch.cat([c * dU[0], U[0]], dim=2))
+        elif k == d - 1:
+            last = c * dU[k] if alpha is None else U[k] + c * dU[k]
+            out.append(torch.cat([V[k], last], dim=0))
+        else:
+            top = torch.cat([V[k], V[k].new_zeros(V[k].shape[0], U[k].shape[1], U[k].shape[2])],
+                            dim=2)
+            out.append(torch.cat([top, torch.cat([c * dU[k], U[k]], dim=2)], dim=0))
+    return [g.contiguous() for g in out]
+
+
+def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
+          precision="fp32", stream=None, callback=None):
+    """Riemannian gradient completion of Sec. 4.2.2.
+
+    values  device float32 [n]: observed entries m_e;
+    idx     device int64 [n]: their row-major linear indices in `shape`;
+    ranks   r_1 .. r_{d-1} (each at most 32: the rank-2r block TT of the
+            tangent vector is evaluated by a plan, whose ranks are at most 64);
+    retraction  "URV" (TT-URV, right-to-left), "ULV" (TT-ULV, left-to-right)
+            or "SVD" (TT-SVD), each at the fixed ranks;
+    p_obs   sampling rate of the spectral initialisation (default n / prod(shape)).
+    The initial point is the retraction of P_Omega(M) / p_obs.  Returns
+    (cores, losses, alphas): losses[t] = 1/2 ||P_Omega(X_t - M)||^2 for
+    t = 0 .. steps, alphas[t] the step of iteration t.  callback(t, cores) is
+    called for every iterate (t = 0 .. steps).
+    """
+    if values.dtype != torch.float32 or idx.dtype != torch.int64:
+        raise TypeError("values must be float32 and idx int64")
+    if not (values.is_cuda and idx.is_cuda) or values.numel() != idx.numel():
+        raise ValueError("values and idx must be device vectors of one length")
+    ranks = [int(r) for r in ranks]
+    if len(ranks) != len(shape) - 1 or any(r < 1 or 2 * r > 64 for r in ranks):
+        raise ValueError("need d - 1 ranks in [1, 32]")
+    n_total = math.prod(shape)
+    if p_obs is None:
+        p_obs = idx.numel() / n_total
+    z0 = torch.zeros(n_total, dtype=torch.float32, device=values.device)
+    z0[idx] = values / p_obs
+    X, orth = _retract(z0.view(*shape), ranks, retraction, precision, stream)
+    del z0
+    plan = EvalPlan(shape, [1, *ranks, 1], idx, stream)
+    plan2 = EvalPlan(shape, [1, *[2 * r for r in ranks], 1], idx, stream)
+    losses, alphas = [], []
+    for t in range(steps + 1):
+        if callback is not None:
+            callback(t, X)
+        z = plan.at(X, stream) - values
+        losses.append(0.5 * float(torch.dot(z, z)))
+        if t == steps:
+            break
+        other = _other_frame(X, orth, ranks, precision, stream)
+        U, V = (other, X) if orth == "right" else (X, other)
+        dU = plan.tangent_project(U, V, z, stream)
+        xi = plan2.at(tangent_block_cores(U, V, dU), stream)
+        den = float(torch.dot(xi, xi))
+        alpha = float(torch.dot(xi, z)) / den if den > 0.0 else 0.0
+        alphas.append(alpha)
+        full = tt_full(tangent_block_cores(U, V, dU, alpha), stream)
+        X, orth = _retract(full, ranks, retraction, precision, stream)
+        del full
+    plan.close(stream)
+    plan2.close(stream)
+    return X, losses, alphas

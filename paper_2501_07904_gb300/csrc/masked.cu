@@ -237,7 +237,11 @@ struct PassArgs {
   int64_t n, nchunks;
   int dims[kEvalMaxD];
   int ranks[kEvalMaxD + 1];
+  // cores left of core k (and core k in the forward and in the left row of
+  // mode 1) come from `cores`, those right of it from `rcores`; the plain
+  // backward passes the same set twice
   const float* cores[kEvalMaxD];
+  const float* rcores[kEvalMaxD];
   const int32_t* ix;   // [d][n]
   const int32_t* perm; // [n] order of core k
   const uint8_t* info; // [nchunks]
@@ -261,6 +265,7 @@ struct PassArgs {
   // shared-memory carve-up (in 4-byte words)
   int sL, sR, sT;      // row strides of the L, R and scratch buffers (0: buffer unused)
   int off_L, off_R, off_T, off_U;
+  int off_U2;          // mode 1 with two core sets: core k's slice from rcores (else -1)
 };
 
 // Left chain step over the chunk: out[p][b] = sum_q in[p][q] G[(q*I + i_p) r1 + b]
@@ -491,7 +496,7 @@ __device__ __forceinline__ void chain_step(const float* G, int I, int r0, int r1
 //   T[q][p] = gout sum_b M[q][b] c[b]       (core 1's row; row stride kChunk + 1)
 //   rows3[pos3] = sum_q L[q] M[q][:]        (core 3's row)
 // c and the running w stay in registers (NB >= round4(rR)).
-template <int NB>
+template <int NB, bool DO_U, bool DO_W>
 __device__ void emit_entry(const PassArgs& a, int p, const float* Ls, const float* Rs, float* Ts,
                            const float* U, float g, int pos3, int rL, int rR) {
   const int rLp = round4_dev(rL), rRp = round4_dev(rR);
@@ -500,7 +505,7 @@ __device__ void emit_entry(const PassArgs& a, int p, const float* Ls, const floa
 #pragma unroll
   for (int b4 = 0; b4 < NB; b4 += 4) {
     float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (b4 < rRp) v = *reinterpret_cast<const float4*>(rp + b4);
+    if (DO_U && b4 < rRp) v = *reinterpret_cast<const float4*>(rp + b4);
     cr[b4 / 2] = make_float2(v.x, v.y);
     cr[b4 / 2 + 1] = make_float2(v.z, v.w);
     w[b4 / 2] = w[b4 / 2 + 1] = make_float2(0.0f, 0.0f);
@@ -508,7 +513,8 @@ __device__ void emit_entry(const PassArgs& a, int p, const float* Ls, const floa
   const float* lp = Ls + p * a.sL;
   float* tp = Ts + p;  // u of entry p at Ts[q * (kChunk + 1) + p]
   for (int q4 = 0; q4 < rLp; q4 += 4) {
-    const float4 l = *reinterpret_cast<const float4*>(lp + q4);
+    float4 l = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (DO_W) l = *reinterpret_cast<const float4*>(lp + q4);
     const float lq[4] = {l.x, l.y, l.z, l.w};
 #pragma unroll
     for (int qq = 0; qq < 4; ++qq) {
@@ -520,15 +526,20 @@ __device__ void emit_entry(const PassArgs& a, int p, const float* Ls, const floa
         if (b4 < rRp) {
           const float4 m = *reinterpret_cast<const float4*>(mrow + b4);
           const float2 m01 = make_float2(m.x, m.y), m23 = make_float2(m.z, m.w);
-          ua = ffma2(m01, cr[b4 / 2], ua);
-          ub = ffma2(m23, cr[b4 / 2 + 1], ub);
-          w[b4 / 2] = ffma2(ll, m01, w[b4 / 2]);
-          w[b4 / 2 + 1] = ffma2(ll, m23, w[b4 / 2 + 1]);
+          if (DO_U) {
+            ua = ffma2(m01, cr[b4 / 2], ua);
+            ub = ffma2(m23, cr[b4 / 2 + 1], ub);
+          }
+          if (DO_W) {
+            w[b4 / 2] = ffma2(ll, m01, w[b4 / 2]);
+            w[b4 / 2 + 1] = ffma2(ll, m23, w[b4 / 2 + 1]);
+          }
         }
       }
-      tp[(q4 + qq) * (kChunk + 1)] = ((ua.x + ua.y) + (ub.x + ub.y)) * g;
+      if (DO_U) tp[(q4 + qq) * (kChunk + 1)] = ((ua.x + ua.y) + (ub.x + ub.y)) * g;
     }
   }
+  if (!DO_W) return;
   float* dst = a.rows3 + (int64_t)pos3 * rR;
   if ((rR & 3) == 0) {
 #pragma unroll
@@ -556,6 +567,7 @@ __global__ void __launch_bounds__(kEvalThreads, 5) eval_pass_kernel(PassArgs a) 
   float* Rs = sm + a.off_R;
   float* Ts = sm + a.off_T;
   float* U = sm + a.off_U;
+  float* U2 = a.off_U2 >= 0 ? sm + a.off_U2 : U;
   const int t = threadIdx.x, k = a.k, d = a.d;
   const int64_t c = blockIdx.x, p0 = c * kChunk;
   const int cnt = (int)min((int64_t)kChunk, a.n - p0);
@@ -637,7 +649,7 @@ __global__ void __launch_bounds__(kEvalThreads, 5) eval_pass_kernel(PassArgs a) 
     float* dst = toR ? Rs : Ts;
     const float* src = s == 0 ? nullptr : (toR ? Ts : Rs);
     // the backward's last right step folds in gout (mode 1: the left side has it)
-    chain_step<false>(a.cores[j], a.dims[j], a.ranks[j], a.ranks[j + 1], ixs + j * kChunk, src,
+    chain_step<false>(a.rcores[j], a.dims[j], a.ranks[j], a.ranks[j + 1], ixs + j * kChunk, src,
                       toR ? a.sT : a.sR, dst, toR ? a.sR : a.sT, cnt,
                       (a.backward && a.mode == 0 && s == nR - 1) ? gs : nullptr);
     __syncthreads();
@@ -701,20 +713,36 @@ __global__ void __launch_bounds__(kEvalThreads, 5) eval_pass_kernel(PassArgs a) 
   if (a.mode == 1) {
     // per run of equal i_2: stage M = G_2[:, i_2, :]; per entry (L = gout a,
     // R = c): u = M c -> gout u into the scratch rows, w = L^T M -> rows3
+    // (two core sets: u takes the right set's slice, w the left set's)
     for (int s = 0; s < nseg; ++s) {
       const int s0 = segs[s], s1 = segs[s + 1];
       const int i = ixs[k * kChunk + s0];
       stage_slice(Gk, I, i, rL, rR, U);
+      if (U2 != U) stage_slice(a.rcores[k], I, i, rL, rR, U2);
       __syncthreads();
       if (t >= s0 && t < s1) {
-        if (rRp <= 4)
-          emit_entry<4>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
-        else if (rRp <= 8)
-          emit_entry<8>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
-        else if (rRp <= 16)
-          emit_entry<16>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
-        else
-          emit_entry<32>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+        // u = M c takes the right set's slice, w = L^T M the left set's: with
+        // two sets the entry is emitted in two halves
+        if (U2 != U) {
+          if (rRp <= 8) {
+            emit_entry<8, true, false>(a, t, Ls, Rs, Ts, U2, gs[t], posB[t], rL, rR);
+            emit_entry<8, false, true>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+          } else if (rRp <= 16) {
+            emit_entry<16, true, false>(a, t, Ls, Rs, Ts, U2, gs[t], posB[t], rL, rR);
+            emit_entry<16, false, true>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+          } else {
+            emit_entry<32, true, false>(a, t, Ls, Rs, Ts, U2, gs[t], posB[t], rL, rR);
+            emit_entry<32, false, true>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+          }
+        } else if (rRp <= 4) {
+          emit_entry<4, true, true>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+        } else if (rRp <= 8) {
+          emit_entry<8, true, true>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+        } else if (rRp <= 16) {
+          emit_entry<16, true, true>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+        } else {
+          emit_entry<32, true, true>(a, t, Ls, Rs, Ts, U, gs[t], posB[t], rL, rR);
+        }
       }
       __syncthreads();
     }
@@ -842,6 +870,87 @@ __global__ void eval_fixup_kernel(PassArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ tangent gauge
+//
+// For an m x r left unfolding U with orthonormal columns and the increment Y
+// of the same shape: Y <- Y - U (U^T Y).  S = U^T Y is summed in FP64 by row
+// blocks (gauge_gram_kernel: block b takes rows [b*rows, (b+1)*rows) and
+// writes its partial), the partials in block order (gauge_reduce_kernel),
+// then every row is updated from S (gauge_apply_kernel).
+
+constexpr int kGaugeThreads = 256;
+constexpr int kGaugeRows = 1024;    // rows per partial sum
+constexpr int kGaugeMaxBlocks = 64;
+constexpr int kGaugeTile = 32;      // rows staged per round
+
+int gauge_blocks(int64_t m) {
+  return (int)std::min<int64_t>(kGaugeMaxBlocks, (m + kGaugeRows - 1) / kGaugeRows);
+}
+
+__global__ void __launch_bounds__(kGaugeThreads) gauge_gram_kernel(const float* __restrict__ U,
+                                                                   const float* __restrict__ Y,
+                                                                   int64_t m, int r, int64_t rows,
+                                                                   double* __restrict__ part) {
+  __shared__ float us[kGaugeTile * kEvalMaxR], ys[kGaugeTile * kEvalMaxR];
+  const int t = threadIdx.x, rr = r * r;
+  const int64_t i0 = blockIdx.x * rows, i1 = min(m, i0 + rows);
+  double acc[kEvalMaxR * kEvalMaxR / kGaugeThreads];
+#pragma unroll
+  for (int j = 0; j < kEvalMaxR * kEvalMaxR / kGaugeThreads; ++j) acc[j] = 0.0;
+  for (int64_t ib = i0; ib < i1; ib += kGaugeTile) {
+    const int nr = (int)min((int64_t)kGaugeTile, i1 - ib);
+    __syncthreads();
+    for (int e = t; e < nr * r; e += kGaugeThreads) {
+      us[e] = U[ib * r + e];
+      ys[e] = Y[ib * r + e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kEvalMaxR * kEvalMaxR / kGaugeThreads; ++j) {
+      const int e = t + j * kGaugeThreads;
+      if (e < rr) {
+        const int a = e / r, b = e - a * r;
+        double v = acc[j];
+        for (int q = 0; q < nr; ++q) v = fma((double)us[q * r + a], (double)ys[q * r + b], v);
+        acc[j] = v;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kEvalMaxR * kEvalMaxR / kGaugeThreads; ++j) {
+    const int e = t + j * kGaugeThreads;
+    if (e < rr) part[(int64_t)blockIdx.x * rr + e] = acc[j];
+  }
+}
+
+__global__ void gauge_reduce_kernel(const double* __restrict__ part, int nblk, int rr,
+                                    double* __restrict__ S) {
+  for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) v += part[(int64_t)b * rr + e];
+    S[e] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kGaugeThreads) gauge_apply_kernel(const float* __restrict__ U,
+                                                                    float* __restrict__ Y,
+                                                                    int64_t m, int r,
+                                                                    const double* __restrict__ S) {
+  __shared__ double ss[kEvalMaxR * kEvalMaxR];
+  for (int e = threadIdx.x; e < r * r; e += kGaugeThreads) ss[e] = S[e];
+  __syncthreads();
+  const int64_t total = m * r;
+  for (int64_t e = (int64_t)blockIdx.x * kGaugeThreads + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * kGaugeThreads) {
+    const int64_t i = e / r;
+    const int b = (int)(e - i * r);
+    const float* ui = U + i * r;
+    double v = 0.0;
+    for (int a = 0; a < r; ++a) v = fma((double)ui[a], ss[a * r + b], v);
+    Y[e] = (float)((double)Y[e] - v);
+  }
+}
+
 }  // namespace
 
 // Byte layout of a plan's device block (computed from d, dims, ranks, n).
@@ -852,7 +961,8 @@ struct Layout {
   int nb[kEvalMaxD];
   bool fast3 = false;  // d = 3 with round4(r_2) <= 32: the backward stores per-entry rows
   size_t off_err = 0, off_ix = 0, off_perm = 0, off_info = 0, off_head = 0, off_slots = 0,
-         off_pos = 0, off_rows1 = 0, off_rows3 = 0, off_tmp = 0, off_hist = 0, total = 0;
+         off_pos = 0, off_rows1 = 0, off_rows3 = 0, off_tmp = 0, off_hist = 0, off_gauge = 0,
+         total = 0;
 };
 
 bool valid_shape(int d, const int64_t* dims, const int64_t* ranks, int64_t n, const char** why) {
@@ -905,6 +1015,12 @@ Layout layout_of(int d, const int64_t* dims, const int64_t* ranks, int64_t n) {
   }
   L.off_tmp = take((size_t)n * sizeof(int32_t));
   L.off_hist = take((size_t)256 * L.ntiles * sizeof(int32_t));
+  // tangent projection: the FP64 partials of U_k^T Y_k (k < d-1), then S
+  size_t gauge = 0;
+  for (int k = 0; k + 1 < d; ++k)
+    gauge = std::max(gauge, (size_t)(gauge_blocks(ranks[k] * dims[k]) + 1) * ranks[k + 1] *
+                                ranks[k + 1] * sizeof(double));
+  L.off_gauge = take(gauge);
   L.total = o;
   return L;
 }
@@ -933,11 +1049,16 @@ size_t pass_smem(PassArgs& a, const int64_t* ranks) {
                               : std::max(round4(rL) * round4(rR), kEvalThreads * 16);
   // the staging / fold buffer is only used after the chains: it shares the
   // scratch buffer when that is large enough
+  a.off_U2 = -1;
   if (a.mode != 1 && a.sT > 0 && kChunk * a.sT >= usz) {
     a.off_U = a.off_T;
     return (size_t)(a.off_T + kChunk * a.sT) * sizeof(float);
   }
   a.off_U = a.off_T + kChunk * a.sT;
+  if (a.mode == 1 && a.rcores[a.k] != a.cores[a.k]) {
+    a.off_U2 = a.off_U + usz;  // usz is a multiple of 16 words: float4-aligned
+    return (size_t)(a.off_U2 + usz) * sizeof(float);
+  }
   return (size_t)(a.off_U + usz) * sizeof(float);
 }
 
@@ -984,7 +1105,8 @@ tt_status plan_cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return plan_cuda_fail(e_, what); \
   } while (0)
 
-ttk::PassArgs pass_args(const tt_eval_plan* P, const float* const* cores, int k, int backward) {
+ttk::PassArgs pass_args(const tt_eval_plan* P, const float* const* cores,
+                        const float* const* rcores, int k, int backward) {
   ttk::PassArgs a;
   std::memset(&a, 0, sizeof a);
   a.d = P->d;
@@ -995,6 +1117,7 @@ ttk::PassArgs pass_args(const tt_eval_plan* P, const float* const* cores, int k,
   for (int j = 0; j < P->d; ++j) {
     a.dims[j] = (int)P->dims[j];
     a.cores[j] = cores[j];
+    a.rcores[j] = rcores[j];
   }
   for (int j = 0; j <= P->d; ++j) a.ranks[j] = (int)P->ranks[j];
   a.ix = reinterpret_cast<const int32_t*>(P->base + P->L.off_ix);
@@ -1143,7 +1266,7 @@ tt_status tt_eval_plan_at(const tt_eval_plan* plan, const float* const* cores, f
   for (int k = 0; k < plan->d; ++k)
     if (!cores[k]) return plan_fail(TT_EINVAL, "NULL core");
   if (plan->n == 0) return TT_OK;
-  ttk::PassArgs a = pass_args(plan, cores, plan->L.pivot, 0);
+  ttk::PassArgs a = pass_args(plan, cores, cores, plan->L.pivot, 0);
   a.out = out;
   const size_t sm = ttk::pass_smem(a, plan->ranks);
   ttk::count_launch();
@@ -1154,17 +1277,24 @@ tt_status tt_eval_plan_at(const tt_eval_plan* plan, const float* const* cores, f
 
 tt_status tt_eval_plan_backward(tt_eval_plan* plan, const float* const* cores, const float* gout,
                                 float* const* grads, void* stream) {
+  return tt_eval_plan_backward_mixed(plan, cores, cores, gout, grads, stream);
+}
+
+tt_status tt_eval_plan_backward_mixed(tt_eval_plan* plan, const float* const* left,
+                                      const float* const* right, const float* gout,
+                                      float* const* grads, void* stream) {
   ttk::set_last_error("");
-  if (!plan || !cores || !grads || (plan->n > 0 && !gout)) return plan_fail(TT_EINVAL, "NULL argument");
+  if (!plan || !left || !right || !grads || (plan->n > 0 && !gout))
+    return plan_fail(TT_EINVAL, "NULL argument");
   for (int k = 0; k < plan->d; ++k)
-    if (!cores[k] || !grads[k]) return plan_fail(TT_EINVAL, "NULL core or gradient");
+    if (!left[k] || !right[k] || !grads[k]) return plan_fail(TT_EINVAL, "NULL core or gradient");
   if (plan->n == 0) return TT_OK;
   cudaStream_t st = (cudaStream_t)stream;
   // d = 3: the middle core's pass first (it writes the outer cores' rows)
   const int order3[3] = {1, 0, 2};
   for (int kk = 0; kk < plan->d; ++kk) {
     const int k = plan->L.fast3 ? order3[kk] : kk;
-    ttk::PassArgs a = pass_args(plan, cores, k, 1);
+    ttk::PassArgs a = pass_args(plan, left, right, k, 1);
     a.gout = gout;
     a.grad = grads[k];
     if (plan->L.fast3) a.mode = k == 1 ? 1 : (k == 0 ? 2 : 3);
@@ -1173,6 +1303,39 @@ tt_status tt_eval_plan_backward(tt_eval_plan* plan, const float* const* cores, c
     ttk::eval_pass_kernel<<<(unsigned)plan->L.nchunks, ttk::kEvalThreads, sm, st>>>(a);
     ttk::eval_fixup_kernel<<<(unsigned)plan->L.nchunks, ttk::kEvalThreads, 0, st>>>(a);
     EV_CK(cudaGetLastError(), "masked evaluation backward");
+  }
+  return TT_OK;
+}
+
+tt_status tt_tangent_project(tt_eval_plan* plan, const float* const* U, const float* const* V,
+                             const float* z, float* const* dU, void* stream) {
+  ttk::set_last_error("");
+  if (!plan || !U || !V || !dU || (plan->n > 0 && !z)) return plan_fail(TT_EINVAL, "NULL argument");
+  for (int k = 0; k < plan->d; ++k)
+    if (!U[k] || !V[k] || !dU[k]) return plan_fail(TT_EINVAL, "NULL core or increment");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int k = 0; k < plan->d; ++k)
+    EV_CK(cudaMemsetAsync(dU[k], 0,
+                          (size_t)plan->ranks[k] * plan->dims[k] * plan->ranks[k + 1] * sizeof(float),
+                          st),
+          "tangent projection");
+  if (plan->n == 0) return TT_OK;
+  const tt_status s = tt_eval_plan_backward_mixed(plan, U, V, z, dU, stream);
+  if (s != TT_OK) return s;
+  double* part = reinterpret_cast<double*>(plan->base + plan->L.off_gauge);
+  for (int k = 0; k + 1 < plan->d; ++k) {
+    const int64_t m = plan->ranks[k] * plan->dims[k];
+    const int r = (int)plan->ranks[k + 1];
+    const int nblk = ttk::gauge_blocks(m);
+    const int64_t rows = (m + nblk - 1) / nblk;
+    double* S = part + (int64_t)nblk * r * r;
+    const int napply = (int)std::min<int64_t>((m * r + ttk::kGaugeThreads - 1) / ttk::kGaugeThreads,
+                                              1024);
+    ttk::count_launch(3);
+    ttk::gauge_gram_kernel<<<nblk, ttk::kGaugeThreads, 0, st>>>(U[k], dU[k], m, r, rows, part);
+    ttk::gauge_reduce_kernel<<<1, ttk::kGaugeThreads, 0, st>>>(part, nblk, r * r, S);
+    ttk::gauge_apply_kernel<<<napply, ttk::kGaugeThreads, 0, st>>>(U[k], dU[k], m, r, S);
+    EV_CK(cudaGetLastError(), "tangent projection");
   }
   return TT_OK;
 }

@@ -246,6 +246,8 @@ def test_eval_plan_arguments_rejected(L):
     ptrs = (ctypes.c_void_p * 2)(1, 1)
     assert L.tt_eval_plan_at(None, ptrs, ctypes.c_void_p(1), None) == 1
     assert L.tt_eval_plan_backward(None, ptrs, ctypes.c_void_p(1), ptrs, None) == 1
+    assert L.tt_eval_plan_backward_mixed(None, ptrs, ptrs, ctypes.c_void_p(1), ptrs, None) == 1
+    assert L.tt_tangent_project(None, ptrs, ptrs, ctypes.c_void_p(1), ptrs, None) == 1
     L.tt_eval_plan_destroy(None, None)
     assert L.tt_eval_plan_device_bytes(None) == 0
 
