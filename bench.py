@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--inner", default="qlp", choices=["qlp", "usvp"],
+                    help="small rank-revealing factor of each sweep step")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain-FP32 comparison timed beside a mixed-precision run")
     ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
@@ -228,7 +230,7 @@ def run_ours(args, wl, rank, world):
     A_host = torch.from_numpy(A_np).pin_memory()
     A = A_host.to(dev)
     st = torch.cuda.current_stream()
-    kw = dict(eps=wl["eps"], variant=wl["variant"], precision=args.precision)
+    kw = dict(eps=wl["eps"], variant=wl["variant"], precision=args.precision, inner=args.inner)
 
     def barrier():
         if world > 1:
@@ -394,7 +396,7 @@ def run_ours(args, wl, rank, world):
         "dtype": {"mixed": "tf32x2/f32", "fp32": "f32", "fp64": "f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {wl['desc']}", "precision": args.precision,
-                   "l2": l2_note(wl),
+                   "inner": args.inner, "l2": l2_note(wl),
                    "parallelism": f"replicas x{world} (independent problems)", "ranks": ranks,
                    "bytes_per_step": nbytes},
         "roofline": roof, "sweep_roofline": sweep_roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

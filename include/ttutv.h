@@ -122,8 +122,27 @@ typedef struct {
                                Y <- X^T X Q with Q an orthonormal basis of the previous Y (the
                                randomized range finder behind randUTV, Sec. 2.2); no effect when
                                Omega = I.  Default 0. */
+  int32_t inner;            /* tt_inner: the small rank-revealing factor of tt_utv, default
+                               TT_INNER_QLP; ignored by tt_svd */
+  int32_t usvp_iters;       /* TT_INNER_USVP: power iterations per basis vector, in [0, 64],
+                               default 8 */
   int32_t pad2_;
 } tt_opts;
+
+/* Inner factor of each tt_utv step, applied to the Gram matrix of the basis
+ * side (or of the range-projected matrix on a sketched step):
+ *  TT_INNER_QLP  : Stewart's pivoted QLP (the default, see tt_utv);
+ *  TT_INNER_USVP : USV-plus-style deflation (the rank-revealing decomposition
+ *                  the paper runs inside TT-ULV in Sec. 4, with its stopping
+ *                  rule adapted to fixed ranks and to Alg. 2): basis vectors
+ *                  one at a time, each started from the column of largest norm
+ *                  of the deflated matrix D = X (I - V V^T) and refined by
+ *                  usvp_iters power iterations on D^T D, re-orthogonalized
+ *                  twice against the basis; the error of keeping i vectors is
+ *                  ||X - X V_i V_i^T||_F^2 (plus the sketch's range miss); the
+ *                  rank is fixed or the first i with error <= eps_k^2.  One CTA,
+ *                  sequential in the rank: slower than the QLP. */
+typedef enum { TT_INNER_QLP = 0, TT_INNER_USVP = 1 } tt_inner;
 
 /* Fill *o with the defaults listed above. */
 void tt_opts_default(tt_opts* o);
@@ -261,6 +280,33 @@ void tt_result_free(tt_result* r, tt_free_fn free_fn, void* alloc_ctx, void* str
 size_t tt_full_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks, int32_t dtype);
 tt_status tt_full(int32_t d, const int64_t* dims, const int64_t* ranks, const void* const* cores,
                   int32_t dtype, void* out, void* work, void* stream);
+
+/* Orthogonalize TT cores (Def. 2.2): the same tensor with left-orthogonal
+ * cores 1..d-1 (side = 1: each left unfolding [r_{k-1} I_k] x [r_k] has
+ * orthonormal columns, core d carries the norm) or right-orthogonal cores
+ * 2..d (side = 0: each right unfolding [r_{k-1}] x [I_k r_k] has orthonormal
+ * rows, core 1 carries the norm), the frames of the tangent space in which
+ * the Riemannian gradient of Sec. 4.2.2 is written.  Left: for k = 1..d-1 the
+ * unfolding of R_{k-1} G_k (R_0 = 1) is factored by Cholesky-QR2 with FP64
+ * Gram matrices, Q_k R_k, Q_k becomes core k and R_k = Q_k^T (R_{k-1} G_k) is
+ * multiplied into core k+1; right: mirrored from core d down to 2.  The two
+ * passes leave the columns orthonormal to the data's rounding when each
+ * unfolding's condition number is below ~1e6 (the first pass's Gram is shifted
+ * by 4 r u_64 of its trace, so a numerically rank-deficient unfolding still
+ * factors, with columns that are then orthonormal only to ~1e-8).
+ *   d, dims, ranks  host; ranks r_0 = r_d = 1, each r_k <= 256, and
+ *                   r_k <= r_{k-1} I_k (left) / r_{k-1} <= I_k r_k (right),
+ *                   else TT_EINVAL;
+ *   cores           host array of d device pointers [r_{k-1}][I_k][r_k] of `dtype`;
+ *   out             host array of d device pointers of the same shapes, none of
+ *                   them one of the input cores (TT_EINVAL);
+ *   work            device scratch of tt_orthogonalize_work_bytes(...) bytes.
+ * Asynchronous on `stream`; a NaN in the input gives NaN cores (not checked). */
+size_t tt_orthogonalize_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks,
+                                   int32_t dtype);
+tt_status tt_orthogonalize(int32_t d, const int64_t* dims, const int64_t* ranks,
+                           const void* const* cores, int32_t dtype, int32_t side, void* const* out,
+                           void* work, void* stream);
 
 /* tt_full without any device allocation, for callers that cannot allocate
  * device memory during the call: code running with every byte of device

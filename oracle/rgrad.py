@@ -147,13 +147,22 @@ def tangent_cores(U, V, dU, alpha=0.0, with_point=False):
     return out
 
 
+def sketch_widths(ranks):
+    """(l_full, p) of the retraction: X - alpha xi has TT-ranks at most 2 r_k,
+    so a sketch of r_k + max(r) + 16 >= 2 r_k + 16 columns holds the range of
+    every unfolding it is used on (basis side above 2 max(r) + 16)."""
+    rmax = max(list(ranks)[1:-1])
+    return 2 * rmax + 16, rmax + 16
+
+
 def retract(Xhat_full, ranks, variant="URV"):
     """Fixed-rank TT-UTV (or TT-SVD with variant "SVD") of the full tensor."""
     r = list(ranks)[1:-1]
+    l_full, p = sketch_widths(ranks)
     if variant == "SVD":
-        res = ott.tt_svd(Xhat_full, ranks=r)
+        res = ott.tt_svd(Xhat_full, ranks=r, l_full=l_full, p=p)
     else:
-        res = ott.tt_utv(Xhat_full, ranks=r, variant=variant)
+        res = ott.tt_utv(Xhat_full, ranks=r, variant=variant, l_full=l_full, p=p)
     return res["cores"]
 
 

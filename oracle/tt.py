@@ -113,6 +113,76 @@ def qlp_tails(L):
     return np.concatenate([np.cumsum(c[::-1])[::-1], [0.0]])
 
 
+USVP_ITERS = 8
+
+
+def usv_plus(X, delta2, r_fixed, r_max, q=USVP_ITERS, mu2=0.0):
+    """USV-plus-style deflation (the rank-revealing decomposition the paper
+    runs as TT-ULV's inner factor in Sec. 4, with its stopping rule adapted to
+    fixed ranks and to Alg. 2's accuracy rule): the right singular vectors of
+    X (N_o x N_b, basis on the column side) are estimated one at a time, each
+    by q power iterations on the deflated matrix D = X (I - V V^T).
+
+    Per vector: the start is D^T D e_j for the column j of D of largest norm
+    (lowest index on ties); q times v <- D^T D v / ||D^T D v||; v is
+    re-orthogonalized twice against V and appended.  tail(i) = mu2 +
+    ||X - X V_i V_i^T||^2 (summed directly) is the error of keeping the first
+    i vectors.  Stops at the fixed rank (clamped to r_max), else at the
+    first i >= 1 with tail(i) <= delta2, else at r_max.  When D vanishes
+    before a fixed rank is reached, unit vectors orthogonalized against V
+    (twice) complete it.  Returns (V (N_b x r), tails [tail(0) .. tail(r)]).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    n_o, n_b = X.shape
+    x2 = float(np.sum(X * X))
+    target = None if r_fixed is None else max(1, min(int(r_fixed), r_max))
+    V = np.zeros((n_b, 0))
+    tails = [mu2 + x2]
+    while V.shape[1] < r_max:
+        i = V.shape[1]
+        if target is not None and i >= target:
+            break
+        if target is None and i >= 1 and tails[-1] <= delta2:
+            break
+        D = X - (X @ V) @ V.T
+        cn = np.einsum("ij,ij->j", D, D)
+        j = int(np.argmax(cn))
+        v = D.T @ D[:, j] if cn[j] > 0.0 else np.zeros(n_b)
+        nv = float(np.linalg.norm(v))
+        if nv > 0.0:
+            v = v / nv
+            for _ in range(q):
+                w = D.T @ (D @ v)
+                nw = float(np.linalg.norm(w))
+                if nw == 0.0:
+                    break
+                v = w / nw
+            for _ in range(2):
+                v = v - V @ (V.T @ v)
+            nv = float(np.linalg.norm(v))
+        if nv <= 0.0 or not np.isfinite(nv):
+            if target is None:
+                break                          # D = 0: nothing left to capture
+            # complete the fixed rank with unit vectors
+            for c in range(n_b):
+                e = np.zeros(n_b)
+                e[c] = 1.0
+                for _ in range(2):
+                    e = e - V @ (V.T @ e)
+                ne = float(np.linalg.norm(e))
+                if ne > 0.5:
+                    v, nv = e / ne, 1.0
+                    break
+            else:
+                break
+        else:
+            v = v / nv
+        V = np.concatenate([V, v[:, None]], axis=1)
+        E = X - (X @ V) @ V.T
+        tails.append(mu2 + float(np.sum(E * E)))
+    return V, np.asarray(tails)
+
+
 def choose_rank(tails, delta2, r_fixed, r_max):
     """Reading S3 of the rule in Sec. 3.1: smallest r >= 1 with tail(r) <= delta^2."""
     if r_fixed is not None:
@@ -124,7 +194,7 @@ def choose_rank(tails, delta2, r_fixed, r_max):
 
 
 def factor_step(X, delta2, r_fixed, r_prev, seed, step, kind="qlp",
-                l_full=L_FULL, p=OVERSAMPLE, q=0):
+                l_full=L_FULL, p=OVERSAMPLE, q=0, usvp_q=USVP_ITERS):
     """One truncated UTV of X (N_o x N_b, basis on the column side).
 
     Returns dict(r, basis (N_b x r), carry (N_o x r) = X basis, tail, l, path).
@@ -143,6 +213,15 @@ def factor_step(X, delta2, r_fixed, r_prev, seed, step, kind="qlp",
     while True:
         if path == "sketch":
             W, B, mu2 = range_step(X, l, seed, step, q)
+        if kind == "usvp":
+            r_max = min(B.shape[1], n_o, n_b)
+            Z, tails = usv_plus(B, delta2, r_fixed, r_max, usvp_q, mu2)
+            r = Z.shape[1]
+            if (path == "sketch" and l < min(n_b, n_o) and r_fixed is None
+                    and (r > l - p or tails[r] > delta2)):
+                l = min(2 * l, n_b, n_o)
+                continue
+            break
         if kind == "qlp":
             Z, L, _ = qlp(B)
             tails = mu2 + qlp_tails(L)
@@ -176,7 +255,7 @@ def _weights(d, weights):
 
 
 def tt_sweep(A, eps=None, ranks=None, variant="URV", kind="qlp", direction=None,
-             weights=None, l_full=L_FULL, p=OVERSAMPLE, seed=0, q=0):
+             weights=None, l_full=L_FULL, p=OVERSAMPLE, seed=0, q=0, usvp_q=USVP_ITERS):
     """TT decomposition by a sweep of truncated UTVs.
 
     variant 'URV' -> right-to-left (Alg. 3), right-orthogonal cores;
@@ -217,7 +296,7 @@ def tt_sweep(A, eps=None, ranks=None, variant="URV", kind="qlp", direction=None,
             C = C.reshape(m, n)
             u = k - 1
             st = factor_step(C, delta2_of(u) if eps is not None else 0.0, fixed_of(u), r_prev,
-                             seed, k, kind, l_full, p, q)
+                             seed, k, kind, l_full, p, q, usvp_q)
             r = st["r"]
             cores[k - 1] = st["basis"].T.reshape(r, dims[k - 1], r_next)
             C = st["carry"]
@@ -236,7 +315,7 @@ def tt_sweep(A, eps=None, ranks=None, variant="URV", kind="qlp", direction=None,
             C = C.reshape(m, n)
             u = k
             st = factor_step(C.T, delta2_of(u) if eps is not None else 0.0, fixed_of(u), r_prev,
-                             seed, k, kind, l_full, p, q)
+                             seed, k, kind, l_full, p, q, usvp_q)
             r = st["r"]
             cores[k - 1] = st["basis"].reshape(r_left, dims[k - 1], r)
             C = st["carry"].T
@@ -251,9 +330,12 @@ def tt_sweep(A, eps=None, ranks=None, variant="URV", kind="qlp", direction=None,
                 orth="right" if direction == "RL" else "left")
 
 
-def tt_utv(A, eps=None, ranks=None, variant="URV", **kw):
-    """TT-URV (right-to-left, Alg. 3) or TT-ULV (left-to-right, Alg. 1/2)."""
-    return tt_sweep(A, eps=eps, ranks=ranks, variant=variant, kind="qlp", **kw)
+def tt_utv(A, eps=None, ranks=None, variant="URV", inner="qlp", **kw):
+    """TT-URV (right-to-left, Alg. 3) or TT-ULV (left-to-right, Alg. 1/2).
+    inner: "qlp" (pivoted QLP, the default) or "usvp" (USV-plus-style
+    deflation, usv_plus)."""
+    assert inner in ("qlp", "usvp")
+    return tt_sweep(A, eps=eps, ranks=ranks, variant=variant, kind=inner, **kw)
 
 
 def tt_svd(A, eps=None, ranks=None, direction="LR", **kw):

@@ -31,6 +31,7 @@ for _code, _name in STATUS.items():
     globals()[_name] = _code
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 SMALL = {"auto": 0, "fp32": 1, "fp64": 2, "df": 3}
+INNER = {"qlp": 0, "usvp": 1}
 TT_F32, TT_F64 = 0, 1
 TT_URV, TT_ULV = 0, 1
 TT_RL, TT_LR = 0, 1
@@ -38,7 +39,7 @@ TT_RL, TT_LR = 0, 1
 # Every symbol include/ttutv.h declares.
 EXPORTS = ["tt_opts_default", "tt_utv", "tt_utv_sharded", "tt_svd", "tt_result_free",
            "tt_full_work_bytes",
-           "tt_full", "tt_full_noalloc", "tt_full_noalloc_max_work_bytes", "tt_rse_work_bytes",
+           "tt_full", "tt_full_noalloc", "tt_orthogonalize_work_bytes", "tt_orthogonalize", "tt_full_noalloc_max_work_bytes", "tt_rse_work_bytes",
            "tt_rse", "tt_eval_plan_create", "tt_eval_plan_destroy", "tt_eval_plan_device_bytes",
            "tt_eval_plan_at", "tt_eval_plan_backward", "tt_eval_plan_backward_mixed",
            "tt_tangent_project", "tt_eval_at",
@@ -61,7 +62,8 @@ class tt_opts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("weights", ctypes.POINTER(ctypes.c_double)),
                 ("orth_precision", ctypes.c_int32), ("reverse", ctypes.c_int32),
                 ("phase_ms", ctypes.POINTER(ctypes.c_double)),
-                ("power_iters", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
+                ("power_iters", ctypes.c_int32), ("inner", ctypes.c_int32),
+                ("usvp_iters", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
 
 
 class tt_result(ctypes.Structure):
@@ -124,6 +126,11 @@ def lib():
     L.tt_full_noalloc_max_work_bytes.restype = SZ
     L.tt_rse_work_bytes.argtypes = [I32, PI64, PI64, I32]
     L.tt_rse_work_bytes.restype = SZ
+    L.tt_orthogonalize_work_bytes.argtypes = [I32, PI64, PI64, I32]
+    L.tt_orthogonalize_work_bytes.restype = SZ
+    L.tt_orthogonalize.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), I32, I32, ctypes.POINTER(P),
+                                   P, P]
+    L.tt_orthogonalize.restype = I32
     L.tt_rse.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), I32, P, P, P, P]
     L.tt_rse.restype = I32
     L.tt_eval_plan_create.argtypes = [I32, PI64, PI64, P, I64, ALLOC_FN, FREE_FN, P, P,
@@ -236,7 +243,8 @@ class TTResult:
 
 
 def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream,
-           timing=False, orth="auto", reverse=False, power_iters=0, dims=None, shard=None):
+           timing=False, orth="auto", reverse=False, power_iters=0, dims=None, shard=None,
+           inner="qlp", usvp_iters=8):
     if not isinstance(A, torch.Tensor):
         raise TypeError("A must be a torch.Tensor")
     if A.dtype not in (torch.float32, torch.float64):
@@ -258,6 +266,8 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
     opts.seed = int(seed)
     opts.reverse = 1 if reverse else 0
     opts.power_iters = int(power_iters)
+    opts.inner = INNER[inner]
+    opts.usvp_iters = int(usvp_iters)
     wbuf = None
     if weights is not None:
         wbuf = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
@@ -299,7 +309,7 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
 
 def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, oversample=16,
            l_full=256, small="auto", weights=None, stream=None, timing=False, orth="auto",
-           reverse=False, direction=None, power_iters=0):
+           reverse=False, direction=None, power_iters=0, inner="qlp", usvp_iters=8):
     """TT-URV right-to-left (Alg. 3) or TT-ULV left-to-right (Alg. 1/2).
 
     Give ``eps`` (prescribed relative accuracy, Alg. 2) or ``ranks``
@@ -310,7 +320,9 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
     "LR" the ULV left-to-right one).  ``reverse`` factors the index-reversed
     tensor and returns its cores read back as cores of ``A`` (Remark after
     Thm 3.2: URV then gives a left-orthogonal TT).  ``power_iters`` adds q
-    subspace iterations to every sketched range.
+    subspace iterations to every sketched range.  ``inner`` picks the small
+    rank-revealing factor: "qlp" (pivoted QLP) or "usvp" (USV-plus-style
+    deflation with ``usvp_iters`` power iterations per basis vector).
     """
     if (eps is None) == (ranks is None):
         raise ValueError("give exactly one of eps or ranks")
@@ -318,7 +330,8 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
         direction = "RL" if variant == "URV" else "LR"
     v = ({"URV": TT_URV, "ULV": TT_ULV}[variant], {"RL": TT_RL, "LR": TT_LR}[direction])
     return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
-                  weights, stream, timing, orth, reverse, power_iters)
+                  weights, stream, timing, orth, reverse, power_iters, inner=inner,
+                  usvp_iters=usvp_iters)
 
 
 class _DevBuf:
@@ -424,13 +437,15 @@ def tt_utv_sharded(A_local, dims, comm, eps=None, ranks=None, variant="URV", dir
 
 
 def tt_svd(A, eps=None, ranks=None, direction="LR", precision="fp32", l_full=256, small="auto",
-           weights=None, stream=None):
-    """TT-SVD (the paper's comparison method) through the same sweep."""
+           weights=None, stream=None, oversample=16):
+    """TT-SVD (the paper's comparison method) through the same sweep.  A step
+    whose basis side exceeds ``l_full`` factors the projection onto a
+    Rademacher range of r + ``oversample`` columns (fixed ranks)."""
     if (eps is None) == (ranks is None):
         raise ValueError("give exactly one of eps or ranks")
     dr = {"LR": TT_LR, "RL": TT_RL}[direction]
-    return _sweep(lib().tt_svd, A, eps, ranks, (dr,), precision, 0, 16, l_full, small, weights,
-                  stream)
+    return _sweep(lib().tt_svd, A, eps, ranks, (dr,), precision, 0, oversample, l_full, small,
+                  weights, stream)
 
 
 def _core_meta(cores):
@@ -456,6 +471,28 @@ def tt_full(cores, stream=None):
         ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores])
         _check(lib().tt_full(d, D, R, ptrs, code, ctypes.c_void_p(out.data_ptr()),
                              ctypes.c_void_p(work.data_ptr()), st_ptr))
+    return out
+
+
+def tt_orthogonalize(cores, side="left", stream=None):
+    """The same TT tensor with left-orthogonal cores 1..d-1 (``side="left"``)
+    or right-orthogonal cores 2..d (``"right"``), by Cholesky-QR2 of each
+    core's unfolding (Def. 2.2; see tt_orthogonalize in ttutv.h)."""
+    d, dims, ranks = _core_meta(cores)
+    dtype = cores[0].dtype
+    cores = [g.contiguous() for g in cores]
+    st, st_ptr = _stream(stream)
+    code = TT_F64 if dtype == torch.float64 else TT_F32
+    D, R = _i64(dims), _i64(ranks)
+    nbytes = lib().tt_orthogonalize_work_bytes(d, D, R, code)
+    dev = cores[0].device
+    with torch.cuda.device(dev), torch.cuda.stream(st):
+        out = [torch.empty_like(g) for g in cores]
+        work = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=dev)
+        ptrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in cores])
+        optrs = (ctypes.c_void_p * d)(*[g.data_ptr() for g in out])
+        _check(lib().tt_orthogonalize(d, D, R, ptrs, code, {"left": 1, "right": 0}[side], optrs,
+                                      ctypes.c_void_p(work.data_ptr()), st_ptr))
     return out
 
 

@@ -20,8 +20,8 @@ tangent vector, takes the exact line-search step
 alpha_k = <P_Omega xi, P_Omega(X_k - M)> / <P_Omega xi, P_Omega xi>,
 forms X_k - alpha_k xi in full (a rank-2r block TT contracted by tt_full) and
 retracts it with a fixed-rank TT-URV, TT-ULV or TT-SVD sweep of the library.
-The other orthogonal frame of the new point comes from the opposite sweep of
-its full tensor (exact at its own ranks).
+The other orthogonal frame of the new point comes from tt_orthogonalize
+(Cholesky-QR2 of its cores' unfoldings, no pass over the full tensor).
 """
 from __future__ import annotations
 
@@ -29,7 +29,7 @@ import math
 
 import torch
 
-from . import EvalPlan, tt_full, tt_svd, tt_utv
+from . import EvalPlan, tt_full, tt_orthogonalize, tt_svd, tt_utv
 
 
 def complete(values, idx, shape, ranks, p_obs=None, steps=200, c1=1e-4, alpha0=1.0,
@@ -87,23 +87,33 @@ def complete(values, idx, shape, ranks, p_obs=None, steps=200, c1=1e-4, alpha0=1
     return cores, losses
 
 
+def sketch_widths(ranks):
+    """(l_full, oversample) of the retraction sweeps: the iterate X - alpha xi
+    has TT-ranks at most 2 r_k, so every unfolding whose basis side exceeds
+    l_full = 2 max(r) + 16 is sketched with l = r_k + max(r) + 16 >= 2 r_k + 16
+    columns, which hold its whole range (no range miss: TT-SVD stays exact)."""
+    rmax = max(ranks)
+    return 2 * rmax + 16, rmax + 16
+
+
 def _retract(full, ranks, method, precision, stream):
     """Fixed-rank decomposition of the full tensor: (cores, "left"|"right")."""
+    l_full, p = sketch_widths(ranks)
     if method == "SVD":
-        res = tt_svd(full, ranks=list(ranks), precision=precision, stream=stream)
+        res = tt_svd(full, ranks=list(ranks), precision=precision, stream=stream, l_full=l_full,
+                     oversample=p)
         return res.cores, res.orth
     if method not in ("URV", "ULV"):
         raise ValueError("retraction must be URV, ULV or SVD")
-    res = tt_utv(full, ranks=list(ranks), variant=method, precision=precision, stream=stream)
+    res = tt_utv(full, ranks=list(ranks), variant=method, precision=precision, stream=stream,
+                 l_full=l_full, oversample=p)
     return res.cores, res.orth
 
 
-def _other_frame(cores, orth, ranks, precision, stream):
-    """The opposite orthogonal frame of the same tensor (its ranks are exact)."""
-    full = tt_full(cores, stream)
-    variant = "ULV" if orth == "right" else "URV"
-    return tt_utv(full, ranks=list(ranks), variant=variant, precision=precision,
-                  stream=stream).cores
+def _other_frame(cores, orth, stream):
+    """The opposite orthogonal frame of the same tensor (Cholesky-QR2 of the
+    cores' unfoldings)."""
+    return tt_orthogonalize(cores, "left" if orth == "right" else "right", stream)
 
 
 def tangent_block_cores(U, V, dU, alpha=None):
@@ -167,7 +177,7 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
         losses.append(0.5 * float(torch.dot(z, z)))
         if t == steps:
             break
-        other = _other_frame(X, orth, ranks, precision, stream)
+        other = _other_frame(X, orth, stream)
         U, V = (other, X) if orth == "right" else (X, other)
         dU = plan.tangent_project(U, V, z, stream)
         xi = plan2.at(tangent_block_cores(U, V, dU), stream)

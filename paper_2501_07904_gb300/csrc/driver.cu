@@ -507,7 +507,9 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
 
     ttk::SmallParams prm;
     memset(&prm, 0, sizeof(prm));
-    prm.mode = cfg.svd ? ttk::SM_JACOBI : ttk::SM_QLP;
+    prm.mode = cfg.svd ? ttk::SM_JACOBI
+                       : (o.inner == TT_INNER_USVP ? ttk::SM_USVP : ttk::SM_QLP);
+    prm.usvp_iters = o.usvp_iters;
     prm.r_fixed = (int)rfix;
     prm.r_cap = (int)rcap;
     prm.delta2_scale = dscale;
@@ -1020,6 +1022,8 @@ tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims,
     return fail(TT_EINVAL, "bad orth_precision");
   if (o.reverse != 0 && o.reverse != 1) return fail(TT_EINVAL, "reverse must be 0 or 1");
   if (o.power_iters < 0 || o.power_iters > 8) return fail(TT_EINVAL, "power_iters must be in [0, 8]");
+  if (o.inner != TT_INNER_QLP && o.inner != TT_INNER_USVP) return fail(TT_EINVAL, "bad inner factor");
+  if (o.usvp_iters < 0 || o.usvp_iters > 64) return fail(TT_EINVAL, "usvp_iters must be in [0, 64]");
   if (o.weights) {
     double s = 0.0;
     for (int k = 0; k < d - 1; ++k) {
@@ -1169,6 +1173,8 @@ void tt_opts_default(tt_opts* o) {
   o->weights = nullptr;
   o->orth_precision = TT_SMALL_AUTO;
   o->phase_ms = nullptr;
+  o->inner = TT_INNER_QLP;
+  o->usvp_iters = 8;
 }
 
 tt_status tt_utv(const void* A, int32_t dtype, int32_t d, const int64_t* dims, double eps,
@@ -1279,6 +1285,195 @@ tt_status tt_full(int32_t d, const int64_t* dims, const int64_t* ranks, const vo
     rows *= dims[k];
   }
   return TT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Orthogonalization of TT cores (Def. 2.2) by Cholesky-QR2 of each core's
+// unfolding with FP64 Grams: left side, k = 1..d-1 in order, the unfolding
+// [r_{k-1} I_k] x [r_k] of R_{k-1} G_k (R_0 = 1) is replaced by Q_k and
+// R_k = Q_k^T (R_{k-1} G_k) is pushed into core k+1; right side, mirrored
+// with the row unfoldings [r_{k-1}] x [I_k r_k], k = d..2.
+struct OrthBufs {
+  size_t g, s, r, core, cb, ws, sws, info, total;
+};
+
+template <typename W>
+OrthBufs orth_layout(int32_t d, const int64_t* dims, const int64_t* ranks) {
+  OrthBufs b{};
+  int64_t rmax = 1, cmax = 1;
+  size_t ws = 0;
+  for (int k = 0; k < d; ++k) {
+    rmax = std::max<int64_t>(rmax, std::max(ranks[k], ranks[k + 1]));
+    cmax = std::max<int64_t>(cmax, ranks[k] * dims[k] * ranks[k + 1]);
+  }
+  for (int k = 0; k < d; ++k) {
+    const int64_t m = ranks[k] * dims[k], r = ranks[k + 1];  // left unfolding
+    const int64_t n = dims[k] * ranks[k + 1], q = ranks[k];   // right unfolding
+    const int64_t shapes[9][4] = {{r, r, m, 1}, {m, r, r, 0}, {r, m, r, 0}, {r, r, m, 0},
+                                  {q, q, n, 1}, {n, q, q, 0}, {q, n, q, 0}, {q, q, n, 0},
+                                  {m, q, q, 0}};
+    for (const auto& sh : shapes)
+      ws = std::max(ws, ttk::gemm_ws_bytes<W>(sh[0], sh[1], sh[2], sh[3] != 0));
+    if (k + 1 < d)  // the push into the next core
+      ws = std::max(ws, ttk::gemm_ws_bytes<W>(r, dims[k + 1] * ranks[k + 2], r, false));
+  }
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += align256(bytes);
+    return at;
+  };
+  b.g = take((size_t)rmax * rmax * sizeof(double));
+  b.s = take((size_t)rmax * rmax * sizeof(W));
+  b.r = take((size_t)rmax * rmax * sizeof(W));
+  b.cb = align256((size_t)cmax * sizeof(W));
+  b.core = take(3 * b.cb);
+  b.ws = take(ws);
+  b.sws = take(ttk::small_ws_bytes((int)rmax, true));
+  b.info = take(sizeof(ttk::StepInfo));
+  b.total = o;
+  return b;
+}
+
+// Q of the Cholesky-QR2 of the columns of X (rows x r, element (i, j) at
+// X(i, j) of the view), written through `store` (a row-major rows x r buffer
+// or, for the right side, the transposed view).  Pass 1 shifts the Gram by
+// 4 r u_64 of its trace so that a numerically rank-deficient unfolding stays
+// factorable; pass 2 restores orthonormality to the data's rounding.
+template <typename W>
+cudaError_t cholqr2(ttk::Mat<W> X, int64_t rows, int64_t r, W* t0, ttk::Mat<W> out_view,
+                    W* out_ptr, int64_t out_ld, char* base, const OrthBufs& b, cudaStream_t st) {
+  double* G = reinterpret_cast<double*>(base + b.g);
+  W* S = reinterpret_cast<W*>(base + b.s);
+  void* ws = base + b.ws;
+  ttk::SmallParams po;
+  memset(&po, 0, sizeof(po));
+  po.n = (int)r;
+  po.mode = ttk::SM_ORTH;
+  po.r_fixed = -1;
+  po.r_cap = (int)r;
+  const double u64 = 1.1102230246251565e-16;
+  ttk::Mat<W> cur = X;
+  for (int pass = 0; pass < 2; ++pass) {
+    // G = cur^T cur: A(i, j) = cur(j, i)
+    ttk::Mat<W> curT{cur.p, cur.ld, !cur.row};
+    cudaError_t e = ttk::gemm<W>(curT, cur, r, r, rows, nullptr, 0, G, true, nullptr, ws, st, true);
+    if (e != cudaSuccess) return e;
+    po.shift_rel = pass == 0 ? 4.0 * (double)r * u64 : 0.0;
+    po.piv_tol = pass == 0 ? 0.0 : 64.0 * (double)r * u64 * u64;
+    e = ttk::small_factor(G, po, true, S, std::is_same<W, double>::value, (int)r, base + b.sws,
+                          reinterpret_cast<ttk::StepInfo*>(base + b.info), st);
+    if (e != cudaSuccess) return e;
+    // next = cur S (rows x r)
+    if (pass == 0) {
+      e = ttk::gemm<W>(cur, {S, r, true}, rows, r, r, t0, r, nullptr, false, nullptr, ws, st);
+      cur = {t0, r, true};
+    } else if (out_view.row) {
+      e = ttk::gemm<W>(cur, {S, r, true}, rows, r, r, out_ptr, out_ld, nullptr, false, nullptr, ws,
+                       st);
+    } else {
+      // transposed output: out^T (r x rows) = S^T cur^T
+      e = ttk::gemm<W>({S, r, false}, {cur.p, cur.ld, !cur.row}, r, rows, r, out_ptr, out_ld,
+                       nullptr, false, nullptr, ws, st);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename W>
+tt_status orth_run(int32_t d, const int64_t* dims, const int64_t* ranks, const void* const* cores,
+                   int32_t side, void* const* out, void* work, cudaStream_t st) {
+  const OrthBufs b = orth_layout<W>(d, dims, ranks);
+  char* base = (char*)work;
+  W* R = reinterpret_cast<W*>(base + b.r);
+  W* buf[3] = {reinterpret_cast<W*>(base + b.core), reinterpret_cast<W*>(base + b.core + b.cb),
+               reinterpret_cast<W*>(base + b.core + 2 * b.cb)};
+  void* ws = base + b.ws;
+  cudaError_t e = cudaSuccess;
+  if (side == 1) {  // left-orthogonal cores 1..d-1
+    const W* M = (const W*)cores[0];
+    for (int k = 0; k + 1 < d; ++k) {
+      const int64_t m = ranks[k] * dims[k], r = ranks[k + 1];
+      W* Q = (W*)out[k];
+      e = cholqr2<W>({M, r, true}, m, r, buf[0], {Q, r, true}, Q, r, base, b, st);
+      if (e != cudaSuccess) return cuda_fail(e, "orthogonalize: Cholesky-QR");
+      // R_k = Q^T M, pushed into the next core
+      e = ttk::gemm<W>({Q, r, false}, {M, r, true}, r, r, m, R, r, nullptr, false, nullptr, ws, st);
+      if (e != cudaSuccess) return cuda_fail(e, "orthogonalize: R");
+      const int64_t N = dims[k + 1] * ranks[k + 2];
+      W* dst = (k + 2 == d) ? (W*)out[d - 1] : buf[1 + (k & 1)];
+      e = ttk::gemm<W>({R, r, true}, {(const W*)cores[k + 1], N, true}, r, N, r, dst, N, nullptr,
+                       false, nullptr, ws, st);
+      if (e != cudaSuccess) return cuda_fail(e, "orthogonalize: push");
+      M = dst;
+    }
+  } else {  // right-orthogonal cores 2..d
+    const W* M = (const W*)cores[d - 1];
+    for (int k = d - 1; k >= 1; --k) {
+      const int64_t q = ranks[k], n = dims[k] * ranks[k + 1];
+      W* Q = (W*)out[k];  // row-major q x n with orthonormal rows
+      e = cholqr2<W>({M, n, false}, n, q, buf[0], {Q, n, false}, Q, n, base, b, st);
+      if (e != cudaSuccess) return cuda_fail(e, "orthogonalize: Cholesky-QR");
+      // R_k = M Q^T, pushed into the previous core
+      e = ttk::gemm<W>({M, n, true}, {Q, n, false}, q, q, n, R, q, nullptr, false, nullptr, ws, st);
+      if (e != cudaSuccess) return cuda_fail(e, "orthogonalize: R");
+      const int64_t mrows = ranks[k - 1] * dims[k - 1];
+      W* dst = (k == 1) ? (W*)out[0] : buf[1 + (k & 1)];
+      e = ttk::gemm<W>({(const W*)cores[k - 1], q, true}, {R, q, true}, mrows, q, q, dst, q,
+                       nullptr, false, nullptr, ws, st);
+      if (e != cudaSuccess) return cuda_fail(e, "orthogonalize: push");
+      M = dst;
+    }
+  }
+  return TT_OK;
+}
+
+tt_status orth_validate(int32_t d, const int64_t* dims, const int64_t* ranks, int32_t dtype,
+                        int32_t side) {
+  if (d < 2 || d > TT_MAXD || !dims || !ranks) return fail(TT_EINVAL, "bad d, dims or ranks");
+  if (dtype != TT_F32 && dtype != TT_F64) return fail(TT_EINVAL, "bad dtype");
+  if (side != 0 && side != 1) return fail(TT_EINVAL, "side must be 0 (right) or 1 (left)");
+  if (ranks[0] != 1 || ranks[d] != 1) return fail(TT_EINVAL, "r_0 and r_d must be 1");
+  for (int k = 0; k < d; ++k) {
+    if (dims[k] < 1 || ranks[k + 1] < 1) return fail(TT_EINVAL, "dims and ranks must be >= 1");
+    if (ranks[k + 1] > ttk::kMaxSmall) return fail(TT_EINVAL, "ranks must be <= 256");
+    if (side == 1 && k + 1 < d && ranks[k + 1] > ranks[k] * dims[k])
+      return fail(TT_EINVAL, "r_k > r_{k-1} I_k: a left unfolding cannot be orthonormal");
+    if (side == 0 && k >= 1 && ranks[k] > dims[k] * ranks[k + 1])
+      return fail(TT_EINVAL, "r_{k-1} > I_k r_k: a right unfolding cannot be orthonormal");
+  }
+  return TT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tt_orthogonalize_work_bytes(int32_t d, const int64_t* dims, const int64_t* ranks,
+                                   int32_t dtype) {
+  if (d < 2 || d > TT_MAXD || !dims || !ranks) return 0;
+  return dtype == TT_F64 ? orth_layout<double>(d, dims, ranks).total
+                         : orth_layout<float>(d, dims, ranks).total;
+}
+
+tt_status tt_orthogonalize(int32_t d, const int64_t* dims, const int64_t* ranks,
+                           const void* const* cores, int32_t dtype, int32_t side, void* const* out,
+                           void* work, void* stream) {
+  g_err.clear();
+  const tt_status v = orth_validate(d, dims, ranks, dtype, side);
+  if (v != TT_OK) return v;
+  if (!cores || !out || !work) return fail(TT_EINVAL, "NULL argument");
+  for (int k = 0; k < d; ++k) {
+    if (!cores[k] || !out[k]) return fail(TT_EINVAL, "NULL core");
+    for (int j = 0; j < d; ++j)
+      if (out[k] == cores[j]) return fail(TT_EINVAL, "out must not alias the input cores");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  return dtype == TT_F64 ? orth_run<double>(d, dims, ranks, cores, side, out, work, st)
+                         : orth_run<float>(d, dims, ranks, cores, side, out, work, st);
 }
 
 }  // extern "C"

@@ -873,14 +873,16 @@ __global__ void eval_fixup_kernel(PassArgs a) {
 // ------------------------------------------------------------------ tangent gauge
 //
 // For an m x r left unfolding U with orthonormal columns and the increment Y
-// of the same shape: Y <- Y - U (U^T Y).  S = U^T Y is summed in FP64 by row
-// blocks (gauge_gram_kernel: block b takes rows [b*rows, (b+1)*rows) and
-// writes its partial), the partials in block order (gauge_reduce_kernel),
-// then every row is updated from S (gauge_apply_kernel).
+// of the same shape: Y <- Y - U (U^T Y).  S = U^T Y is summed by row blocks
+// (gauge_gram_kernel: block b takes rows [b*rows, (b+1)*rows) and writes its
+// partial; products in FP32 over 32-row tiles, the tiles' sums added in
+// FP64, since GB300 issues FP64 at 1/64 of the FP32 rate), the partials in
+// block order (gauge_reduce_kernel), then every row is updated from S in
+// FP64 (gauge_apply_kernel).
 
 constexpr int kGaugeThreads = 256;
-constexpr int kGaugeRows = 1024;    // rows per partial sum
-constexpr int kGaugeMaxBlocks = 64;
+constexpr int kGaugeRows = 128;     // rows per partial sum
+constexpr int kGaugeMaxBlocks = 152;
 constexpr int kGaugeTile = 32;      // rows staged per round
 
 int gauge_blocks(int64_t m) {
@@ -910,9 +912,9 @@ __global__ void __launch_bounds__(kGaugeThreads) gauge_gram_kernel(const float* 
       const int e = t + j * kGaugeThreads;
       if (e < rr) {
         const int a = e / r, b = e - a * r;
-        double v = acc[j];
-        for (int q = 0; q < nr; ++q) v = fma((double)us[q * r + a], (double)ys[q * r + b], v);
-        acc[j] = v;
+        float v = 0.0f;
+        for (int q = 0; q < nr; ++q) v = fmaf(us[q * r + a], ys[q * r + b], v);
+        acc[j] += (double)v;
       }
     }
   }

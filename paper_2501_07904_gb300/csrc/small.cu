@@ -20,6 +20,14 @@
 //             passes make the columns orthonormal to working precision
 //             (shifted Cholesky-QR3).  A column with no positive pivot even
 //             then (an exactly dependent column) is dropped: zero in S.
+//  SM_USVP    USV-plus-style deflation (the inner factor the paper runs in
+//             TT-ULV, Sec. 4): basis vectors one at a time, each from the
+//             column of largest norm of the deflated matrix D = X (I - V V^T)
+//             followed by q power iterations v <- D^T D v / ||.||, then
+//             re-orthogonalized twice against V.  D^T D is kept explicitly
+//             (the Gram, deflated after each vector by a rank-two update), so
+//             the error of rank i is mu^2 + trace(D^T D).  Stops at the
+//             fixed rank, or at the first i >= 1 with error <= delta^2.
 #include <math.h>
 
 #include "internal.h"
@@ -414,6 +422,152 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
         z = V[i * n + order[c]];
       }
       Z[(size_t)i * ldz + c] = (ZT)z;
+    }
+    return;
+  }
+
+  if (prm.mode == SM_USVP) {
+    __shared__ T sv[kMaxSmall];
+    T* Vb = Mq;            // basis, column c at Vb[i * n + c]
+    T* w = Qe;             // n
+    T* cf = Qe + n;        // n
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    const int rmax = fixed ? rt : min(prm.r_cap, n);
+    const int q = max(0, prm.usvp_iters);
+    // w = A v (A: the deflated Gram, global; v in sv), one warp per row
+    auto matvec = [&]() {
+      for (int i = warp; i < n; i += nwarps) {
+        T acc = T(0);
+        for (int c = lane; c < n; c += 32) acc += A[i * n + c] * sv[c];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) w[i] = acc;
+      }
+      __syncthreads();
+    };
+    // sv <- src / ||src|| (returns ||src||^2)
+    auto normalize_from = [&](const T* src) -> T {
+      T s = T(0);
+      for (int i = tid; i < n; i += nt) s += src[i] * src[i];
+      s = block_sum(s, redt);
+      const T inv = s > T(0) ? T(1) / sqrt(s) : T(0);
+      for (int i = tid; i < n; i += nt) sv[i] = src[i] * inv;
+      __syncthreads();
+      return s;
+    };
+    // sv <- sv - V (V^T sv), twice, for the first r basis columns
+    auto reorth = [&](int r) {
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int c = tid; c < r; c += nt) {
+          T acc = T(0);
+          for (int i = 0; i < n; ++i) acc += Vb[i * n + c] * sv[i];
+          cf[c] = acc;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += nt) {
+          T acc = sv[i];
+          for (int c = 0; c < r; ++c) acc -= Vb[i * n + c] * cf[c];
+          w[i] = acc;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += nt) sv[i] = w[i];
+        __syncthreads();
+      }
+    };
+    double tail = mu2 + tr;
+    if (tid == 0) info->tails[0] = tail;
+    int r = 0;
+    while (r < rmax) {
+      if (!fixed && r >= 1 && tail <= delta2) break;
+      T best = lowest_value<T>();
+      int bi = 0x7fffffff;
+      for (int i = tid; i < n; i += nt) {
+        const T a = A[i * n + i];
+        if (a > best) {
+          best = a;
+          bi = i;
+        }
+      }
+      T dmax;
+      int j;
+      block_argmax(best, bi, redt, redi, dmax, j);
+      bool ok = dmax > T(0);
+      if (ok) {
+        // start: D^T D e_j (row j of the symmetric deflated Gram)
+        for (int i = tid; i < n; i += nt) w[i] = A[j * n + i];
+        __syncthreads();
+        ok = normalize_from(w) > T(0);
+        for (int it = 0; ok && it < q; ++it) {
+          matvec();
+          if (!(normalize_from(w) > T(0))) {
+            // D^T D v = 0: keep the previous v (restored from the basis-free copy)
+            for (int i = tid; i < n; i += nt) w[i] = A[j * n + i];
+            __syncthreads();
+            normalize_from(w);
+            break;
+          }
+        }
+        if (ok) {
+          reorth(r);
+          for (int i = tid; i < n; i += nt) w[i] = sv[i];
+          __syncthreads();
+          ok = normalize_from(w) > T(0);
+        }
+      }
+      if (!ok) {
+        if (!fixed) break;  // nothing left to capture
+        // complete the fixed rank with unit vectors orthogonal to V
+        bool found = false;
+        for (int cand = 0; cand < n && !found; ++cand) {
+          for (int i = tid; i < n; i += nt) sv[i] = (i == cand) ? T(1) : T(0);
+          __syncthreads();
+          reorth(r);
+          for (int i = tid; i < n; i += nt) w[i] = sv[i];
+          __syncthreads();
+          found = normalize_from(w) > T(0.25);
+        }
+        if (!found) break;
+      }
+      // deflate: u = A v, lam = v^T u, A <- A - v u^T - u v^T + lam v v^T
+      matvec();
+      T lam = T(0);
+      for (int i = tid; i < n; i += nt) lam += sv[i] * w[i];
+      lam = block_sum(lam, redt);
+      for (int e = tid; e < n * n; e += nt) {
+        const int i = e / n, c = e % n;
+        A[e] = A[e] - sv[i] * w[c] - w[i] * sv[c] + lam * sv[i] * sv[c];
+      }
+      for (int i = tid; i < n; i += nt) Vb[i * n + r] = sv[i];
+      __syncthreads();
+      double t2 = 0.0;
+      for (int i = tid; i < n; i += nt) t2 += (double)A[i * n + i];
+      t2 = block_sum(t2, redd);
+      tail = mu2 + fmax(t2, 0.0);
+      ++r;
+      if (tid == 0) info->tails[r] = tail;
+    }
+    if (r == 0) {  // a zero matrix: one unit vector (rank >= 1)
+      for (int i = tid; i < n; i += nt) Vb[i * n] = (i == 0) ? T(1) : T(0);
+      r = 1;
+      if (tid == 0) info->tails[1] = tail;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * ldz; e += nt) {
+      const int i = e / ldz, c = e % ldz;
+      T z = T(0);
+      if (c < r) {
+        if (prm.Gw)
+          for (int k = i; k < n; ++k) z += Ti[i * n + k] * Vb[k * n + c];
+        else
+          z = Vb[i * n + c];
+      }
+      Z[(size_t)i * ldz + c] = (ZT)z;
+    }
+    if (tid == 0) {
+      info->r = r;
+      info->k1 = r;
+      info->nsteps = r;
+      info->s1 = 0.0;
+      info->tail = tail;
     }
     return;
   }

@@ -248,6 +248,15 @@ def test_eval_plan_arguments_rejected(L):
     assert L.tt_eval_plan_backward(None, ptrs, ctypes.c_void_p(1), ptrs, None) == 1
     assert L.tt_eval_plan_backward_mixed(None, ptrs, ptrs, ctypes.c_void_p(1), ptrs, None) == 1
     assert L.tt_tangent_project(None, ptrs, ptrs, ctypes.c_void_p(1), ptrs, None) == 1
+    # orthogonalization: d, dtype, side, rank and aliasing checks (no kernel runs)
+    D, R = tu._i64([3, 4]), tu._i64([1, 2, 1])
+    w = ctypes.c_void_p(1)
+    assert L.tt_orthogonalize(1, D, R, ptrs, 0, 1, ptrs, w, None) == 1
+    assert L.tt_orthogonalize(2, D, R, ptrs, 5, 1, ptrs, w, None) == 1
+    assert L.tt_orthogonalize(2, D, R, ptrs, 0, 2, ptrs, w, None) == 1
+    assert L.tt_orthogonalize(2, D, tu._i64([1, 4, 1]), ptrs, 0, 1, ptrs, w, None) == 1
+    assert L.tt_orthogonalize(2, D, R, ptrs, 0, 1, ptrs, w, None) == 1   # out aliases cores
+    assert L.tt_orthogonalize_work_bytes(2, D, R, 0) > 0
     L.tt_eval_plan_destroy(None, None)
     assert L.tt_eval_plan_device_bytes(None) == 0
 

@@ -107,6 +107,65 @@ def test_tangent_projection_matches_oracle(tu, name):
             assert np.abs(m.T @ gk).max() <= 1e-5 * np.abs(Y[k]).max()
 
 
+def _interfaces(cores, side):
+    """Gauge-invariant spans: the projectors onto the column spaces of the
+    left interfaces G_1..G_k ((I_1..I_k) x r_k) or onto the row spaces of the
+    right interfaces G_k..G_d (r_{k-1} x (I_k..I_d))."""
+    out = []
+    d = len(cores)
+    if side == "left":
+        L = np.ones((1, 1))
+        for k in range(d - 1):
+            g = cores[k]
+            L = (L @ g.reshape(g.shape[0], -1)).reshape(-1, g.shape[2])
+            out.append(L)
+    else:
+        R = np.ones((1, 1))
+        for k in range(d - 1, 0, -1):
+            g = cores[k]
+            R = (g.reshape(-1, g.shape[2]) @ R).reshape(g.shape[0], -1)
+            out.append(R.T)
+    return out
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_orthogonalize_matches_oracle(tu, dtype):
+    """Both sides, against the oracle's Householder frames: the same tensor,
+    orthonormal unfoldings, and the same nested interface spans (a
+    left-orthogonal TT is unique up to an orthogonal change of basis between
+    neighbouring cores, so the spans are what is unique); the shape has a
+    rank-64 core whose left unfolding is square."""
+    dims, ranks = (8, 8, 8, 8), (1, 8, 64, 8, 1)
+    X = [np.asarray(c, np.float64) / np.sqrt(c.shape[0]) for c in
+         synth.gaussian_cores(dims, ranks, seed=90)]
+    Xd = [c.astype(dtype) for c in X]
+    X64 = [c.astype(np.float64) for c in Xd]
+    full = otc.tt_full(X64)
+    tol = 1e-5 if dtype == np.float32 else 1e-12
+    for side, ref in (("left", org.left_orthogonal(X64)), ("right", org.right_orthogonal(X64))):
+        got = [g.double().cpu().numpy() for g in tu.tt_orthogonalize(_dev(Xd), side)]
+        assert np.abs(otc.tt_full(got) - full).max() <= tol * np.abs(full).max(), side
+        ks = range(len(dims) - 1) if side == "left" else range(1, len(dims))
+        for k in ks:
+            if side == "left":
+                a = got[k].reshape(-1, ranks[k + 1])
+            else:
+                a = got[k].reshape(ranks[k], -1).T
+            assert np.abs(a.T @ a - np.eye(a.shape[1])).max() <= tol, (side, k)
+        for a, b in zip(_interfaces(got, side), _interfaces(ref, side)):
+            assert np.abs(a @ a.T - b @ b.T).max() <= 10 * tol, side
+
+
+def test_orthogonalize_rejects_bad_arguments(tu):
+    g = [torch.zeros(1, 3, 5, device="cuda"), torch.zeros(5, 2, 1, device="cuda")]
+    with pytest.raises(tu.TTError) as ei:      # r_1 = 5 > r_0 I_1 = 3
+        tu.tt_orthogonalize(g, "left")
+    assert ei.value.status == tu.TT_EINVAL
+    with pytest.raises(tu.TTError) as ei:      # r_1 = 5 > I_2 r_2 = 2
+        tu.tt_orthogonalize(g, "right")
+    assert ei.value.status == tu.TT_EINVAL
+
+
 def test_tangent_projection_empty_index_set(tu):
     dims, ranks = (4, 5, 3), (1, 2, 3, 1)
     L, R = _frames32(dims, ranks, 84)
