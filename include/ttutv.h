@@ -6,8 +6,10 @@
  * TT-URV right-to-left (Alg. 3 and its prescribed-accuracy analogue,
  * Sec. 3.2), TT-ULV left-to-right (Alg. 1 and Alg. 2, Sec. 3.1), and TT-SVD
  * (the paper's comparison method, Sec. 4), plus contraction of a TT back to a
- * full tensor (Eq. TT) and masked evaluation of a TT with its gradient (the
- * observation operator P_Omega of the completion experiment, Sec. 4.2.2).
+ * full tensor (Eq. TT), orthogonalization of TT cores (Def. 2.2), and masked
+ * evaluation of a TT with its gradient and the tangent-space projection of
+ * the Riemannian gradient (the observation operator P_Omega and the solver
+ * of the completion experiment, Sec. 4.2.2).
  *
  * Conventions shared by every entry point
  * ---------------------------------------

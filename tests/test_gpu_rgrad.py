@@ -221,7 +221,7 @@ def test_rgrad_c4_retractions(tu):
     spectral initialisation.  The loss falls, the error on the full volume
     falls, and both TT-UTV retractions end at an RSE no worse than the TT-SVD
     retraction's (Sec. 4.2.2 finds them as effective; on this volume TT-URV
-    reached 0.040, TT-ULV 0.091 and TT-SVD 0.123 after 40 iterations)."""
+    reached 0.043, TT-ULV 0.046 and TT-SVD 0.070 after 40 iterations)."""
     from paper_2501_07904_gb300.completion import rgrad
 
     cfg = synth.CONFIGS["c4"]
