@@ -811,6 +811,12 @@ bool make_plan(int64_t M, int64_t N, int64_t K, bool sym, bool out64, bool a_spl
   a.all_partial = (sym || out64) ? 1 : 0;
   int64_t G = std::min<int64_t>((int64_t)sms, std::max<int64_t>(1, ceil_div(a.total, 4)));
   if (a.all_partial) {
+    // Every CTA leaves a kBM x nreg partial for the fix-up to sum: at least
+    // 8 k-blocks per CTA, so that a short product (a Cholesky-QR Gram of a
+    // few MB) writes and re-reads fewer partials than it reads operands
+    // (16 k-blocks per CTA was slower: the split operand's conversion bounds
+    // a CTA's rate)
+    G = std::min<int64_t>(G, std::max<int64_t>(1, ceil_div(a.total, 8)));
     // each CTA range no longer than a tile: at most two tiles (partial slots) per CTA
     G = std::max<int64_t>(G, a.ntiles);
     if (G > sms) return false;
@@ -950,7 +956,12 @@ cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K,
   else
     e = launch<128, 1>(p, ma, mb, d, slot, st);
   if (e != cudaSuccess) return e;
-  const bool need_fix = a.all_partial || a.G > 1;
+  // without FP64 output or a Gram, the fix-up only sums tiles that a CTA
+  // boundary splits: none when every boundary falls on a tile edge
+  bool split_tile = false;
+  for (int b = 1; b < a.G && !split_tile; ++b)
+    split_tile = ((int64_t)b * a.total / a.G) % a.kb != 0;
+  const bool need_fix = a.all_partial || (a.G > 1 && split_tile);
   const unsigned fg_y = a.all_partial ? kBM : 16;
   if (need_fix) {
     ++nl;
@@ -997,5 +1008,7 @@ cudaError_t wait_selftest(bool arrive, uint64_t limit_ns, int* err, cudaStream_t
   wait_selftest_kernel<<<1, 32, 0, st>>>(arrive ? 1 : 0, limit_ns, err);
   return cudaGetLastError();
 }
+
+TT_BOUNDS_READER(bounds_tc_gemm)
 
 }  // namespace ttk
