@@ -448,6 +448,18 @@ tt_status tt_sketch_matrix(int64_t rows, int64_t cols, uint64_t seed, int32_t st
  * context stays usable).  Synchronizes `stream`. */
 tt_status tt_wait_selftest(int32_t arrive, int64_t limit_ns, void* stream);
 
+/* Bounds-checked build (compiled with -DTT_BOUNDS_CHECK; build.py --checked
+ * makes libttutv_bc.so): every checked device access whose index falls
+ * outside its buffer is skipped and counted instead of performed (indices
+ * read from data -- the masked evaluation's decoded indices, permutations
+ * and positions -- core slices, tensor-map coordinates and their 16-byte
+ * alignment, gathered copies).  Returns the number of violations counted
+ * since the last reset (the device counters of every translation unit,
+ * read with a synchronizing copy), the source line of the first in
+ * *first_line (may be NULL), and zeroes the counters when reset != 0.
+ * Returns -1 from the normal build. */
+int64_t tt_bounds_violations(int32_t* first_line, int32_t reset);
+
 /* Number of kernels this library has launched in the process so far
  * (all threads); a diagnostic for counting launches per call. */
 uint64_t tt_kernel_launches(void);

@@ -22,7 +22,9 @@ from dataclasses import dataclass, field
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libttutv.so")
+# TTUTV_CHECKED=1 loads the bounds-checked build (libttutv_bc.so) instead
+LIB_PATH = os.path.join(_PKG, "libttutv_bc.so" if os.environ.get("TTUTV_CHECKED") == "1"
+                        else "libttutv.so")
 TT_MAXD = 16
 
 STATUS = {0: "TT_OK", 1: "TT_EINVAL", 2: "TT_ENONFINITE", 3: "TT_ENOMEM", 4: "TT_ECUDA",
@@ -43,7 +45,8 @@ EXPORTS = ["tt_opts_default", "tt_utv", "tt_utv_sharded", "tt_svd", "tt_result_f
            "tt_rse", "tt_eval_plan_create", "tt_eval_plan_destroy", "tt_eval_plan_device_bytes",
            "tt_eval_plan_at", "tt_eval_plan_backward", "tt_eval_plan_backward_mixed",
            "tt_tangent_project", "tt_eval_at",
-           "tt_eval_at_backward", "tt_sketch_matrix", "tt_wait_selftest", "tt_kernel_launches",
+           "tt_eval_at_backward", "tt_sketch_matrix", "tt_wait_selftest", "tt_bounds_violations",
+           "tt_kernel_launches",
            "tt_last_error",
            "tt_version"]
 PHASES = ["gram", "small", "carry", "core", "sketch", "orth", "project"]
@@ -159,6 +162,8 @@ def lib():
     L.tt_wait_selftest.argtypes = [I32, I64, P]
     L.tt_wait_selftest.restype = I32
     L.tt_kernel_launches.argtypes = []
+    L.tt_bounds_violations.argtypes = [ctypes.POINTER(I32), I32]
+    L.tt_bounds_violations.restype = I64
     L.tt_kernel_launches.restype = ctypes.c_uint64
     L.tt_last_error.argtypes = []
     L.tt_last_error.restype = ctypes.c_char_p
@@ -765,6 +770,14 @@ def wait_selftest(arrive, limit_ns=50_000_000, stream=None):
 
 def version():
     return lib().tt_version().decode()
+
+
+def bounds_violations(reset=False):
+    """(count, first source line) of the bounds-checked build's skipped
+    out-of-range accesses since the last reset; count -1 from the normal build."""
+    line = ctypes.c_int32(0)
+    n = lib().tt_bounds_violations(ctypes.byref(line), 1 if reset else 0)
+    return int(n), int(line.value)
 
 
 def kernel_launches():

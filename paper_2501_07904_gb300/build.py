@@ -18,6 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libttutv.so")
+# the bounds-checked variant (-DTT_BOUNDS_CHECK), built beside it
+BUILD_BC = os.path.join(PKG, "_build_bc")
+LIB_BC = os.path.join(PKG, "libttutv_bc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
@@ -41,16 +44,20 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False):
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, checked=False):
+    """Compile and link the library; checked=True builds the bounds-checked
+    variant libttutv_bc.so (-DTT_BOUNDS_CHECK) in its own folder."""
+    bdir, lib = (BUILD_BC, LIB_BC) if checked else (BUILD, LIB)
+    flags = FLAGS + (["-DTT_BOUNDS_CHECK"] if checked else [])
+    os.makedirs(bdir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "ttutv.h"))
     jobs = []
     for src in sources():
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src[:-3] + ".o")
+        o = os.path.join(bdir, src[:-3] + ".o")
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o])
+            jobs.append([nvcc(), *ARCH, *flags, "-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             for cmd, res in zip(jobs, ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs)):
@@ -58,14 +65,14 @@ def build(force=False, verbose=False):
                     raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + res.stdout + res.stderr)
                 if verbose and res.stderr:
                     print(res.stderr, file=sys.stderr)
-    objs = [os.path.join(BUILD, s[:-3] + ".o") for s in sources()]
-    if force or jobs or _stale(LIB, objs):
-        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs]
+    objs = [os.path.join(bdir, s[:-3] + ".o") for s in sources()]
+    if force or jobs or _stale(lib, objs):
+        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", lib, *objs]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + res.stdout + res.stderr)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

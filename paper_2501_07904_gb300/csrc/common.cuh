@@ -7,6 +7,44 @@ namespace ttk {
 
 constexpr int kMaxSmall = 256;  // largest Gram / sketch side factored by one CTA
 
+// Bounds-checked build (-DTT_BOUNDS_CHECK): TT_IN(i, n) is false when i lies
+// outside [0, n), and then counts the violation (and the source line of the
+// first one) in this translation unit's device words; the caller skips the
+// access, so the kernel goes on and the host reads the count through
+// tt_bounds_violations.  Without the flag TT_IN is the constant true.
+#ifdef TT_BOUNDS_CHECK
+static __device__ unsigned int g_bc_count;
+static __device__ int g_bc_line;
+__device__ __forceinline__ bool bc_in(long long i, long long n, int line) {
+  if (i >= 0 && i < n) return true;
+  if (atomicAdd(&g_bc_count, 1u) == 0u) g_bc_line = line;
+  return false;
+}
+#define TT_IN(i, n) (::ttk::bc_in((long long)(i), (long long)(n), __LINE__))
+// This translation unit's count (and first line); reset zeroes it.
+static inline unsigned int bc_read_tu(int* line, bool reset) {
+  unsigned int c = 0;
+  int l = 0;
+  cudaMemcpyFromSymbol(&c, g_bc_count, sizeof c);
+  cudaMemcpyFromSymbol(&l, g_bc_line, sizeof l);
+  if (reset) {
+    const unsigned int z = 0;
+    cudaMemcpyToSymbol(g_bc_count, &z, sizeof z);
+  }
+  if (line) *line = l;
+  return c;
+}
+#define TT_BOUNDS_READER(name) \
+  unsigned int name(int* line, bool reset) { return bc_read_tu(line, reset); }
+#else
+#define TT_IN(i, n) true
+#define TT_BOUNDS_READER(name)                    \
+  unsigned int name(int* line, bool /*reset*/) {  \
+    if (line) *line = 0;                          \
+    return 0u;                                    \
+  }
+#endif
+
 // Result of one small factorization, written by the single-CTA kernels and
 // copied to the host once per sweep step (the next step's shapes need r).
 struct StepInfo {

@@ -1158,6 +1158,7 @@ tt_status sweep_entry(const void* A, int32_t dtype, int32_t d, const int64_t* di
 
 namespace ttk {
 void set_last_error(const char* msg) { g_err = msg; }
+TT_BOUNDS_READER(bounds_driver)
 }  // namespace ttk
 
 extern "C" {
@@ -1562,6 +1563,28 @@ tt_status tt_sketch_matrix(int64_t rows, int64_t cols, uint64_t seed, int32_t st
                                    (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "tt_sketch_matrix");
   return TT_OK;
+}
+
+int64_t tt_bounds_violations(int32_t* first_line, int32_t reset) {
+#ifdef TT_BOUNDS_CHECK
+  unsigned int (*const readers[])(int*, bool) = {
+      ttk::bounds_driver, ttk::bounds_gemm,       ttk::bounds_masked, ttk::bounds_misc,
+      ttk::bounds_small,  ttk::bounds_small_fast, ttk::bounds_tc_gemm};
+  int64_t total = 0;
+  int32_t line = 0;
+  for (auto rd : readers) {
+    int l = 0;
+    const unsigned int c = rd(&l, reset != 0);
+    if (c && !line) line = l;
+    total += c;
+  }
+  if (first_line) *first_line = line;
+  return total;
+#else
+  (void)reset;
+  if (first_line) *first_line = 0;
+  return -1;
+#endif
 }
 
 tt_status tt_wait_selftest(int32_t arrive, int64_t limit_ns, void* stream) {

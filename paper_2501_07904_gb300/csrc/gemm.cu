@@ -390,4 +390,6 @@ template cudaError_t gemm<float>(Mat<float>, Mat<float>, int64_t, int64_t, int64
 template cudaError_t gemm<double>(Mat<double>, Mat<double>, int64_t, int64_t, int64_t, double*,
                                   int64_t, double*, bool, double*, void*, cudaStream_t, bool);
 
+TT_BOUNDS_READER(bounds_gemm)
+
 }  // namespace ttk

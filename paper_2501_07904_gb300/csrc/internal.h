@@ -132,4 +132,13 @@ cudaError_t diff_sumsq(const void* a, const void* x, bool fp64, int64_t n, doubl
                        bool first, cudaStream_t st);
 cudaError_t sum_pairs(const double* part, double* out, cudaStream_t st);
 
+// Bounds-check counters of each translation unit (zero without -DTT_BOUNDS_CHECK).
+unsigned int bounds_driver(int* line, bool reset);
+unsigned int bounds_gemm(int* line, bool reset);
+unsigned int bounds_masked(int* line, bool reset);
+unsigned int bounds_misc(int* line, bool reset);
+unsigned int bounds_small(int* line, bool reset);
+unsigned int bounds_small_fast(int* line, bool reset);
+unsigned int bounds_tc_gemm(int* line, bool reset);
+
 }  // namespace ttk

@@ -1074,6 +1074,8 @@ cudaError_t configure_once() {
   return st;
 }
 
+TT_BOUNDS_READER(bounds_masked)
+
 }  // namespace ttk
 
 struct tt_eval_plan {

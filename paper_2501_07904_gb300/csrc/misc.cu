@@ -339,4 +339,6 @@ cudaError_t sum_pairs(const double* part, double* out, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+TT_BOUNDS_READER(bounds_misc)
+
 }  // namespace ttk

@@ -730,4 +730,6 @@ cudaError_t small_factor(const double* G, SmallParams prm, bool fp64_math, void*
                 : launch_small<float, float>(G, prm, Z, ldz, ws, info, st);
 }
 
+TT_BOUNDS_READER(bounds_small)
+
 }  // namespace ttk

@@ -863,4 +863,6 @@ cudaError_t small_factor_fast(const double* G, SmallParams prm, bool fp64_math, 
                 : launch_fast<float, float>(G, prm, Z, ldz, ws, info, st);
 }
 
+TT_BOUNDS_READER(bounds_small_fast)
+
 }  // namespace ttk
