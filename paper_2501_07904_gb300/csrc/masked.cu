@@ -573,16 +573,25 @@ __global__ void __launch_bounds__(kEvalThreads, 5) eval_pass_kernel(PassArgs a) 
   const int cnt = (int)min((int64_t)kChunk, a.n - p0);
   int32_t* posA = reinterpret_cast<int32_t*>(gs + kChunk);  // [kChunk] (mode 1)
   int32_t* posB = posA + kChunk;                              // [kChunk] (mode 1)
+  // (bounds-checked build: an entry id, mode index or position read from the
+  // plan outside its range is counted and replaced by 0, so every later
+  // access of the pass stays inside its buffer)
   for (int p = t; p < cnt; p += kEvalThreads) {
-    const int e = a.perm[p0 + p];
+    int e = a.perm[p0 + p];
+    if (!TT_IN(e, a.n)) e = 0;
     if (a.mode >= 2) {  // the given rows replace the chains: only i_k is needed
-      ixs[k * kChunk + p] = a.ix[(int64_t)k * a.n + e];
+      const int v = a.ix[(int64_t)k * a.n + e];
+      ixs[k * kChunk + p] = TT_IN(v, a.dims[k]) ? v : 0;
     } else {
-      for (int j = 0; j < d; ++j) ixs[j * kChunk + p] = a.ix[(int64_t)j * a.n + e];
+      for (int j = 0; j < d; ++j) {
+        const int v = a.ix[(int64_t)j * a.n + e];
+        ixs[j * kChunk + p] = TT_IN(v, a.dims[j]) ? v : 0;
+      }
       if (a.backward) gs[p] = a.gout[e];
       if (a.mode == 1) {
-        posA[p] = a.pos1[e];
-        posB[p] = a.pos3[e];
+        const int pa = a.pos1[e], pb = a.pos3[e];
+        posA[p] = TT_IN(pa, a.n) ? pa : 0;
+        posB[p] = TT_IN(pb, a.n) ? pb : 0;
       }
     }
   }
@@ -703,7 +712,8 @@ __global__ void __launch_bounds__(kEvalThreads, 5) eval_pass_kernel(PassArgs a) 
             }
           }
         }
-        a.out[a.perm[p0 + p]] = x;
+        const int o = a.perm[p0 + p];
+        if (TT_IN(o, a.n)) a.out[o] = x;
       }
       __syncthreads();
     }
@@ -859,7 +869,10 @@ __global__ void eval_fixup_kernel(PassArgs a) {
   const int k = a.k, rL = a.ranks[k], rR = a.ranks[k + 1], rRp = round4_dev(rR);
   const int rLp = round4_dev(rL), I = a.dims[k];
   const int64_t last = min(a.n, (c + 1) * kChunk) - 1;
-  const int i = a.ix[(int64_t)k * a.n + a.perm[last]];
+  int el = a.perm[last];
+  if (!TT_IN(el, a.n)) el = 0;
+  int i = a.ix[(int64_t)k * a.n + el];
+  if (!TT_IN(i, I)) i = 0;
   for (int e = threadIdx.x; e < rLp * rRp; e += blockDim.x) {
     const int q = e / rRp, b = e % rRp;
     if (q >= rL || b >= rR) continue;

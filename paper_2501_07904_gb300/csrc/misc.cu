@@ -88,7 +88,8 @@ __global__ void unshard_cols_kernel(const T* __restrict__ in, T* __restrict__ ou
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t t = e % blk, o = (e / blk) % outer, i = (e / nl) % rows, p = e / (nl * rows);
-    out[i * (outer * P * blk) + o * P * blk + p * blk + t] = in[e];
+    const int64_t dst = i * (outer * P * blk) + o * P * blk + p * blk + t;
+    if (TT_IN(dst, total)) out[dst] = in[e];
   }
 }
 
@@ -101,6 +102,7 @@ struct RevArgs {
   int64_t mid_out[kMaxModes];  // output stride of each middle mode
   int64_t s_in1, s_outd;       // input stride of mode 1, output stride of mode d
   int64_t nmidtot, t1, td;     // middle index count; tiles along modes 1 and d
+  int64_t total;               // elements of the tensor (bounds-checked build)
 };
 
 // out[i_d, ..., i_1] = in[i_1, ..., i_d], both row-major.  A block moves one
@@ -124,12 +126,14 @@ __global__ void __launch_bounds__(256) reverse_modes_kernel(const T* __restrict_
     }
     for (int q = ty; q < 32; q += 8) {
       const int64_t i1 = t1i * 32 + q, id = tdi * 32 + tx;
-      if (i1 < a.i1 && id < a.id) tile[q][tx] = in[i1 * a.s_in1 + mi + id];
+      const int64_t src = i1 * a.s_in1 + mi + id;
+      if (i1 < a.i1 && id < a.id && TT_IN(src, a.total)) tile[q][tx] = in[src];
     }
     __syncthreads();
     for (int q = ty; q < 32; q += 8) {
       const int64_t id = tdi * 32 + q, i1 = t1i * 32 + tx;
-      if (i1 < a.i1 && id < a.id) out[id * a.s_outd + mo + i1] = tile[tx][q];
+      const int64_t dst = id * a.s_outd + mo + i1;
+      if (i1 < a.i1 && id < a.id && TT_IN(dst, a.total)) out[dst] = tile[tx][q];
     }
     __syncthreads();
   }
@@ -145,7 +149,8 @@ __global__ void swap_outer_kernel(const T* __restrict__ in, T* __restrict__ out,
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t a = e % A, rest = e / A;
     const int64_t i = rest % I, b = rest / I;
-    out[e] = in[(a * I + i) * B + b];
+    const int64_t src = (a * I + i) * B + b;
+    if (TT_IN(src, total)) out[e] = in[src];
   }
 }
 
@@ -295,6 +300,7 @@ cudaError_t reverse_modes(const void* in, void* out, bool fp64, int d, const int
   a.s_outd = sout[d - 1];
   a.t1 = (a.i1 + 31) / 32;
   a.td = (a.id + 31) / 32;
+  a.total = a.i1 * a.nmidtot * a.id;
   const int64_t ntiles = a.nmidtot * a.t1 * a.td;
   if (ntiles <= 0) return cudaSuccess;
   const int g = (int)std::min<int64_t>(ntiles, (int64_t)kGrid * 2);

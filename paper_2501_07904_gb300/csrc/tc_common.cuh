@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "common.cuh"
+
 namespace ttk {
 namespace tc {
 
@@ -86,6 +88,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // the innermost (contiguous) coordinate.  Out-of-range elements read as zero.
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t c0, int32_t c1,
                                             uint64_t* bar) {
+  // bounds-checked build: an innermost coordinate that is negative or not on a
+  // 16-byte boundary (4 FP32 elements) is counted and the copy skipped; the
+  // consumer's bounded wait then reports TT_ETIMEOUT
+  if (!TT_IN(c0 & 3, 1) || !TT_IN(c0, 0x7fffffff)) return;
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
       "%3}], [%4];" ::"r"(smem_u32(dst)),
