@@ -128,8 +128,22 @@ typedef struct {
                                TT_INNER_QLP; ignored by tt_svd */
   int32_t usvp_iters;       /* TT_INNER_USVP: power iterations per basis vector, in [0, 64],
                                default 8 */
-  int32_t pad2_;
+  int32_t lhat;             /* tt_lhat: the kept middle block of TT-ULV right-to-left (the
+                               appendix's Alg. 4), default TT_LHAT_FULL */
 } tt_opts;
+
+/* Middle block kept by TT-ULV right-to-left (appendix, Alg. 4), whose inner
+ * factor is the ULV form C ~ U L V^T of the pivoted QLP:
+ *  TT_LHAT_FULL : [L_11; L_21]: carry U L(:, 1:r) = C V_1, residual
+ *                 U_2 L_22 V_2^T orthogonal to V_1 (the bounds of Thm 3.1);
+ *                 computes exactly the TT-URV right-to-left sweep.
+ *  TT_LHAT_L11  : L_11 alone (Alg. 4 as printed): carry U_1 L_11, step error
+ *                 mu^2 + ||L||_F^2 - ||L_11||_F^2, errors adding in norm (the
+ *                 appendix's Proposition: ||A - A_hat|| <= sum_k eps_k), so the
+ *                 default weights are w_k = 1/(d-1) and given weights must sum
+ *                 to 1.  Only with TT_ULV, TT_RL and TT_INNER_QLP (else
+ *                 TT_EINVAL); its small factors run on the generic kernel. */
+typedef enum { TT_LHAT_FULL = 0, TT_LHAT_L11 = 1 } tt_lhat;
 
 /* Inner factor of each tt_utv step, applied to the Gram matrix of the basis
  * side (or of the range-projected matrix on a sketched step):
@@ -194,7 +208,7 @@ typedef struct {
  *              the bounds of Thm 3.1 / Cor. 3.1 hold); with the pivoted-QLP
  *              inner factor it computes exactly the TT_URV / TT_RL sweep, and
  *              TT_URV with TT_LR ([R_11 R_12] kept) exactly the TT_ULV / TT_LR
- *              one.  Alg. 4's cheaper L_11-only carry is not built.
+ *              one.  Alg. 4's L_11-only carry: tt_opts.lhat.
  *   opts       host, may be NULL (defaults).
  * Each unfolding step: if the basis side (columns for URV, rows for ULV) has
  * at most l_full entries, its Gram matrix is factored exactly; otherwise a

@@ -66,7 +66,7 @@ class tt_opts(ctypes.Structure):
                 ("orth_precision", ctypes.c_int32), ("reverse", ctypes.c_int32),
                 ("phase_ms", ctypes.POINTER(ctypes.c_double)),
                 ("power_iters", ctypes.c_int32), ("inner", ctypes.c_int32),
-                ("usvp_iters", ctypes.c_int32), ("pad2_", ctypes.c_int32)]
+                ("usvp_iters", ctypes.c_int32), ("lhat", ctypes.c_int32)]
 
 
 class tt_result(ctypes.Structure):
@@ -249,7 +249,7 @@ class TTResult:
 
 def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream,
            timing=False, orth="auto", reverse=False, power_iters=0, dims=None, shard=None,
-           inner="qlp", usvp_iters=8):
+           inner="qlp", usvp_iters=8, lhat="full"):
     if not isinstance(A, torch.Tensor):
         raise TypeError("A must be a torch.Tensor")
     if A.dtype not in (torch.float32, torch.float64):
@@ -273,6 +273,7 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
     opts.power_iters = int(power_iters)
     opts.inner = INNER[inner]
     opts.usvp_iters = int(usvp_iters)
+    opts.lhat = {"full": 0, "l11": 1}[lhat]
     wbuf = None
     if weights is not None:
         wbuf = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
@@ -314,7 +315,8 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
 
 def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, oversample=16,
            l_full=256, small="auto", weights=None, stream=None, timing=False, orth="auto",
-           reverse=False, direction=None, power_iters=0, inner="qlp", usvp_iters=8):
+           reverse=False, direction=None, power_iters=0, inner="qlp", usvp_iters=8,
+           lhat="full"):
     """TT-URV right-to-left (Alg. 3) or TT-ULV left-to-right (Alg. 1/2).
 
     Give ``eps`` (prescribed relative accuracy, Alg. 2) or ``ranks``
@@ -328,6 +330,9 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
     subspace iterations to every sketched range.  ``inner`` picks the small
     rank-revealing factor: "qlp" (pivoted QLP) or "usvp" (USV-plus-style
     deflation with ``usvp_iters`` power iterations per basis vector).
+    ``lhat="l11"`` with variant "ULV" and direction "RL" runs the appendix's
+    Alg. 4 as printed: the carry keeps L_11 alone and the default weights are
+    1/(d-1).
     """
     if (eps is None) == (ranks is None):
         raise ValueError("give exactly one of eps or ranks")
@@ -336,7 +341,7 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
     v = ({"URV": TT_URV, "ULV": TT_ULV}[variant], {"RL": TT_RL, "LR": TT_LR}[direction])
     return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
                   weights, stream, timing, orth, reverse, power_iters, inner=inner,
-                  usvp_iters=usvp_iters)
+                  usvp_iters=usvp_iters, lhat=lhat)
 
 
 class _DevBuf:

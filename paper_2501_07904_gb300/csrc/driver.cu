@@ -325,6 +325,7 @@ cudaError_t mm_run(const MM& mm, ttk::Mat<W> A, ttk::Mat<W> B, int64_t M, int64_
 struct SweepCfg {
   bool urv;   // basis on the column side, right-to-left
   bool svd;   // Jacobi small factor (TT-SVD)
+  bool l11 = false;  // appendix Alg. 4 keeping L_11 alone (TT-ULV right-to-left)
 };
 
 // True for host memory (pageable or pinned), false for device memory.
@@ -346,7 +347,9 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   const int64_t p_over = o.oversample;
   const int64_t l_full = o.l_full;
 
-  std::vector<double> w(d - 1, 1.0 / sqrt((double)(d - 1)));
+  // equal weights: sum w_k^2 = 1 (errors orthogonal, Thm 3.1), or for Alg. 4
+  // keeping L_11 alone, whose errors add in norm, sum w_k = 1 (its Proposition)
+  std::vector<double> w(d - 1, cfg.l11 ? 1.0 / (double)(d - 1) : 1.0 / sqrt((double)(d - 1)));
   if (o.weights)
     for (int i = 0; i < d - 1; ++i) w[i] = o.weights[i];
 
@@ -510,6 +513,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     prm.mode = cfg.svd ? ttk::SM_JACOBI
                        : (o.inner == TT_INNER_USVP ? ttk::SM_USVP : ttk::SM_QLP);
     prm.usvp_iters = o.usvp_iters;
+    prm.l11 = cfg.l11 ? 1 : 0;
     prm.r_fixed = (int)rfix;
     prm.r_cap = (int)rcap;
     prm.delta2_scale = dscale;
@@ -517,7 +521,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
 
     Buf carry(&al), core(&al), ws_extra(&al);
     Buf cfull(&al);  // the whole unfolding, gathered for an identity sketch
-    Piece zb, ws, ws2, gb, omega, yb, s1b, w1b, wb, bb, gy, gwb;
+    Piece zb, ws, ws2, gb, omega, yb, s1b, w1b, wb, bb, gy, gwb, tb;
     size_t ws_bytes = 0;  // size of ws (reused by the carry and core products)
     int64_t r = 1, l = 0;
     bool small64 = false;
@@ -538,9 +542,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       ws_bytes = std::max(ws_bytes, cfg.urv ? mm_ws<W>(mm_all, m, rmax, n, false)
                                             : mm_ws<W>(mm_all, rmax, n, m, false));
       TT_RESERVE(scr, align256((size_t)nb * nb * sizeof(double)) + align256((size_t)nb * nb * sizeof(W)) +
-                          align256(ws_bytes));
+                          align256(ws_bytes) + (cfg.l11 ? align256((size_t)nb * nb * sizeof(W)) : 0));
       TT_TAKE(gb, (size_t)nb * nb * sizeof(double));
       TT_TAKE(zb, (size_t)nb * nb * sizeof(W));
+      if (cfg.l11) TT_TAKE(tb, (size_t)nb * nb * sizeof(W));
       TT_TAKE(ws, ws_bytes);
       const bool acc = !W64 && tight(nb);
       acc_gram = acc;
@@ -563,6 +568,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       prm.piv_tol = small64 ? (small_df ? 1e-13 : 1e-15) : 1e-6;
       prm.df_math = small_df ? 1 : 0;
       ldz = nb;
+      prm.Tl = tb.p;
       tm.begin(s, TT_PH_SMALL);
       TT_CK(ttk::small_factor(gb.as<double>(), prm, small64, zb.p, W64, (int)ldz, ws.p,
                               dinfo.as<ttk::StepInfo>(), st), "small factor");
@@ -638,7 +644,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
           const size_t nl = align256((size_t)nb * l * sizeof(W)), ol = align256((size_t)no * l * sizeof(W));
           const size_t ll8 = align256((size_t)l * l * sizeof(double)), llw = align256((size_t)l * l * sizeof(W));
           size_t tot = (identity ? 0 : ol) + nl + align256(wsz) + align256(ttk::small_ws_bytes((int)l, true)) +
-                       ll8 + llw + 2 * nl + ol + (whiten_l ? ll8 : 0) + llw;
+                       ll8 + llw + 2 * nl + ol + (whiten_l ? ll8 : 0) + llw + (cfg.l11 ? llw : 0);
           if (powered) tot += ol;
           if (precise) tot += align256((size_t)no * l * sizeof(double));  // B in FP64
           if (active) {
@@ -816,6 +822,8 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         prm.piv_tol = small64 ? (small_df ? 1e-13 : 1e-15) : 1e-6;
         prm.df_math = small_df ? 1 : 0;
         TT_TAKE(zb, (size_t)l * l * sizeof(W));
+        if (cfg.l11) TT_TAKE(tb, (size_t)l * l * sizeof(W));
+        prm.Tl = tb.p;
         ldz = l;
         tm.begin(s, TT_PH_SMALL);
         TT_CK(ttk::small_factor(gy.as<double>(), prm, small64, zb.p, W64, (int)ldz, ws2.p,
@@ -902,8 +910,9 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     if (exact) {
       tm.begin(s, TT_PH_CARRY);
       if (cfg.urv)
-        TT_CK(mm_run<W>(mm, {C, n, true}, {Zp, ldz, true}, m, r, n, carry.as<W>(), r, nullptr, false,
-                        carry_sq, ws.p, precise, true, true, false), "carry C Z1");
+        TT_CK(mm_run<W>(mm, {C, n, true}, {cfg.l11 ? tb.as<W>() : Zp, ldz, true}, m, r, n,
+                        carry.as<W>(), r, nullptr, false, carry_sq, ws.p, precise, true, true, false),
+              cfg.l11 ? "carry C T (U_1 L_11)" : "carry C Z1");
       else
         TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {C, n, true}, r, n, m, carry.as<W>(), n, nullptr, false,
                         carry_sq, ws.p, precise, true, true, false), "carry Z1^T C");
@@ -919,8 +928,9 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       const W* Wm = Wfin;
       tm.begin(s, TT_PH_CARRY);
       if (cfg.urv)
-        TT_CK(mm_run<W>(mm, {Bm, l, true}, {Zp, ldz, true}, m, r, l, carry.as<W>(), r, nullptr, false,
-                        carry_sq, ws.p, precise, true, true, false), "carry B Z1");
+        TT_CK(mm_run<W>(mm, {Bm, l, true}, {cfg.l11 ? tb.as<W>() : Zp, ldz, true}, m, r, l,
+                        carry.as<W>(), r, nullptr, false, carry_sq, ws.p, precise, true, true, false),
+              cfg.l11 ? "carry B T (U_1 L_11)" : "carry B Z1");
       else
         TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {Bm, l, false}, r, n, l, carry.as<W>(), n, nullptr, false,
                         carry_sq, ws.p, precise, true, true, false), "carry (B Z1)^T");
@@ -1024,13 +1034,21 @@ tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims,
   if (o.power_iters < 0 || o.power_iters > 8) return fail(TT_EINVAL, "power_iters must be in [0, 8]");
   if (o.inner != TT_INNER_QLP && o.inner != TT_INNER_USVP) return fail(TT_EINVAL, "bad inner factor");
   if (o.usvp_iters < 0 || o.usvp_iters > 64) return fail(TT_EINVAL, "usvp_iters must be in [0, 64]");
+  if (o.lhat != TT_LHAT_FULL && o.lhat != TT_LHAT_L11) return fail(TT_EINVAL, "bad lhat");
+  if (o.lhat == TT_LHAT_L11 && o.inner != TT_INNER_QLP)
+    return fail(TT_EINVAL, "the L_11-only carry needs the pivoted QLP inner factor");
   if (o.weights) {
-    double s = 0.0;
+    double s = 0.0, s1 = 0.0;
     for (int k = 0; k < d - 1; ++k) {
       if (!(o.weights[k] > 0.0) || !isfinite(o.weights[k])) return fail(TT_EINVAL, "weights must be positive");
       s += o.weights[k] * o.weights[k];
+      s1 += o.weights[k];
     }
-    if (fabs(s - 1.0) > 1e-6) return fail(TT_EINVAL, "weights must satisfy sum w_k^2 = 1");
+    if (o.lhat == TT_LHAT_L11) {
+      if (fabs(s1 - 1.0) > 1e-6) return fail(TT_EINVAL, "L_11-only weights must satisfy sum w_k = 1");
+    } else if (fabs(s - 1.0) > 1e-6) {
+      return fail(TT_EINVAL, "weights must satisfy sum w_k^2 = 1");
+    }
   }
   return TT_OK;
 }
@@ -1187,10 +1205,16 @@ tt_status tt_utv(const void* A, int32_t dtype, int32_t d, const int64_t* dims, d
   // keeps the middle block [L_11; L_21] (the appendix's first case of Alg. 4)
   // carries C V_1 with error ||L_22||^2 -- exactly the right-to-left TT-URV;
   // mirrored, a left-to-right TT-URV keeping [R_11 R_12] is the left-to-right
-  // TT-ULV.  Both pairings therefore run those sweeps.
+  // TT-ULV.  Both pairings therefore run those sweeps.  Alg. 4 as printed
+  // keeps L_11 alone (tt_opts.lhat = TT_LHAT_L11): its carry U_1 L_11 is
+  // formed from the QLP's factors by the small kernel (T with C T = U_1 L_11).
   if (variant != TT_URV && variant != TT_ULV) return fail(TT_EINVAL, "bad variant");
   if (direction != TT_RL && direction != TT_LR) return fail(TT_EINVAL, "bad direction");
-  const SweepCfg cfg{direction == TT_RL, false};
+  const bool l11 = opts && opts->lhat == TT_LHAT_L11;
+  if (l11 && !(variant == TT_ULV && direction == TT_RL))
+    return fail(TT_EINVAL, "the L_11-only carry is Alg. 4: TT-ULV right-to-left");
+  SweepCfg cfg{direction == TT_RL, false};
+  cfg.l11 = l11;
   return sweep_entry(A, dtype, d, dims, eps, fixed_ranks, cfg, opts, alloc, free_fn, alloc_ctx,
                      stream, out);
 }
@@ -1202,7 +1226,11 @@ tt_status tt_utv_sharded(const void* A_local, int32_t dtype, int32_t d, const in
   if (!shard) return fail(TT_EINVAL, "NULL shard");
   if (variant != TT_URV && variant != TT_ULV) return fail(TT_EINVAL, "bad variant");
   if (direction != TT_RL && direction != TT_LR) return fail(TT_EINVAL, "bad direction");
-  const SweepCfg cfg{direction == TT_RL, false};
+  const bool l11 = opts && opts->lhat == TT_LHAT_L11;
+  if (l11 && !(variant == TT_ULV && direction == TT_RL))
+    return fail(TT_EINVAL, "the L_11-only carry is Alg. 4: TT-ULV right-to-left");
+  SweepCfg cfg{direction == TT_RL, false};
+  cfg.l11 = l11;
   return sweep_entry(A_local, dtype, d, dims, eps, fixed_ranks, cfg, opts, alloc, free_fn, alloc_ctx,
                      stream, out, shard);
 }
@@ -1212,6 +1240,7 @@ tt_status tt_svd(const void* A, int32_t dtype, int32_t d, const int64_t* dims, d
                  tt_alloc_fn alloc, tt_free_fn free_fn, void* alloc_ctx, void* stream,
                  tt_result* out) {
   if (direction != TT_RL && direction != TT_LR) return fail(TT_EINVAL, "bad direction");
+  if (opts && opts->lhat == TT_LHAT_L11) return fail(TT_EINVAL, "TT-SVD has no L_11-only carry");
   SweepCfg cfg{direction == TT_RL, true};
   return sweep_entry(A, dtype, d, dims, eps, fixed_ranks, cfg, opts, alloc, free_fn, alloc_ctx,
                      stream, out);

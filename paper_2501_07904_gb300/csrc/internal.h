@@ -90,6 +90,11 @@ struct SmallParams {
   int range_exact;        // 1: the sketch is the identity, so W spans X's row space (mu^2 = 0)
   int df_math;            // with fp64_math: run the fast path in double-float (n <= 64)
   int usvp_iters;         // SM_USVP: power iterations per vector
+  // SM_QLP, appendix Alg. 4 with L_11 kept alone: rank by the error
+  // mu^2 + ||L||^2 - ||L_11||^2, and Tl (n x r, ld = ldz, Z's type) receives
+  // T with B T = U_1 L_11 (runs on the generic kernel)
+  int l11;
+  void* Tl;
 };
 size_t small_ws_bytes(int n, bool fp64);
 // Register-resident fast path (small_fast.cu) for SM_QLP / SM_ORTH with

@@ -573,6 +573,10 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
   }
 
   // ---- SM_QLP ----
+  // (with prm.l11, the appendix's Alg. 4 keeping L_11 alone: order[] records
+  // the second pivoting, d2[] the diagonal of R_2, and the error of rank j is
+  // mu^2 + s1 + ||L||^2 - ||L(0:j, 0:j)||^2)
+  __shared__ T d2[kMaxSmall];
   double s1;
   const int k1 = pivoted_cholesky(A, n, perm1, prm.piv_tol, s1, redt, redi, redd);
   // M = R_1^T (n x k1): rows are pivoted columns of X, columns the Cholesky rows.
@@ -580,7 +584,17 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
     const int i = e / k1, c = e % k1;
     Mq[i * n + c] = A[c * n + i];
   }
+  for (int c = tid; c < n; c += nt) order[c] = c;
   __syncthreads();
+  double totL2 = 0.0, l11sq = 0.0;
+  if (prm.l11) {
+    double part = 0.0;
+    for (int e = tid; e < n * k1; e += nt) {
+      const double x = (double)Mq[(e / k1) * n + e % k1];
+      part += x * x;
+    }
+    totL2 = block_sum(part, redd);
+  }
   const int kk = min(n, k1);
   int j = 0, r = 1;
   for (;; ++j) {
@@ -595,7 +609,19 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
       part += (double)s;
     }
     const double trail = block_sum(part, redd);
-    const double tj = mu2 + s1 + trail;
+    double tj = mu2 + s1 + trail;
+    if (prm.l11) {
+      if (j >= 1) {  // column j-1 of R_2 is final: its part above and on the diagonal
+        double pc = 0.0;
+        for (int i = tid; i < j - 1; i += nt) {
+          const double x = (double)Mq[i * n + (j - 1)];
+          pc += x * x;
+        }
+        pc = block_sum(pc, redd);
+        l11sq += pc + (double)d2[j - 1] * (double)d2[j - 1];
+      }
+      tj = mu2 + s1 + fmax(totL2 - l11sq, 0.0);
+    }
     if (tid == 0) info->tails[j] = tj;
     if (fixed) {
       if (j == rt || j >= kk) {
@@ -626,11 +652,13 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
     block_argmax(v, idx, redt, redi, cq, q);
     if (q != j) {
       for (int i = tid; i < n; i += nt) swap_vals(Mq[i * n + j], Mq[i * n + q]);
+      if (tid == 0) swap_vals(order[j], order[q]);
     }
     __syncthreads();
     const T alpha = sqrt(cq > T(0) ? cq : T(0));
     const T x0 = Mq[j * n + j];
     const T sg = x0 >= T(0) ? T(1) : T(-1);
+    if (tid == 0) d2[j] = -sg * alpha;
     // tau = 2 / ||v||^2 from the stored v itself (FP64 sum): the reflector is
     // then orthogonal to working precision even when the column norm used for
     // alpha carries FP32 summation error.
@@ -669,6 +697,48 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
     }
   }
   __syncthreads();
+  if (prm.l11) {
+    // B T = U_1 L_11 with T = Pi_1 R_11^{-1} E_J L_11: U_1 = Q_1(:, J) for the
+    // rows J = order[0..rr) of R_1 taken first by the second pivoting, Q_1 =
+    // B Pi_1 R_11^{-1}, and L_11 = R_1(J, :) Q_2(:, 0:r) (= R_2(0:r, 0:r)^T).
+    // One thread per column t: the right-hand side E_J L_11(:, t) in Mq(:, t)
+    // (pivot order), then back substitution with R_11 in place.
+    const int rr = min(r, nref);
+    for (int t = tid; t < r; t += nt) {
+      for (int i = 0; i < k1; ++i) Mq[i * n + t] = T(0);
+      for (int s2 = 0; s2 < rr; ++s2) {
+        const int row = order[s2];
+        T acc = T(0);
+        for (int i = row; i < n; ++i) acc += A[row * n + i] * Qe[i * n + t];
+        Mq[row * n + t] = acc;
+      }
+      for (int i = k1 - 1; i >= 0; --i) {
+        T acc = Mq[i * n + t];
+        for (int k = i + 1; k < k1; ++k) acc -= A[i * n + k] * Mq[k * n + t];
+        Mq[i * n + t] = acc / A[i * n + i];
+      }
+    }
+    __syncthreads();
+    // Pi_1 Y into A (R_1 is no longer needed)
+    for (int e = tid; e < n * r; e += nt) {
+      const int i = e / r, t = e % r;
+      A[perm1[i] * n + t] = i < k1 ? Mq[i * n + t] : T(0);
+    }
+    __syncthreads();
+    ZT* Tl = reinterpret_cast<ZT*>(prm.Tl);
+    for (int e = tid; e < n * r; e += nt) {
+      const int i = e / r, t = e % r;
+      T v;
+      if (prm.Gw) {
+        v = T(0);
+        for (int k = i; k < n; ++k) v += Ti[i * n + k] * A[k * n + t];
+      } else {
+        v = A[i * n + t];
+      }
+      Tl[(size_t)i * ldz + t] = (ZT)v;
+    }
+    __syncthreads();
+  }
   if (prm.Gw) {
     // Z_1 = T^{-1} Pi_1 Q_2(:, 0:r) (Mq is free again: hold Pi_1 Q_2 there)
     for (int e = tid; e < n * r; e += nt) {

@@ -847,6 +847,7 @@ cudaError_t launch_fast(const double* G, SmallParams prm, void* Z, int ldz, void
 
 bool small_fast_eligible(const SmallParams& prm, bool fp64) {
   if (prm.mode != SM_QLP && prm.mode != SM_ORTH) return false;
+  if (prm.l11) return false;
   const int lim = fp64 ? tile_n<double>() : tile_n<float>();
   return prm.n >= 1 && prm.n <= lim;
 }

@@ -286,6 +286,51 @@ def test_alg4_pairings(tu, precision, tol):
             assert torch.equal(x, y)
 
 
+@pytest.mark.parametrize("precision, tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("l_full", [256, 24])
+def test_alg4_l11_matches_oracle(tu, precision, tol, l_full):
+    # the appendix's Alg. 4 as printed (L_11 kept alone) against the oracle's,
+    # which forms U_1 L_11 from Householder factors: same ranks, tensors and
+    # step errors, the Proposition's bound RSE <= sum eps_k = eps (weights
+    # 1/(d-1)), and its error = the sum of the step errors no longer an
+    # equality (the errors add in norm); exact and sketched steps
+    A = RAGGED if precision == "fp64" else RAGGED.astype(np.float32)
+    A64 = np.asarray(A, np.float64)
+    A_t = torch.from_numpy(A).cuda()
+    for eps in (1e-2, 1e-5):
+        res = tu.tt_utv(A_t, eps=eps, variant="ULV", direction="RL", lhat="l11",
+                        precision=precision, l_full=l_full)
+        ref = otc.tt_ulv_rl(A64, eps=eps, lhat="l11", l_full=l_full)
+        assert res.ranks == ref["ranks"], (eps, res.ranks, ref["ranks"])
+        assert res.orth == "right"
+        cores = np_cores(res)
+        assert rel_diff(cores, ref["cores"], ref["normA2"]) <= tol
+        rse = otc.rse(A64, cores)
+        assert rse <= eps
+        if precision == "fp64":  # FP32 step errors this small sit below FP32 rounding of ||C||^2
+            for t, tr in zip(res.tail_sq, ref["tails"]):
+                assert abs(t - tr) <= max(1e-6 * tr, 1e-12 * ref["normA2"])
+    # fixed ranks: the same cores as the oracle's
+    res = tu.tt_utv(A_t, ranks=[4, 6, 3], variant="ULV", direction="RL", lhat="l11",
+                    precision=precision, l_full=l_full)
+    ref = otc.tt_ulv_rl(A64, ranks=[4, 6, 3], lhat="l11", l_full=l_full)
+    assert res.ranks == ref["ranks"]
+    assert rel_diff(np_cores(res), ref["cores"], ref["normA2"]) <= tol
+
+
+def test_alg4_l11_argument_checks(tu):
+    A = torch.from_numpy(RAGGED.astype(np.float32)).cuda()
+    for kw in (dict(variant="URV", direction="RL"), dict(variant="ULV", direction="LR"),
+               dict(variant="ULV", direction="RL", inner="usvp")):
+        with pytest.raises(tu.TTError) as ei:
+            tu.tt_utv(A, eps=1e-2, lhat="l11", **kw)
+        assert ei.value.status == tu.TT_EINVAL
+    with pytest.raises(tu.TTError) as ei:      # L_11 weights must sum to 1
+        tu.tt_utv(A, eps=1e-2, variant="ULV", direction="RL", lhat="l11",
+                  weights=[3 ** -0.5] * 3)
+    assert ei.value.status == tu.TT_EINVAL
+
+
 def test_deterministic(tu):
     A = torch.from_numpy(RAGGED.astype(np.float32)).cuda()
     a = tu.tt_utv(A, eps=1e-3, l_full=24)
