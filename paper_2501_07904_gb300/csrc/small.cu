@@ -358,8 +358,10 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
           A[q * n + k] = s * ap + c * aq;
         }
         __syncthreads();
+        // columns p, q of every row k: consecutive threads take the pairs of
+        // one row, so a warp's loads fall in that row's few cache lines
         for (int e = tid; e < npairs * n; e += nt) {
-          const int i = e / n, k = e % n;
+          const int k = e / npairs, i = e % npairs;
           const int p = rp[i], q = rq[i];
           if (q < 0 || rs[i] == T(0)) continue;
           const T c = rc[i], s = rs[i];
