@@ -24,6 +24,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 #include "ttutv.h"
 
@@ -219,6 +221,17 @@ bool debug_trace() {
   return on;
 }
 
+// Test hook: TTUTV_JACOBI_SWEEPS=k caps the TT-SVD Jacobi iteration at k
+// sweeps (default 60), so that a test can reach TT_ENOCONV without a fault.
+int jacobi_sweeps() {
+  static const int k = [] {
+    const char* v = getenv("TTUTV_JACOBI_SWEEPS");
+    const int x = v ? atoi(v) : 0;
+    return x > 0 && x < 60 ? x : 0;
+  }();
+  return k;
+}
+
 // Sketch width l: r + p for a fixed rank, else roundup16(max(2 r_prev,
 // r_prev + p, 32)); never more than either side nor the small-factor limit.
 int64_t sketch_size(int64_t nb, int64_t no, int64_t r_prev, int64_t p, int64_t rfix) {
@@ -229,8 +242,13 @@ int64_t sketch_size(int64_t nb, int64_t no, int64_t r_prev, int64_t p, int64_t r
 
 // CUDA-event timing of the sweep's phases (only when opts.phase_ms is set).
 // Events come from a per-thread pool that is created once and reused, so a
-// timed sweep adds only event records to its stream.
+// timed sweep adds only event records to its stream.  Every phase is also an
+// NVTX range ("step s: phase"), free unless a profiler is attached.
 struct PhaseTimer {
+  bool nvtx_open = false;
+  ~PhaseTimer() {
+    if (nvtx_open) nvtxRangePop();
+  }
   double* out = nullptr;
   cudaStream_t st = nullptr;
   struct Rec {
@@ -257,6 +275,13 @@ struct PhaseTimer {
     return p[used++];
   }
   void begin(int step, int phase) {
+    static const char* const names[TT_NPHASES] = {"gram", "small", "carry", "core",
+                                                  "sketch", "orth", "project", "other"};
+    char label[48];
+    snprintf(label, sizeof label, "step %d: %s", step, names[phase & 7]);
+    if (nvtx_open) nvtxRangePop();
+    nvtxRangePushA(label);
+    nvtx_open = true;
     if (!out) return;
     Rec r{step, phase, take(), take()};
     if (!r.a || !r.b) return;
@@ -265,6 +290,10 @@ struct PhaseTimer {
     open = (int)recs.size() - 1;
   }
   void end() {
+    if (nvtx_open) {
+      nvtxRangePop();
+      nvtx_open = false;
+    }
     if (!out || open < 0) return;
     cudaEventRecord(recs[open].b, st);
     open = -1;
@@ -514,6 +543,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
                        : (o.inner == TT_INNER_USVP ? ttk::SM_USVP : ttk::SM_QLP);
     prm.usvp_iters = o.usvp_iters;
     prm.l11 = cfg.l11 ? 1 : 0;
+    prm.jacobi_sweeps = jacobi_sweeps();
     prm.r_fixed = (int)rfix;
     prm.r_cap = (int)rcap;
     prm.delta2_scale = dscale;
@@ -1136,6 +1166,10 @@ tt_status sweep_entry(const void* A, int32_t dtype, int32_t d, const int64_t* di
                       tt_free_fn free_fn, void* ctx, void* stream, tt_result* out,
                       const tt_shard* sh = nullptr) {
   g_err.clear();
+  struct NvtxSweep {  // one NVTX range around the whole sweep
+    NvtxSweep() { nvtxRangePushA("ttutv sweep"); }
+    ~NvtxSweep() { nvtxRangePop(); }
+  } nvtx_sweep;
   tt_opts o;
   tt_opts_default(&o);
   if (opts) o = *opts;

@@ -95,6 +95,7 @@ struct SmallParams {
   // T with B T = U_1 L_11 (runs on the generic kernel)
   int l11;
   void* Tl;
+  int jacobi_sweeps;      // SM_JACOBI sweep cap (0: the default 60)
 };
 size_t small_ws_bytes(int n, bool fp64);
 // Register-resident fast path (small_fast.cu) for SM_QLP / SM_ORTH with

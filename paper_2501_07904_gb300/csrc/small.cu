@@ -311,7 +311,8 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
     const double eps_t = sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920929e-07;
     int sweep = 0;
     bool conv = false;
-    for (; sweep < 60; ++sweep) {
+    const int max_sweeps = prm.jacobi_sweeps > 0 ? prm.jacobi_sweeps : 60;
+    for (; sweep < max_sweeps; ++sweep) {
       double off = 0.0, dg = 0.0;
       for (int e = tid; e < n * n; e += nt) {
         const double a = (double)A[e];

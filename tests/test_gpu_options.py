@@ -82,3 +82,32 @@ def test_bounded_wait_runs_out_and_the_context_survives(tu):
                                            dtype=np.float32)).cuda()
     res = tu.tt_utv(A, eps=1e-3, precision="mixed")
     assert res.ranks == [1, 3, 4, 1]
+
+
+def test_jacobi_cap_reports_enoconv():
+    """The TT-SVD Jacobi sweep cap (60) reached returns TT_ENOCONV, in a child
+    process whose cap is lowered to one sweep by the test hook
+    TTUTV_JACOBI_SWEEPS; the kernel ends normally (status word), and the same
+    decomposition converges with the default cap."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = (
+        "import numpy as np, torch, synth\n"
+        "import paper_2501_07904_gb300 as tu\n"
+        "A = torch.from_numpy(synth.gaussian_tt((30, 20, 25), (1, 6, 5, 1), 1e-3, seed=3)).cuda()\n"
+        "try:\n"
+        "    tu.tt_svd(A, eps=1e-2)\n"
+        "    print('converged')\n"
+        "except tu.TTError as e:\n"
+        "    print('status', e.status)\n"
+    )
+    for cap, want in (("1", "status 5"), ("0", "converged")):
+        env = dict(os.environ, TTUTV_JACOBI_SWEEPS=cap,
+                   PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+        res = subprocess.run([sys.executable, "-c", child], cwd=root, env=env,
+                             capture_output=True, text=True, timeout=600)
+        assert res.returncode == 0, res.stderr[-2000:]
+        assert want in res.stdout, (cap, res.stdout, res.stderr[-2000:])
