@@ -61,6 +61,11 @@ WORKLOADS = {
                           "blob volume from its Bernoulli(0.3) observation set, TT ranks "
                           "(1,32,16,1): tangent projection, exact line-search step, fixed-rank "
                           "TT-URV retraction of the full 4.2M-entry iterate"),
+    "mri-rgrad": dict(kind="rgrad", problem="mri", ranks=(1, 55, 41, 1),
+                      desc="Riemannian gradient completion at the size and TT ranks of the "
+                           "paper's MRI experiment (Sec. 4.2.2): a 181x217x181 f32 volume of "
+                           "40 Gaussian blobs standing in for the MRI data, Bernoulli(0.3) "
+                           "observation set, TT ranks (1,55,41,1), TT-URV retraction"),
     "c5-half": dict(dims=(64, 128, 128, 128), ranks=(1, 64, 64, 64, 1), rel_noise=1e-3, seed=0,
                     eps=1e-2, variant="URV",
                     desc="64x128^3 f32 (512 MiB) slab of the 128^4 workload's generator, for "
@@ -753,10 +758,10 @@ def run_reference_c4(args, wl, rank, world):
 RGRAD_METRIC = "RGrad completion iterations/s"
 
 
-def rgrad_problem():
-    cfg = synth.CONFIGS["c4"]
+def rgrad_problem(name="c4"):
+    cfg = synth.CONFIGS[name]
     shape = cfg["shape"]
-    M = synth.make_config("c4")
+    M = synth.make_config(name)
     idx = synth.observation_mask(shape, cfg["p_obs"], cfg["mask_seed"])
     return cfg, shape, M, idx, np.ascontiguousarray(M.reshape(-1)[idx])
 
@@ -774,7 +779,7 @@ def run_rgrad(args, wl, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg, shape, M, idx, vals = rgrad_problem()
+    cfg, shape, M, idx, vals = rgrad_problem(wl.get("problem", "c4"))
     ranks = list(cfg["ranks"][1:-1])
     i_t = torch.from_numpy(idx).to(dev)
     v_t = torch.from_numpy(vals).to(dev)
@@ -861,7 +866,7 @@ def run_rgrad(args, wl, rank, world):
         "metric": RGRAD_METRIC, "value": round(value, 3), "unit": "iterations/s", "n_gpus": world,
         "steps": K, "warmup": W, "ms_per_step": round(ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"c4-rgrad: {wl['desc']}", "entries": len(idx), "ranks": ranks,
+        "config": {"workload": f"{args.workload}: {wl['desc']}", "entries": len(idx), "ranks": ranks,
                    "l2": "inputs larger than L2 (the 4.2M-entry full iterate and its sweeps, "
                          "the 1.26M-entry plans)",
                    "parallelism": f"replicas x{world} (independent problems)"},
@@ -904,7 +909,7 @@ def rgrad_cpu_baseline(shape, idx, vals, ranks):
 def run_reference_rgrad(args, wl, rank, world):
     if rank != 0:
         return None
-    cfg, shape, M, idx, vals = rgrad_problem()
+    cfg, shape, M, idx, vals = rgrad_problem(wl.get("problem", "c4"))
     ranks = list(cfg["ranks"][1:-1])
     cores = synth.gaussian_cores(shape, [1, *ranks, 1], seed=0)
     v64 = vals.astype(np.float64)
@@ -919,7 +924,7 @@ def run_reference_rgrad(args, wl, rank, world):
             "unit": "iterations/s", "n_gpus": world, "steps": steps, "warmup": 0,
             "ms_per_step": round(dt * 1e3, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"c4-rgrad: {wl['desc']}", "precision": "fp64 oracle",
+            "config": {"workload": f"{args.workload}: {wl['desc']}", "precision": "fp64 oracle",
                        "l2": "n/a (CPU)", "parallelism": "1 process, host cores"},
             "cpu_baseline": {"value": round(value, 5), "unit": "iterations/s",
                              "cores": os.cpu_count(), "kind": "oracle", "sample": sample},

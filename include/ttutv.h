@@ -437,6 +437,15 @@ tt_status tt_eval_plan_backward_mixed(tt_eval_plan* plan, const float* const* le
  * d memsets and 2 d + 3 (d - 1) launches. */
 tt_status tt_tangent_project(tt_eval_plan* plan, const float* const* U, const float* const* V,
                              const float* z, float* const* dU, void* stream);
+/* The tangent vector xi = sum_k U_1 .. U_{k-1} dU_k V_{k+1} .. V_d at the
+ * plan's indices (P_Omega xi, for the step size of Sec. 4.2.2):
+ *   out_e = sum_k (U_1[i_1] .. U_{k-1}[i_{k-1}]) dU_k[:, i_k, :] (V_{k+1}[i_{k+1}] .. V_d[i_d]).
+ * U, V as for tt_tangent_project, dU shaped like the cores (host arrays of d
+ * device pointers); out: device float[n], overwritten.  The terms are added
+ * in the order k = 1..d, so the result is deterministic.  Works at the
+ * plan's own ranks (no rank-2r block TT).  Asynchronous; d launches. */
+tt_status tt_tangent_eval(const tt_eval_plan* plan, const float* const* U, const float* const* V,
+                          const float* const* dU, float* out, void* stream);
 
 /* One-shot forms: build a plan (cudaMallocAsync), run, destroy.  Each
  * synchronizes `stream` once (the index check); TT_EINVAL for an index

@@ -44,7 +44,7 @@ EXPORTS = ["tt_opts_default", "tt_utv", "tt_utv_sharded", "tt_svd", "tt_result_f
            "tt_full", "tt_full_noalloc", "tt_orthogonalize_work_bytes", "tt_orthogonalize", "tt_full_noalloc_max_work_bytes", "tt_rse_work_bytes",
            "tt_rse", "tt_eval_plan_create", "tt_eval_plan_destroy", "tt_eval_plan_device_bytes",
            "tt_eval_plan_at", "tt_eval_plan_backward", "tt_eval_plan_backward_mixed",
-           "tt_tangent_project", "tt_eval_at",
+           "tt_tangent_project", "tt_tangent_eval", "tt_eval_at",
            "tt_eval_at_backward", "tt_sketch_matrix", "tt_wait_selftest", "tt_bounds_violations",
            "tt_kernel_launches",
            "tt_last_error",
@@ -152,6 +152,8 @@ def lib():
     L.tt_eval_plan_backward_mixed.restype = I32
     L.tt_tangent_project.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), P, ctypes.POINTER(P), P]
     L.tt_tangent_project.restype = I32
+    L.tt_tangent_eval.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P, P]
+    L.tt_tangent_eval.restype = I32
     L.tt_eval_at.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P, P]
     L.tt_eval_at.restype = I32
     L.tt_eval_at_backward.argtypes = [I32, PI64, PI64, ctypes.POINTER(P), P, I64, P,
@@ -678,6 +680,17 @@ class EvalPlan:
                                             ctypes.c_void_p(z_c.data_ptr()), self._ptrs(dU),
                                             st_ptr))
         return dU
+
+    def tangent_eval(self, U, V, dU, stream=None):
+        """P_Omega of the tangent vector sum_k U_<k dU_k V_>k at the plan's
+        indices (see tt_tangent_eval), at the plan's own ranks."""
+        U_c, V_c, dU_c = self._cores(U), self._cores(V), self._cores(dU)
+        st, st_ptr = _stream(stream)
+        with torch.cuda.device(self.device), torch.cuda.stream(st):
+            out = torch.empty(self.n, dtype=torch.float32, device=self.device)
+            _check(lib().tt_tangent_eval(self._h, self._ptrs(U_c), self._ptrs(V_c),
+                                         self._ptrs(dU_c), ctypes.c_void_p(out.data_ptr()), st_ptr))
+        return out.view(self.shape)
 
     def close(self, stream=None):
         if getattr(self, "_h", None) is not None:

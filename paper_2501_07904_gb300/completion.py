@@ -15,8 +15,8 @@ rgrad() is the paper's own solver: Riemannian gradient descent on the
 manifold of TT tensors of fixed ranks.  Each iteration projects the residual
 P_Omega(X_k - M) onto the tangent space at X_k (tt_tangent_project: one
 two-frame masked backward and an FP64 gauge), evaluates that Riemannian
-gradient xi on the observed entries through the rank-2r block TT of the
-tangent vector, takes the exact line-search step
+gradient xi on the observed entries (tt_tangent_eval: one forward pass per
+core at the iterate's own ranks), takes the exact line-search step
 alpha_k = <P_Omega xi, P_Omega(X_k - M)> / <P_Omega xi, P_Omega xi>,
 forms X_k - alpha_k xi in full (a rank-2r block TT contracted by tt_full) and
 retracts it with a fixed-rank TT-URV, TT-ULV or TT-SVD sweep of the library.
@@ -143,8 +143,7 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
 
     values  device float32 [n]: observed entries m_e;
     idx     device int64 [n]: their row-major linear indices in `shape`;
-    ranks   r_1 .. r_{d-1} (each at most 32: the rank-2r block TT of the
-            tangent vector is evaluated by a plan, whose ranks are at most 64);
+    ranks   r_1 .. r_{d-1} (each at most 64, the masked-evaluation plan's limit);
     retraction  "URV" (TT-URV, right-to-left), "ULV" (TT-ULV, left-to-right)
             or "SVD" (TT-SVD), each at the fixed ranks;
     p_obs   sampling rate of the spectral initialisation (default n / prod(shape)).
@@ -158,8 +157,8 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
     if not (values.is_cuda and idx.is_cuda) or values.numel() != idx.numel():
         raise ValueError("values and idx must be device vectors of one length")
     ranks = [int(r) for r in ranks]
-    if len(ranks) != len(shape) - 1 or any(r < 1 or 2 * r > 64 for r in ranks):
-        raise ValueError("need d - 1 ranks in [1, 32]")
+    if len(ranks) != len(shape) - 1 or any(r < 1 or r > 64 for r in ranks):
+        raise ValueError("need d - 1 ranks in [1, 64]")
     n_total = math.prod(shape)
     if p_obs is None:
         p_obs = idx.numel() / n_total
@@ -168,7 +167,6 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
     X, orth = _retract(z0.view(*shape), ranks, retraction, precision, stream)
     del z0
     plan = EvalPlan(shape, [1, *ranks, 1], idx, stream)
-    plan2 = EvalPlan(shape, [1, *[2 * r for r in ranks], 1], idx, stream)
     losses, alphas = [], []
     for t in range(steps + 1):
         if callback is not None:
@@ -180,7 +178,7 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
         other = _other_frame(X, orth, stream)
         U, V = (other, X) if orth == "right" else (X, other)
         dU = plan.tangent_project(U, V, z, stream)
-        xi = plan2.at(tangent_block_cores(U, V, dU), stream)
+        xi = plan.tangent_eval(U, V, dU, stream)
         den = float(torch.dot(xi, xi))
         alpha = float(torch.dot(xi, z)) / den if den > 0.0 else 0.0
         alphas.append(alpha)
@@ -188,5 +186,4 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
         X, orth = _retract(full, ranks, retraction, precision, stream)
         del full
     plan.close(stream)
-    plan2.close(stream)
     return X, losses, alphas

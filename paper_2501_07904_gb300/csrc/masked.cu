@@ -258,6 +258,7 @@ struct PassArgs {
   // read those rows as their interface (mode 2: right side given, core 1;
   // mode 3: left side given, core 3).  Mode 0: interfaces from chains.
   int mode;
+  int accumulate;      // forward: out += x (the tangent evaluation's passes) instead of out = x
   const int32_t* pos1;  // [n] entry -> position in core 1's order (mode 1)
   const int32_t* pos3;  // [n] entry -> position in core 3's order (mode 1)
   float* rows1;         // [n][r_1]
@@ -713,7 +714,7 @@ __global__ void __launch_bounds__(kEvalThreads, 5) eval_pass_kernel(PassArgs a) 
           }
         }
         const int o = a.perm[p0 + p];
-        if (TT_IN(o, a.n)) a.out[o] = x;
+        if (TT_IN(o, a.n)) a.out[o] = a.accumulate ? a.out[o] + x : x;
       }
       __syncthreads();
     }
@@ -1353,6 +1354,30 @@ tt_status tt_tangent_project(tt_eval_plan* plan, const float* const* U, const fl
     ttk::gauge_reduce_kernel<<<1, ttk::kGaugeThreads, 0, st>>>(part, nblk, r * r, S);
     ttk::gauge_apply_kernel<<<napply, ttk::kGaugeThreads, 0, st>>>(U[k], dU[k], m, r, S);
     EV_CK(cudaGetLastError(), "tangent projection");
+  }
+  return TT_OK;
+}
+
+tt_status tt_tangent_eval(const tt_eval_plan* plan, const float* const* U, const float* const* V,
+                          const float* const* dU, float* out, void* stream) {
+  ttk::set_last_error("");
+  if (!plan || !U || !V || !dU || (plan->n > 0 && !out)) return plan_fail(TT_EINVAL, "NULL argument");
+  for (int k = 0; k < plan->d; ++k)
+    if (!U[k] || !V[k] || !dU[k]) return plan_fail(TT_EINVAL, "NULL core");
+  if (plan->n == 0) return TT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // pass k: the forward contraction with U left of core k, dU_k in its place
+  // and V right of it, in core k's order, added to out (pass 0 writes it)
+  for (int k = 0; k < plan->d; ++k) {
+    const float* left[TT_MAXD];
+    for (int j = 0; j < plan->d; ++j) left[j] = j == k ? dU[k] : U[j];
+    ttk::PassArgs a = pass_args(plan, left, V, k, 0);
+    a.out = out;
+    a.accumulate = k > 0 ? 1 : 0;
+    const size_t sm = ttk::pass_smem(a, plan->ranks);
+    ttk::count_launch();
+    ttk::eval_pass_kernel<<<(unsigned)plan->L.nchunks, ttk::kEvalThreads, sm, st>>>(a);
+    EV_CK(cudaGetLastError(), "tangent evaluation");
   }
   return TT_OK;
 }

@@ -131,6 +131,10 @@ CONFIGS = {
                rel_noise=1e-4, seed=0, dtype="float32", eps=1e-3),
     "c4": dict(kind="blobs", shape=(256, 256, 64), nblobs=20, seed=0, p_obs=0.3,
                mask_seed=1, dtype="float32", ranks=(1, 32, 16, 1)),
+    # the size and TT ranks of the completion experiment's MRI volume (Sec. 4.2.2:
+    # 181 x 217 x 181, ranks (55, 41), 70% of the entries removed), as blobs
+    "mri": dict(kind="blobs", shape=(181, 217, 181), nblobs=40, seed=2, p_obs=0.3,
+                mask_seed=3, dtype="float32", ranks=(1, 55, 41, 1)),
     "c5": dict(kind="gaussian_tt", dims=(128, 128, 128, 128), ranks=(1, 64, 64, 64, 1),
                rel_noise=1e-3, seed=0, dtype="float32", eps=1e-2),
 }

@@ -166,6 +166,43 @@ def test_orthogonalize_rejects_bad_arguments(tu):
     assert ei.value.status == tu.TT_EINVAL
 
 
+@pytest.mark.parametrize("name", sorted(MIXED_CASES))
+def test_tangent_eval_matches_oracle(tu, name):
+    """P_Omega of the tangent vector sum_k U_<k dU_k V_>k against the oracle's
+    block TT of it contracted in full (FP64)."""
+    dims, ranks, n = MIXED_CASES[name]
+    idx = synth.random_indices(dims, n, seed=91 + len(name))
+    L, R = _frames32(dims, ranks, 92)
+    dU = [np.random.default_rng(93 + k).standard_normal(c.shape).astype(np.float32)
+          for k, c in enumerate(L)]
+    plan = tu.EvalPlan(dims, ranks, torch.from_numpy(idx).cuda())
+    got = plan.tangent_eval(_dev(L), _dev(R), _dev(dU)).double().cpu().numpy()
+    L64, R64, d64 = ([c.astype(np.float64) for c in x] for x in (L, R, dU))
+    ref = otc.tt_full(org.tangent_cores(L64, R64, d64)).reshape(-1)[idx]
+    mag = otc.tt_full(org.tangent_cores([np.abs(c) for c in L64], [np.abs(c) for c in R64],
+                                        [np.abs(c) for c in d64])).reshape(-1)[idx]
+    depth = sum(ranks) + 8 + len(dims)
+    assert np.all(np.abs(got - ref) <= depth * U32 * mag + 1e-30), name
+
+
+def test_rgrad_ranks_above_32(tu):
+    """Ranks the rank-2r block TT could not take (r_1 = 40 > 32): the first
+    iterations follow the oracle's, and the loss falls."""
+    from paper_2501_07904_gb300.completion import rgrad
+
+    dims, ranks = (48, 40, 30), (1, 40, 12, 1)
+    T = otc.tt_full([np.asarray(c, np.float64) for c in synth.gaussian_cores(dims, ranks, seed=94)])
+    T = (T / np.abs(T).max()).astype(np.float32)
+    idx = np.sort(np.random.default_rng(95).choice(T.size, T.size // 2, replace=False))
+    vals = T.reshape(-1)[idx]
+    _, losses, _ = rgrad(torch.from_numpy(vals).cuda(), torch.from_numpy(idx).cuda(), dims,
+                         ranks[1:-1], steps=8, retraction="URV")
+    _, ref = org.rgrad(vals.astype(np.float64), idx, dims, ranks, steps=3, variant="URV")
+    for t in range(4):
+        assert losses[t] == pytest.approx(ref[t], rel=2e-3), t
+    assert losses[-1] < 0.1 * losses[0]
+
+
 def test_tangent_projection_empty_index_set(tu):
     dims, ranks = (4, 5, 3), (1, 2, 3, 1)
     L, R = _frames32(dims, ranks, 84)
