@@ -15,8 +15,10 @@ rgrad() is the paper's own solver: Riemannian gradient descent on the
 manifold of TT tensors of fixed ranks.  Each iteration projects the residual
 P_Omega(X_k - M) onto the tangent space at X_k (tt_tangent_project: one
 two-frame masked backward and an FP64 gauge), evaluates that Riemannian
-gradient xi on the observed entries (tt_tangent_eval: one forward pass per
-core at the iterate's own ranks), takes the exact line-search step
+gradient xi on the observed entries (through a second plan at ranks 2r, one
+masked evaluation of the block TT of xi, when 2r fits the plan's limit of 64;
+else tt_tangent_eval, one forward pass per core at the iterate's own ranks),
+takes the exact line-search step
 alpha_k = <P_Omega xi, P_Omega(X_k - M)> / <P_Omega xi, P_Omega xi>,
 forms X_k - alpha_k xi in full (a rank-2r block TT contracted by tt_full) and
 retracts it with a fixed-rank TT-URV, TT-ULV or TT-SVD sweep of the library.
@@ -167,6 +169,10 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
     X, orth = _retract(z0.view(*shape), ranks, retraction, precision, stream)
     del z0
     plan = EvalPlan(shape, [1, *ranks, 1], idx, stream)
+    # P_Omega xi: one evaluation of xi's rank-2r block TT when 2r fits a plan
+    # (faster than d passes), else d passes at the iterate's ranks
+    plan2 = EvalPlan(shape, [1, *[2 * r for r in ranks], 1], idx, stream) \
+        if 2 * max(ranks) <= 64 else None
     losses, alphas = [], []
     for t in range(steps + 1):
         if callback is not None:
@@ -178,7 +184,8 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
         other = _other_frame(X, orth, stream)
         U, V = (other, X) if orth == "right" else (X, other)
         dU = plan.tangent_project(U, V, z, stream)
-        xi = plan.tangent_eval(U, V, dU, stream)
+        xi = plan2.at(tangent_block_cores(U, V, dU), stream) if plan2 is not None \
+            else plan.tangent_eval(U, V, dU, stream)
         den = float(torch.dot(xi, xi))
         alpha = float(torch.dot(xi, z)) / den if den > 0.0 else 0.0
         alphas.append(alpha)
@@ -186,4 +193,6 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
         X, orth = _retract(full, ranks, retraction, precision, stream)
         del full
     plan.close(stream)
+    if plan2 is not None:
+        plan2.close(stream)
     return X, losses, alphas
