@@ -173,12 +173,14 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
     # (faster than d passes), else d passes at the iterate's ranks
     plan2 = EvalPlan(shape, [1, *[2 * r for r in ranks], 1], idx, stream) \
         if 2 * max(ranks) <= 64 else None
+    # losses and steps stay on the device (read once at the end): the loop's
+    # only host synchronizations are the retraction sweep's rank reads
     losses, alphas = [], []
     for t in range(steps + 1):
         if callback is not None:
             callback(t, X)
         z = plan.at(X, stream) - values
-        losses.append(0.5 * float(torch.dot(z, z)))
+        losses.append(0.5 * torch.dot(z, z))
         if t == steps:
             break
         other = _other_frame(X, orth, stream)
@@ -186,8 +188,9 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
         dU = plan.tangent_project(U, V, z, stream)
         xi = plan2.at(tangent_block_cores(U, V, dU), stream) if plan2 is not None \
             else plan.tangent_eval(U, V, dU, stream)
-        den = float(torch.dot(xi, xi))
-        alpha = float(torch.dot(xi, z)) / den if den > 0.0 else 0.0
+        den = torch.dot(xi, xi)
+        alpha = torch.where(den > 0, torch.dot(xi, z) / torch.where(den > 0, den, 1.0),
+                            torch.zeros_like(den))
         alphas.append(alpha)
         full = tt_full(tangent_block_cores(U, V, dU, alpha), stream)
         X, orth = _retract(full, ranks, retraction, precision, stream)
@@ -195,4 +198,6 @@ def rgrad(values, idx, shape, ranks, steps=40, retraction="URV", p_obs=None,
     plan.close(stream)
     if plan2 is not None:
         plan2.close(stream)
+    losses = [float(v) for v in torch.stack(losses).double().cpu()]
+    alphas = [float(v) for v in torch.stack(alphas).double().cpu()] if alphas else []
     return X, losses, alphas
