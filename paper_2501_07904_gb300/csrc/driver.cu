@@ -441,6 +441,8 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   double* d_scal = scal.as<double>();
   double* d_x2first = d_scal;            // ||A||^2 when the first step is sketched
   double* d_carry2 = d_scal + 4;         // per step: ||carry||^2 (sum of squares of stored values)
+  double* d_tdirect = d_scal + 4 + TT_MAXD;  // per step: a directly summed tail (identity sketch)
+  std::vector<char> has_direct(d, 0);
   int* d_err = (int*)(d_scal + 1);       // set by a tensor-core kernel whose bounded wait ran out
   TT_CK(cudaMemsetAsync(d_scal, 0, sizeof(double) * (4 + 2 * TT_MAXD), st), "memset");
   int* herr = pinned_err();
@@ -930,6 +932,8 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
       } else {
         wsz = std::max(cfg.urv ? mm_ws<W>(mm, m, r, l, false) : mm_ws<W>(mm, r, n, l, false),
                        cfg.urv ? mm_ws<W>(mm, r, n, l, false) : mm_ws<W>(mm, m, r, l, false));
+        if (l >= no_g && r < l)  // the identity sketch's residual product
+          wsz = std::max(wsz, cfg.urv ? mm_ws<W>(mm, m, l, r, false) : mm_ws<W>(mm, n, l, r, false));
       }
       if (sq_pass) wsz = std::max(wsz, ttk::sumsq_ws_bytes(crow * ccol));
       if (wsz > ws_bytes) {
@@ -965,6 +969,33 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {Bm, l, false}, r, n, l, carry.as<W>(), n, nullptr, false,
                         carry_sq, ws.p, precise, true, true, false), "carry (B Z1)^T");
       tm.end();
+      // Omega = I: W spans the whole row space (mu^2 = 0), so the step's
+      // error is ||B - B Z1 Z1^T||^2, summed directly from that residual
+      // instead of as ||C||^2 - ||carry||^2, where the products' rounding
+      // (~1e-6 of ||C||^2 on the tensor cores) swamps a small tail
+      if (!exact && l >= no_g && r < l && !cfg.l11 && ftail[s] < 0.0) {
+        const int64_t nbl = (cfg.urv ? m : n) * l;
+        const size_t pbytes = align256(ttk::diff_sumsq_parts_bytes());
+        Buf trail(&al);
+        TT_ALLOC(trail, align256((size_t)nbl * sizeof(W)) + pbytes + 2 * sizeof(double));
+        W* Pm = trail.as<W>();
+        double* part = (double*)((char*)trail.p + align256((size_t)nbl * sizeof(W)));
+        double* pair = (double*)((char*)part + pbytes);
+        // P = carry Z1^T in B's layout (URV: m x l row-major; ULV: B^T, n x l)
+        if (cfg.urv)
+          TT_CK(mm_run<W>(mm, {carry.as<W>(), r, true}, {Zp, ldz, false}, m, l, r, Pm, l, nullptr,
+                          false, nullptr, ws.p, precise, true, true, false),
+                "carry Z1^T");
+        else
+          TT_CK(mm_run<W>(mm, {carry.as<W>(), n, false}, {Zp, ldz, false}, n, l, r, Pm, l, nullptr,
+                          false, nullptr, ws.p, precise, true, true, false),
+                "carry^T Z1^T");
+        TT_CK(ttk::diff_sumsq(Bm, Pm, W64, nbl, part, true, st), "residual of the identity sketch");
+        TT_CK(ttk::sum_pairs(part, pair, st), "residual of the identity sketch");
+        TT_CK(cudaMemcpyAsync(d_tdirect + s, pair, sizeof(double), cudaMemcpyDeviceToDevice, st),
+              "residual of the identity sketch");
+        has_direct[s] = 1;
+      }
       tm.begin(s, TT_PH_CORE);
       if (cfg.urv)
         TT_CK(mm_run<W>(mm, {Zp, ldz, false}, {Wm, l, false}, r, n, l, core.as<W>(), n, nullptr, false,
@@ -1014,8 +1045,10 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     cbuf.p = whole.release();
   }
   cores[cfg.urv ? 0 : d - 1] = cbuf.release();
-  double h_carry2[TT_MAXD];
+  double h_carry2[TT_MAXD], h_tdirect[TT_MAXD];
   TT_CK(cudaMemcpyAsync(h_carry2, d_carry2, sizeof(double) * (d - 1), cudaMemcpyDeviceToHost, st), "tails");
+  TT_CK(cudaMemcpyAsync(h_tdirect, d_tdirect, sizeof(double) * (d - 1), cudaMemcpyDeviceToHost, st),
+        "direct tails");
   TT_CK(cudaMemcpyAsync(herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "error word");
   {
     const double t0 = host_us();
@@ -1027,7 +1060,7 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
   for (int s = 0; s < d - 1; ++s) {
     const int k = cfg.urv ? d - s : s + 1;
     const int u = cfg.urv ? k - 1 : k;
-    const double t = ftail[s] >= 0.0 ? ftail[s] : x2s[s] - h_carry2[s];
+    const double t = ftail[s] >= 0.0 ? ftail[s] : has_direct[s] ? h_tdirect[s] : x2s[s] - h_carry2[s];
     out->tail_sq[u - 1] = t > 0.0 ? t : 0.0;
   }
   out->norm_sq = normA2;
