@@ -183,6 +183,88 @@ def usv_plus(X, delta2, r_fixed, r_max, q=USVP_ITERS, mu2=0.0):
     return V, np.asarray(tails)
 
 
+LURV_ITERS = 8
+
+
+def givens(a, b):
+    """(c, s) with [c s; -s c] [a; b] = [rho; 0], rho = hypot(a, b) >= 0
+    ((1, 0) when a = b = 0)."""
+    rho = float(np.hypot(a, b))
+    if rho == 0.0:
+        return 1.0, 0.0
+    return a / rho, b / rho
+
+
+def lurv(X, delta2, r_fixed, r_max, q=LURV_ITERS, mu2=0.0, return_r=False):
+    """Low-rank revealing URV with Givens rotations, warm-started from a
+    pivoted QR (the family of Fierro and Hansen's low-rank UTV algorithms that
+    the paper's TT-URV experiments run as the inner factor, Sec. 4):
+    X (N_o x N_b, basis on the column side) = Q R V^T, started from the
+    column-pivoted QR X Pi = Q R (V = Pi).  For i = 0, 1, ...:
+
+    * the trailing block T = R[i:, i:] gets its dominant right singular
+      vector estimated: start T^T T e_j for the column j of T of largest norm
+      (lowest index on ties), then q power iterations v <- T^T T v / ||.||;
+    * v is rotated onto the first coordinate of the block by Givens rotations
+      on columns (j-1, j), j from the last down to i+1 (applied to R and V);
+      each leaves a fill at R[j, j-1], removed at once by a Givens rotation on
+      rows (j-1, j), which keeps R upper trapezoidal;
+    * the error of keeping i + 1 basis vectors is mu2 + ||R[:, i+1:]||_F^2.
+
+    Stops at the fixed rank (clamped to r_max) or at the first i >= 1 whose
+    error is at most delta2.  Returns (V[:, :r], tails [tail(0) .. tail(r)])
+    with tail(0) = mu2 + ||R||^2.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    n_o, n_b = X.shape
+    _, R, p1 = householder_qr(X, pivoting=True)
+    R = np.array(R, dtype=np.float64)
+    k = R.shape[0]
+    V = np.zeros((n_b, n_b))
+    V[p1, np.arange(n_b)] = 1.0
+    target = None if r_fixed is None else max(1, min(int(r_fixed), r_max))
+    tails = [mu2 + float(np.sum(R * R))]
+    i = 0
+    while i < r_max:
+        if target is not None and i >= target:
+            break
+        if target is None and i >= 1 and tails[-1] <= delta2:
+            break
+        if i < k:
+            T = R[i:, i:]
+            cn = np.einsum("ij,ij->j", T, T)
+            j0 = int(np.argmax(cn))
+            v = T.T @ T[:, j0]
+            nv = float(np.linalg.norm(v))
+            if nv > 0.0:
+                v = v / nv
+                for _ in range(q):
+                    w = T.T @ (T @ v)
+                    nw = float(np.linalg.norm(w))
+                    if nw == 0.0:
+                        break
+                    v = w / nw
+                # rotate v onto e_1 of the block: columns (j-1, j), bottom up
+                for jj in range(n_b - i - 1, 0, -1):
+                    c, s_ = givens(v[jj - 1], v[jj])
+                    v[jj - 1], v[jj] = c * v[jj - 1] + s_ * v[jj], 0.0
+                    a, b = i + jj - 1, i + jj
+                    Ra, Rb = R[:, a].copy(), R[:, b].copy()
+                    R[:, a], R[:, b] = c * Ra + s_ * Rb, -s_ * Ra + c * Rb
+                    Va, Vb = V[:, a].copy(), V[:, b].copy()
+                    V[:, a], V[:, b] = c * Va + s_ * Vb, -s_ * Va + c * Vb
+                    if b < k:  # fill at R[b, a]: rotate rows (a, b)
+                        cr, sr = givens(R[a, a], R[b, a])
+                        Ra, Rb = R[a, :].copy(), R[b, :].copy()
+                        R[a, :], R[b, :] = cr * Ra + sr * Rb, -sr * Ra + cr * Rb
+                        R[b, a] = 0.0
+        i += 1
+        tails.append(mu2 + float(np.sum(R[:, i:] ** 2)))
+    if return_r:
+        return V[:, :i], np.asarray(tails), R, V
+    return V[:, :i], np.asarray(tails)
+
+
 def choose_rank(tails, delta2, r_fixed, r_max):
     """Reading S3 of the rule in Sec. 3.1: smallest r >= 1 with tail(r) <= delta^2."""
     if r_fixed is not None:
@@ -213,9 +295,9 @@ def factor_step(X, delta2, r_fixed, r_prev, seed, step, kind="qlp",
     while True:
         if path == "sketch":
             W, B, mu2 = range_step(X, l, seed, step, q)
-        if kind == "usvp":
+        if kind in ("usvp", "lurv"):
             r_max = min(B.shape[1], n_o, n_b)
-            Z, tails = usv_plus(B, delta2, r_fixed, r_max, usvp_q, mu2)
+            Z, tails = (usv_plus if kind == "usvp" else lurv)(B, delta2, r_fixed, r_max, usvp_q, mu2)
             r = Z.shape[1]
             if (path == "sketch" and l < min(n_b, n_o) and r_fixed is None
                     and (r > l - p or tails[r] > delta2)):
@@ -332,9 +414,10 @@ def tt_sweep(A, eps=None, ranks=None, variant="URV", kind="qlp", direction=None,
 
 def tt_utv(A, eps=None, ranks=None, variant="URV", inner="qlp", **kw):
     """TT-URV (right-to-left, Alg. 3) or TT-ULV (left-to-right, Alg. 1/2).
-    inner: "qlp" (pivoted QLP, the default) or "usvp" (USV-plus-style
-    deflation, usv_plus)."""
-    assert inner in ("qlp", "usvp")
+    inner: "qlp" (pivoted QLP, the default), "usvp" (USV-plus-style
+    deflation, usv_plus) or "lurv" (Givens-based low-rank URV, lurv); the
+    last two take usvp_q power iterations per basis vector."""
+    assert inner in ("qlp", "usvp", "lurv")
     return tt_sweep(A, eps=eps, ranks=ranks, variant=variant, kind=inner, **kw)
 
 
