@@ -103,3 +103,15 @@ def test_sketch_path_and_fixed_ranks():
     assert res["ranks"] == [1, 3, 4, 1]
     assert res["steps"][0]["path"] == "sketch"
     assert otc.rse(A, res["cores"]) < 1e-3
+
+
+def test_start_vector_with_no_iterations():
+    # q = 0: the first basis vector is X^T X e_j / ||.|| for the column j of X
+    # of largest norm (the warm start's first pivot)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((25, 8)) @ rng.standard_normal((8, 8))
+    V, _ = otc.lurv(X, 0.0, 2, 8, q=0)
+    j = int(np.argmax(np.sum(X * X, axis=0)))
+    v = X.T @ X[:, j]
+    v /= np.linalg.norm(v)
+    assert abs(abs(float(v @ V[:, 0])) - 1.0) < 1e-12
