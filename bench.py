@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
-    ap.add_argument("--inner", default="qlp", choices=["qlp", "usvp"],
+    ap.add_argument("--inner", default="qlp", choices=["qlp", "usvp", "lurv"],
                     help="small rank-revealing factor of each sweep step")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain-FP32 comparison timed beside a mixed-precision run")
@@ -392,7 +392,7 @@ def run_ours(args, wl, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl)
+        cpu = cpu_baseline(wl, inner=args.inner)
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
@@ -452,6 +452,7 @@ def accuracy(tu, torch, A, res, workload):
         g = np.load(gold)
         vals = tu.tt_eval_at([c.float() for c in res.cores],
                              torch.from_numpy(g["sample_idx"]).to(A.device)).double().cpu().numpy()
+        out["oracle_inner"] = "qlp"  # the stored expected values come from the pivoted-QLP oracle
         out["oracle_ranks"] = [int(x) for x in g["ranks"]]
         out["oracle_rse"] = float(g["rse"])
         # tails ||E_k||^2 / ||A||^2 per unfolding k = 1..d-1 beside the oracle's
@@ -474,14 +475,14 @@ def cpu_sample(wl, steps=1):
     return s, dims
 
 
-def cpu_baseline(wl, repeats=1):
+def cpu_baseline(wl, repeats=1, inner="qlp"):
     from oracle import tt as otc  # the FP64 oracle: only this leg of bench.py runs it
 
     s, dims = cpu_sample(wl)
     A = make_input(wl)[:s].astype(np.float64)
     t0 = time.perf_counter()
     for _ in range(repeats):
-        otc.tt_utv(A, eps=wl["eps"], variant=wl["variant"])
+        otc.tt_utv(A, eps=wl["eps"], variant=wl["variant"], inner=inner)
     dt = (time.perf_counter() - t0) / repeats
     nbytes = A.size * 4
     return {"value": round(nbytes / dt / 1e9, 4), "unit": "GB/s", "cores": os.cpu_count(),
@@ -500,10 +501,10 @@ def run_reference(args, wl, rank, world):
     A = make_input(wl)[:s].astype(np.float64)
     nbytes = A.size * 4
     for _ in range(min(args.warmup, 1)):
-        otc.tt_utv(A, eps=wl["eps"], variant=wl["variant"])
+        otc.tt_utv(A, eps=wl["eps"], variant=wl["variant"], inner=args.inner)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        otc.tt_utv(A, eps=wl["eps"], variant=wl["variant"])
+        otc.tt_utv(A, eps=wl["eps"], variant=wl["variant"], inner=args.inner)
     dt = (time.perf_counter() - t0) / args.steps
     value = nbytes / dt / 1e9
     sample = (f"first {s} of {dims[0]} mode-1 slices ({s}x{'x'.join(map(str, dims[1:]))} f32, "

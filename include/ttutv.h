@@ -126,8 +126,8 @@ typedef struct {
                                Omega = I.  Default 0. */
   int32_t inner;            /* tt_inner: the small rank-revealing factor of tt_utv, default
                                TT_INNER_QLP; ignored by tt_svd */
-  int32_t usvp_iters;       /* TT_INNER_USVP: power iterations per basis vector, in [0, 64],
-                               default 8 */
+  int32_t usvp_iters;       /* TT_INNER_USVP, TT_INNER_LURV: power iterations per basis vector,
+                               in [0, 64], default 8 */
   int32_t lhat;             /* tt_lhat: the kept middle block of TT-ULV right-to-left (the
                                appendix's Alg. 4), default TT_LHAT_FULL */
 } tt_opts;
@@ -157,8 +157,19 @@ typedef enum { TT_LHAT_FULL = 0, TT_LHAT_L11 = 1 } tt_lhat;
  *                  twice against the basis; the error of keeping i vectors is
  *                  ||X - X V_i V_i^T||_F^2 (plus the sketch's range miss); the
  *                  rank is fixed or the first i with error <= eps_k^2.  One CTA,
- *                  sequential in the rank: slower than the QLP. */
-typedef enum { TT_INNER_QLP = 0, TT_INNER_USVP = 1 } tt_inner;
+ *                  sequential in the rank: slower than the QLP.
+ *  TT_INNER_LURV : low-rank revealing URV with Givens rotations (the
+ *                  Fierro-Hansen family the paper runs inside TT-URV in Sec. 4),
+ *                  warm-started from the column-pivoted QR X Pi = Q R (V = Pi):
+ *                  for i = 0, 1, ... the dominant right singular vector of the
+ *                  trailing block R(i:, i:) is estimated (its column of largest
+ *                  norm, then usvp_iters power iterations), rotated onto e_i by
+ *                  Givens rotations on adjacent columns of R and V, and the fill
+ *                  below the diagonal removed by rotations of adjacent rows; the
+ *                  error of keeping i vectors is ||R(:, i:)||_F^2 (plus the
+ *                  sketch's range miss); the rank is fixed or the first i with
+ *                  error <= eps_k^2.  One CTA, sequential in the rank. */
+typedef enum { TT_INNER_QLP = 0, TT_INNER_USVP = 1, TT_INNER_LURV = 2 } tt_inner;
 
 /* Fill *o with the defaults listed above. */
 void tt_opts_default(tt_opts* o);

@@ -33,7 +33,7 @@ for _code, _name in STATUS.items():
     globals()[_name] = _code
 PRECISION = {"fp64": 0, "fp32": 1, "mixed": 2}
 SMALL = {"auto": 0, "fp32": 1, "fp64": 2, "df": 3}
-INNER = {"qlp": 0, "usvp": 1}
+INNER = {"qlp": 0, "usvp": 1, "lurv": 2}
 TT_F32, TT_F64 = 0, 1
 TT_URV, TT_ULV = 0, 1
 TT_RL, TT_LR = 0, 1
@@ -330,8 +330,10 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
     tensor and returns its cores read back as cores of ``A`` (Remark after
     Thm 3.2: URV then gives a left-orthogonal TT).  ``power_iters`` adds q
     subspace iterations to every sketched range.  ``inner`` picks the small
-    rank-revealing factor: "qlp" (pivoted QLP) or "usvp" (USV-plus-style
-    deflation with ``usvp_iters`` power iterations per basis vector).
+    rank-revealing factor: "qlp" (pivoted QLP), "usvp" (USV-plus-style
+    deflation) or "lurv" (Givens-based low-rank URV warm-started from a
+    pivoted QR), the last two with ``usvp_iters`` power iterations per basis
+    vector.
     ``lhat="l11"`` with variant "ULV" and direction "RL" runs the appendix's
     Alg. 4 as printed: the carry keeps L_11 alone and the default weights are
     1/(d-1).

@@ -542,7 +542,9 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
     ttk::SmallParams prm;
     memset(&prm, 0, sizeof(prm));
     prm.mode = cfg.svd ? ttk::SM_JACOBI
-                       : (o.inner == TT_INNER_USVP ? ttk::SM_USVP : ttk::SM_QLP);
+                       : (o.inner == TT_INNER_USVP   ? ttk::SM_USVP
+                          : o.inner == TT_INNER_LURV ? ttk::SM_LURV
+                                                     : ttk::SM_QLP);
     prm.usvp_iters = o.usvp_iters;
     prm.l11 = cfg.l11 ? 1 : 0;
     prm.jacobi_sweeps = jacobi_sweeps();
@@ -1095,7 +1097,8 @@ tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims,
     return fail(TT_EINVAL, "bad orth_precision");
   if (o.reverse != 0 && o.reverse != 1) return fail(TT_EINVAL, "reverse must be 0 or 1");
   if (o.power_iters < 0 || o.power_iters > 8) return fail(TT_EINVAL, "power_iters must be in [0, 8]");
-  if (o.inner != TT_INNER_QLP && o.inner != TT_INNER_USVP) return fail(TT_EINVAL, "bad inner factor");
+  if (o.inner != TT_INNER_QLP && o.inner != TT_INNER_USVP && o.inner != TT_INNER_LURV)
+    return fail(TT_EINVAL, "bad inner factor");
   if (o.usvp_iters < 0 || o.usvp_iters > 64) return fail(TT_EINVAL, "usvp_iters must be in [0, 64]");
   if (o.lhat != TT_LHAT_FULL && o.lhat != TT_LHAT_L11) return fail(TT_EINVAL, "bad lhat");
   if (o.lhat == TT_LHAT_L11 && o.inner != TT_INNER_QLP)

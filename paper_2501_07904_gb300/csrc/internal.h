@@ -73,7 +73,7 @@ cudaError_t tc_gemm(Mat<float> A, Mat<float> B, int64_t M, int64_t N, int64_t K,
 cudaError_t wait_selftest(bool arrive, uint64_t limit_ns, int* err, cudaStream_t st);
 
 // Small single-CTA factorizations of an n x n FP64 Gram matrix (n <= 256).
-enum SmallMode { SM_QLP = 0, SM_JACOBI = 1, SM_ORTH = 2, SM_USVP = 3 };
+enum SmallMode { SM_QLP = 0, SM_JACOBI = 1, SM_ORTH = 2, SM_USVP = 3, SM_LURV = 4 };
 struct SmallParams {
   int n;                  // Gram size
   int mode;               // SmallMode
@@ -89,7 +89,7 @@ struct SmallParams {
   const double* Gw;       // QLP/Jacobi on a sketch: W^T W of the range basis, or null
   int range_exact;        // 1: the sketch is the identity, so W spans X's row space (mu^2 = 0)
   int df_math;            // with fp64_math: run the fast path in double-float (n <= 64)
-  int usvp_iters;         // SM_USVP: power iterations per vector
+  int usvp_iters;         // SM_USVP / SM_LURV: power iterations per vector
   // SM_QLP, appendix Alg. 4 with L_11 kept alone: rank by the error
   // mu^2 + ||L||^2 - ||L_11||^2, and Tl (n x r, ld = ldz, Z's type) receives
   // T with B T = U_1 L_11 (runs on the generic kernel)

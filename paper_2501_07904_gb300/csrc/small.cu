@@ -28,6 +28,16 @@
 //             (the Gram, deflated after each vector by a rank-two update), so
 //             the error of rank i is mu^2 + trace(D^T D).  Stops at the
 //             fixed rank, or at the first i >= 1 with error <= delta^2.
+//  SM_LURV    low-rank revealing URV with Givens rotations (the Fierro-Hansen
+//             family the paper runs inside TT-URV in Sec. 4), warm-started
+//             from the pivoted QR X Pi = Q R (the pivoted Cholesky of G), V =
+//             Pi.  Vector i: the dominant right singular vector v of the
+//             trailing block R(i:, i:) is estimated (start from the block's
+//             column of largest norm, then q power iterations), rotated onto
+//             e_i by column Givens rotations (pairs (c, c+1), c from n-2 down
+//             to i, on R and V), and the subdiagonal fill each leaves is
+//             chased away by a row rotation of the same pair; the error of
+//             keeping i+1 vectors is mu^2 + s1 + ||R(:, i+1:)||_F^2.
 #include <math.h>
 
 #include "internal.h"
@@ -570,6 +580,230 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
       info->k1 = r;
       info->nsteps = r;
       info->s1 = 0.0;
+      info->tail = tail;
+    }
+    return;
+  }
+
+  if (prm.mode == SM_LURV) {
+    // The whole chase of one vector is R <- Qr R G with G the column rotations
+    // (fixed by v alone) and Qr the row rotations.  The row-rotation angles
+    // follow from one scalar recurrence: at pair (p, p+1) the rotation zeroes
+    // s_p rho_{p+1} against y_p = c_p R(p,p) + s_p R(p,p+1) (row p seen through
+    // the column rotations right of it), giving rho_p^2 = y_p^2 + s_p^2
+    // rho_{p+1}^2.  So the column rotations run first (one thread per row of
+    // R and of V), the recurrence next (one thread, FP64 fused multiply-adds),
+    // and the row rotations last (one thread per column); the product equals
+    // the interleaved chase, and the entries below the diagonal, zero in exact
+    // arithmetic, are set to zero.
+    __shared__ T lv[kMaxSmall], lw[kMaxSmall], lt[kMaxSmall], lcn[kMaxSmall];
+    __shared__ T lcs[kMaxSmall], lsn[kMaxSmall], lcr[kMaxSmall], lsr[kMaxSmall];
+    __shared__ T ldg[kMaxSmall], lx[kMaxSmall], ly[kMaxSmall];
+    __shared__ double lq[kMaxSmall];
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5, half = nt >> 1;
+    double s1;
+    const int k1 = pivoted_cholesky(A, n, perm1, prm.piv_tol, s1, redt, redi, redd);
+    // R and V column-major: entry (p, c) at [c * n + p]
+    T* Rt = Mq;
+    T* Vt = Qe;
+    for (int e = tid; e < n * n; e += nt) {
+      const int c = e / n, p = e % n;
+      Rt[e] = A[p * n + c];
+      Vt[e] = perm1[c] == p ? T(1) : T(0);
+    }
+    __syncthreads();
+    const int rmax = max(1, fixed ? rt : min(prm.r_cap, n));
+    const int q = max(0, prm.usvp_iters);
+    const double base = mu2 + s1;
+    // lcn[c] = ||R(i0:k1, c)||^2 for c >= i0; returns sum_{c >= i0} ||R(:, c)||^2
+    auto col_sums = [&](int i0) -> double {
+      double part = 0.0;
+      for (int c = i0 + warp; c < n; c += nwarps) {
+        T sa = T(0), st = T(0);
+        const int pe = min(c + 1, k1);
+        for (int p = lane; p < pe; p += 32) {
+          const T x = Rt[c * n + p];
+          sa += x * x;
+          if (p >= i0) st += x * x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          sa += __shfl_xor_sync(0xffffffffu, sa, o);
+          st += __shfl_xor_sync(0xffffffffu, st, o);
+        }
+        if (lane == 0) {
+          lcn[c] = st;
+          part += (double)sa;
+        }
+      }
+      return block_sum(part, redd);
+    };
+    // dst[c] = sum_p R(p, c) src[p] over rows [i0, k1), columns c >= i0
+    auto rt_mv = [&](T* dst, const T* src, int i0) {
+      for (int c = i0 + warp; c < n; c += nwarps) {
+        T acc = T(0);
+        const int pe = min(c + 1, k1);
+        for (int p = i0 + lane; p < pe; p += 32) acc += Rt[c * n + p] * src[p];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) dst[c] = acc;
+      }
+      __syncthreads();
+    };
+    // dst[p] = sum_c R(p, c) src[c] over rows [i0, k1), columns c >= i0 (the
+    // zeros below the diagonal included, so that a warp reads one column at a time)
+    auto r_mv = [&](T* dst, const T* src, int i0) {
+      for (int p = i0 + tid; p < k1; p += nt) {
+        T acc = T(0);
+        for (int c = i0; c < n; ++c) acc += Rt[c * n + p] * src[c];
+        dst[p] = acc;
+      }
+      __syncthreads();
+    };
+    auto sumsq = [&](const T* x, int i0) -> T {
+      T s = T(0);
+      for (int c = i0 + tid; c < n; c += nt) s += x[c] * x[c];
+      return block_sum(s, redt);
+    };
+    double tail = base + col_sums(0);
+    if (tid == 0) info->tails[0] = tail;
+    int i = 0;
+    while (i < rmax) {
+      if (fixed ? i >= rt : (i >= 1 && tail <= delta2)) break;
+      bool rot = false;
+      if (i < k1) {
+        T best = lowest_value<T>();
+        int bi = 0x7fffffff;
+        for (int c = i + tid; c < n; c += nt)
+          if (lcn[c] > best) {
+            best = lcn[c];
+            bi = c;
+          }
+        T cmax;
+        int j0;
+        block_argmax(best, bi, redt, redi, cmax, j0);
+        if (cmax > T(0)) {
+          // v = T^T T e_j0 / ||.||, then q power iterations v <- T^T T v / ||.||
+          for (int p = i + tid; p < k1; p += nt) lw[p] = Rt[j0 * n + p];
+          __syncthreads();
+          rt_mv(lv, lw, i);
+          const T nv = sumsq(lv, i);
+          rot = nv > T(0);
+          if (rot) {
+            const T inv = T(1) / sqrt(nv);
+            for (int c = i + tid; c < n; c += nt) lv[c] *= inv;
+            __syncthreads();
+            for (int it = 0; it < q; ++it) {
+              r_mv(lw, lv, i);
+              rt_mv(lt, lw, i);
+              const T nw = sumsq(lt, i);
+              if (!(nw > T(0))) break;  // T^T T v = 0: keep v
+              const T iw = T(1) / sqrt(nw);
+              for (int c = i + tid; c < n; c += nt) lv[c] = lt[c] * iw;
+              __syncthreads();
+            }
+          }
+        }
+      }
+      if (rot) {
+        // column rotations: (c_c, s_c) rotates (v_c, ||v(c+1:)||) onto
+        // (||v(c:)||, 0); the last pair takes v_{n-1} itself
+        for (int c = i + tid; c < n; c += nt) {
+          double s = 0.0;
+          for (int t = n - 1; t >= c; --t) s += (double)lv[t] * (double)lv[t];
+          lq[c] = s;
+        }
+        __syncthreads();
+        for (int c = i + tid; c < n - 1; c += nt) {
+          const double h = sqrt(lq[c]);
+          const double b = c == n - 2 ? (double)lv[n - 1] : sqrt(lq[c + 1]);
+          lcs[c] = h > 0.0 ? (T)((double)lv[c] / h) : T(1);
+          lsn[c] = h > 0.0 ? (T)(b / h) : T(0);
+        }
+        __syncthreads();
+        if (tid < half) {
+          for (int p = tid; p < k1; p += half) {
+            T carry = Rt[(n - 1) * n + p];
+            ldg[p] = Rt[p * n + p];
+            for (int c = n - 2; c >= i; --c) {
+              const T a = Rt[c * n + p], cs = lcs[c], sn = lsn[c];
+              const T na = cs * a + sn * carry;
+              if (c == p) {
+                lx[p] = carry;
+                ly[p] = na;
+              }
+              Rt[(c + 1) * n + p] = -sn * a + cs * carry;
+              carry = na;
+            }
+            Rt[i * n + p] = carry;
+          }
+        } else {
+          for (int p = tid - half; p < n; p += nt - half) {
+            T carry = Vt[(n - 1) * n + p];
+            for (int c = n - 2; c >= i; --c) {
+              const T a = Vt[c * n + p], cs = lcs[c], sn = lsn[c];
+              Vt[(c + 1) * n + p] = -sn * a + cs * carry;
+              carry = cs * a + sn * carry;
+            }
+            Vt[i * n + p] = carry;
+          }
+        }
+        __syncthreads();
+        // row rotations on (p, p+1), p from P0 down to i (rows below k1 only)
+        const int P0 = min(n - 2, k1 - 2);
+        if (P0 >= i) {
+          const double rc0 = P0 + 1 <= n - 2 ? (double)ly[P0 + 1] : (double)ldg[P0 + 1];
+          if (tid == 0) {
+            double acc = rc0 * rc0;
+            for (int p = P0; p >= i; --p) {
+              const double sp = (double)lsn[p], yp = (double)ly[p];
+              acc = fma(yp, yp, sp * sp * acc);
+              lq[p] = acc;
+            }
+          }
+          __syncthreads();
+          for (int p = i + tid; p <= P0; p += nt) {
+            const double rho = sqrt(lq[p]);
+            const double prev = p == P0 ? rc0 : sqrt(lq[p + 1]);
+            const double b = (double)lsn[p] * prev;
+            lcr[p] = rho > 0.0 ? (T)((double)ly[p] / rho) : T(1);
+            lsr[p] = rho > 0.0 ? (T)(b / rho) : T(0);
+          }
+          __syncthreads();
+          for (int c = i + tid; c < n; c += nt) {
+            T* col = Rt + (size_t)c * n;
+            T carry = col[P0 + 1];
+            for (int p = P0; p >= i; --p) {
+              const T a = col[p], cr = lcr[p], sr = lsr[p];
+              col[p + 1] = -sr * a + cr * carry;
+              carry = cr * a + sr * carry;
+            }
+            col[i] = carry;
+            for (int p = max(c + 1, i); p < k1; ++p) col[p] = T(0);
+          }
+          __syncthreads();
+        }
+      }
+      ++i;
+      tail = base + col_sums(i);
+      if (tid == 0) info->tails[i] = tail;
+    }
+    const int r = i;
+    __syncthreads();
+    for (int e = tid; e < n * ldz; e += nt) {
+      const int row = e / ldz, c = e % ldz;
+      T z = T(0);
+      if (c < r) {
+        if (prm.Gw)
+          for (int k = row; k < n; ++k) z += Ti[row * n + k] * Vt[c * n + k];
+        else
+          z = Vt[c * n + row];
+      }
+      Z[(size_t)row * ldz + c] = (ZT)z;
+    }
+    if (tid == 0) {
+      info->r = r;
+      info->k1 = k1;
+      info->nsteps = r;
+      info->s1 = s1;
       info->tail = tail;
     }
     return;

@@ -5,7 +5,7 @@ their 16-byte alignment, gathered copies) is verified before it is made, and
 a violation is counted and skipped instead of performed.  The whole API is
 driven through that build in a child process on small cases of every path --
 exact, sketched, mixed-precision and FP64 sweeps, TT-SVD, reversed sweeps,
-USV-plus, contraction and RSE, orthogonalization, the masked evaluation, its
+USV-plus and the Givens URV, contraction and RSE, orthogonalization, the masked evaluation, its
 two-frame backward and the tangent projection -- and the results are checked
 against the FP64 oracle and the counters must read zero.
 """
@@ -43,8 +43,9 @@ for prec in ("fp64", "fp32", "mixed"):
     assert res.ranks == ref["ranks"]
 res = tu.tt_svd(A, eps=1e-4)
 assert res.ranks == ref["ranks"]
-res = tu.tt_utv(A, eps=1e-4, variant="ULV", precision="fp64", inner="usvp")
-assert res.ranks == ref["ranks"]
+for inner in ("lurv", "usvp"):
+    res = tu.tt_utv(A, eps=1e-4, variant="ULV", precision="fp64", inner=inner)
+    assert res.ranks == ref["ranks"], inner
 full = tu.tt_full(res.cores)
 assert float((full - A).norm() / A.norm()) <= 1e-4
 err2, n2 = tu.tt_rse(A, res.cores)

@@ -321,7 +321,8 @@ def test_alg4_l11_matches_oracle(tu, precision, tol, l_full):
 def test_alg4_l11_argument_checks(tu):
     A = torch.from_numpy(RAGGED.astype(np.float32)).cuda()
     for kw in (dict(variant="URV", direction="RL"), dict(variant="ULV", direction="LR"),
-               dict(variant="ULV", direction="RL", inner="usvp")):
+               dict(variant="ULV", direction="RL", inner="usvp"),
+               dict(variant="ULV", direction="RL", inner="lurv")):
         with pytest.raises(tu.TTError) as ei:
             tu.tt_utv(A, eps=1e-2, lhat="l11", **kw)
         assert ei.value.status == tu.TT_EINVAL
