@@ -49,7 +49,8 @@ static inline unsigned int bc_read_tu(int* line, bool reset) {
 // copied to the host once per sweep step (the next step's shapes need r).
 struct StepInfo {
   int32_t r;         // chosen rank (or numerical rank k1 for the orthonormalization kernel)
-  int32_t status;    // bit 0: non-finite input, bit 1: Jacobi not converged
+  int32_t status;    // bit 0: non-finite input, bit 1: Jacobi not converged;
+                     // bits 2-3 (Givens URV): R, or R and V, held in shared memory
   int32_t k1;        // steps taken by the pivoted Cholesky (numerical rank of the Gram)
   int32_t nsteps;    // QLP / Jacobi steps or sweeps done
   double x2;         // ||X||_F^2 of the factored matrix

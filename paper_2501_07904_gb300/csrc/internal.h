@@ -96,6 +96,7 @@ struct SmallParams {
   int l11;
   void* Tl;
   int jacobi_sweeps;      // SM_JACOBI sweep cap (0: the default 60)
+  int lurv_smem;          // SM_LURV, set by the launcher: 1 R, 2 R and V in dynamic shared memory
 };
 size_t small_ws_bytes(int n, bool fp64);
 // Register-resident fast path (small_fast.cu) for SM_QLP / SM_ORTH with

@@ -55,20 +55,21 @@ __device__ __forceinline__ void swap_vals(T& a, T& b) {
 }
 
 // Block-cooperative pivoted Cholesky of the symmetric n x n matrix A (full
-// storage, row-major).  Pivot = largest remaining diagonal (lowest index on
+// storage, row-major, leading dimension lda >= n; 0 means n).  Pivot = largest remaining diagonal (lowest index on
 // ties); stops when it is not above tol_rel * (largest initial diagonal).
 // On return rows 0..k1-1 of A hold R_1 (upper trapezoidal, columns in pivot
 // order), everything else is zero; perm[i] = original index of position i;
 // rem = remaining Schur-complement diagonal (clamped at 0), in FP64.
 template <typename T>
 __device__ int pivoted_cholesky(T* A, int n, int* perm, double tol_rel, double& rem, T* redt,
-                                int* redi, double* redd) {
+                                int* redi, double* redd, int lda = 0) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (lda < n) lda = n;
   for (int i = tid; i < n; i += nt) perm[i] = i;
   T v = lowest_value<T>();
   int idx = 0x7fffffff;
   for (int i = tid; i < n; i += nt) {
-    const T a = A[i * n + i];
+    const T a = A[i * lda + i];
     if (a > v) {
       v = a;
       idx = i;
@@ -83,7 +84,7 @@ __device__ int pivoted_cholesky(T* A, int n, int* perm, double tol_rel, double& 
     v = lowest_value<T>();
     idx = 0x7fffffff;
     for (int i = j + tid; i < n; i += nt) {
-      const T a = A[i * n + i];
+      const T a = A[i * lda + i];
       if (a > v) {
         v = a;
         idx = i;
@@ -94,33 +95,33 @@ __device__ int pivoted_cholesky(T* A, int n, int* perm, double tol_rel, double& 
     block_argmax(v, idx, redt, redi, dp, p);
     if (!(dp > T(0)) || !((double)dp > tol_rel * (double)d0)) break;
     if (p != j) {
-      for (int c = tid; c < n; c += nt) swap_vals(A[j * n + c], A[p * n + c]);
+      for (int c = tid; c < n; c += nt) swap_vals(A[j * lda + c], A[p * lda + c]);
       __syncthreads();
-      for (int r = tid; r < n; r += nt) swap_vals(A[r * n + j], A[r * n + p]);
+      for (int r = tid; r < n; r += nt) swap_vals(A[r * lda + j], A[r * lda + p]);
       if (tid == 0) swap_vals(perm[j], perm[p]);
       __syncthreads();
     }
-    const T rjj = sqrt(A[j * n + j]);
+    const T rjj = sqrt(A[j * lda + j]);
     __syncthreads();
-    for (int c = j + tid; c < n; c += nt) A[j * n + c] = (c == j) ? rjj : A[j * n + c] / rjj;
+    for (int c = j + tid; c < n; c += nt) A[j * lda + c] = (c == j) ? rjj : A[j * lda + c] / rjj;
     __syncthreads();
     const int m = n - j - 1;
     for (int e = tid; e < m * m; e += nt) {
       const int r = j + 1 + e / m, c = j + 1 + e % m;
-      A[r * n + c] -= A[j * n + r] * A[j * n + c];
+      A[r * lda + c] -= A[j * lda + r] * A[j * lda + c];
     }
     __syncthreads();
   }
   const int k1 = j;
   double s = 0.0;
   for (int i = k1 + tid; i < n; i += nt) {
-    const double a = (double)A[i * n + i];
+    const double a = (double)A[i * lda + i];
     s += a > 0.0 ? a : 0.0;
   }
   rem = block_sum(s, redd);
   for (int e = tid; e < n * n; e += nt) {
     const int r = e / n, c = e % n;
-    if (r >= k1 || c < r) A[e] = T(0);
+    if (r >= k1 || c < r) A[r * lda + c] = T(0);
   }
   __syncthreads();
   return k1;
@@ -592,24 +593,52 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
     // s_p rho_{p+1} against y_p = c_p R(p,p) + s_p R(p,p+1) (row p seen through
     // the column rotations right of it), giving rho_p^2 = y_p^2 + s_p^2
     // rho_{p+1}^2.  So the column rotations run first (one thread per row of
-    // R and of V), the recurrence next (one thread, FP64 fused multiply-adds),
-    // and the row rotations last (one thread per column); the product equals
-    // the interleaved chase, and the entries below the diagonal, zero in exact
-    // arithmetic, are set to zero.
-    __shared__ T lv[kMaxSmall], lw[kMaxSmall], lt[kMaxSmall], lcn[kMaxSmall];
+    // R and of V), the recurrence next (a warp scan of affine maps), and the
+    // row rotations last (one thread per column); the product equals the
+    // interleaved chase, and the entries below the diagonal, zero in exact
+    // arithmetic, are set to zero.  R (and V) live in shared memory when they
+    // fit, row-major R and column-major V with an odd leading dimension (both
+    // the row-wise and the column-wise walks are then free of bank conflicts);
+    // else column-major in the global work area.
+    __shared__ T lva[kMaxSmall], lvb[kMaxSmall], lw[kMaxSmall], lcn[kMaxSmall];
     __shared__ T lcs[kMaxSmall], lsn[kMaxSmall], lcr[kMaxSmall], lsr[kMaxSmall];
-    __shared__ T ldg[kMaxSmall], lx[kMaxSmall], ly[kMaxSmall];
+    __shared__ T ldg[kMaxSmall], ly[kMaxSmall];
     __shared__ double lq[kMaxSmall];
+    __shared__ T wpart[32];
+    extern __shared__ __align__(16) unsigned char small_dyn[];
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5, half = nt >> 1;
+    const unsigned full = 0xffffffffu;
     double s1;
-    const int k1 = pivoted_cholesky(A, n, perm1, prm.piv_tol, s1, redt, redi, redd);
-    // R and V column-major: entry (p, c) at [c * n + p]
-    T* Rt = Mq;
-    T* Vt = Qe;
+    const int lds = n | 1;
+    T* Rb;     // R(p, c) at Rb[p * rsp + c * rsc]
+    T* Vb;     // V(p, c) at Vb[p + c * vsc]
+    int rsp, rsc, vsc;
+    int k1;
+    if (prm.lurv_smem) {
+      Rb = reinterpret_cast<T*>(small_dyn);
+      rsp = lds;
+      rsc = 1;
+      for (int e = tid; e < n * n; e += nt) Rb[(e / n) * lds + e % n] = A[e];
+      __syncthreads();
+      k1 = pivoted_cholesky(Rb, n, perm1, prm.piv_tol, s1, redt, redi, redd, lds);
+    } else {
+      k1 = pivoted_cholesky(A, n, perm1, prm.piv_tol, s1, redt, redi, redd);
+      Rb = Mq;
+      rsp = 1;
+      rsc = n;
+      for (int e = tid; e < n * n; e += nt) Mq[e] = A[(e % n) * n + e / n];
+    }
+    if (prm.lurv_smem == 2) {
+      Vb = Rb + (size_t)n * lds;
+      vsc = lds;
+    } else {
+      Vb = Qe;
+      vsc = n;
+    }
+    auto R_ = [&](int p, int c) -> T& { return Rb[p * rsp + c * rsc]; };
     for (int e = tid; e < n * n; e += nt) {
       const int c = e / n, p = e % n;
-      Rt[e] = A[p * n + c];
-      Vt[e] = perm1[c] == p ? T(1) : T(0);
+      Vb[p + c * vsc] = perm1[c] == p ? T(1) : T(0);
     }
     __syncthreads();
     const int rmax = max(1, fixed ? rt : min(prm.r_cap, n));
@@ -622,13 +651,13 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
         T sa = T(0), st = T(0);
         const int pe = min(c + 1, k1);
         for (int p = lane; p < pe; p += 32) {
-          const T x = Rt[c * n + p];
+          const T x = R_(p, c);
           sa += x * x;
           if (p >= i0) st += x * x;
         }
         for (int o = 16; o > 0; o >>= 1) {
-          sa += __shfl_xor_sync(0xffffffffu, sa, o);
-          st += __shfl_xor_sync(0xffffffffu, st, o);
+          sa += __shfl_xor_sync(full, sa, o);
+          st += __shfl_xor_sync(full, st, o);
         }
         if (lane == 0) {
           lcn[c] = st;
@@ -637,31 +666,41 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
       }
       return block_sum(part, redd);
     };
-    // dst[c] = sum_p R(p, c) src[p] over rows [i0, k1), columns c >= i0
-    auto rt_mv = [&](T* dst, const T* src, int i0) {
+    // dst[c] = sum_p R(p, c) src[p] over rows [i0, k1), columns c >= i0;
+    // returns ||dst||^2 (every thread, the warps' partials summed in one order)
+    auto rt_mv = [&](T* dst, const T* src, int i0) -> T {
+      T part = T(0);
       for (int c = i0 + warp; c < n; c += nwarps) {
         T acc = T(0);
         const int pe = min(c + 1, k1);
-        for (int p = i0 + lane; p < pe; p += 32) acc += Rt[c * n + p] * src[p];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        for (int p = i0 + lane; p < pe; p += 32) acc += R_(p, c) * src[p];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(full, acc, o);
         if (lane == 0) dst[c] = acc;
+        part += acc * acc;
       }
+      if (lane == 0) wpart[warp] = part;
       __syncthreads();
-    };
-    // dst[p] = sum_c R(p, c) src[c] over rows [i0, k1), columns c >= i0 (the
-    // zeros below the diagonal included, so that a warp reads one column at a time)
-    auto r_mv = [&](T* dst, const T* src, int i0) {
-      for (int p = i0 + tid; p < k1; p += nt) {
-        T acc = T(0);
-        for (int c = i0; c < n; ++c) acc += Rt[c * n + p] * src[c];
-        dst[p] = acc;
-      }
-      __syncthreads();
-    };
-    auto sumsq = [&](const T* x, int i0) -> T {
       T s = T(0);
-      for (int c = i0 + tid; c < n; c += nt) s += x[c] * x[c];
-      return block_sum(s, redt);
+      for (int w = 0; w < nwarps; ++w) s += wpart[w];
+      return s;
+    };
+    // dst[p] = scale * sum_c R(p, c) src[c] over rows [i0, k1), columns
+    // c >= i0 (the zeros below the diagonal included: a warp reads one column
+    // at a time); four partial sums break the dependency chain
+    auto r_mv = [&](T* dst, const T* src, T scale, int i0) {
+      for (int p = i0 + tid; p < k1; p += nt) {
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int c = i0;
+        for (; c + 3 < n; c += 4) {
+          a0 += R_(p, c) * src[c];
+          a1 += R_(p, c + 1) * src[c + 1];
+          a2 += R_(p, c + 2) * src[c + 2];
+          a3 += R_(p, c + 3) * src[c + 3];
+        }
+        for (; c < n; ++c) a0 += R_(p, c) * src[c];
+        dst[p] = ((a0 + a1) + (a2 + a3)) * scale;
+      }
+      __syncthreads();
     };
     double tail = base + col_sums(0);
     if (tid == 0) info->tails[0] = tail;
@@ -669,6 +708,7 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
     while (i < rmax) {
       if (fixed ? i >= rt : (i >= 1 && tail <= delta2)) break;
       bool rot = false;
+      T* pv = lva;
       if (i < k1) {
         T best = lowest_value<T>();
         int bi = 0x7fffffff;
@@ -681,82 +721,123 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
         int j0;
         block_argmax(best, bi, redt, redi, cmax, j0);
         if (cmax > T(0)) {
-          // v = T^T T e_j0 / ||.||, then q power iterations v <- T^T T v / ||.||
-          for (int p = i + tid; p < k1; p += nt) lw[p] = Rt[j0 * n + p];
+          // v ~ T^T T e_j0, then q power iterations v <- T^T T v; v is kept
+          // unnormalized (the rotation angles depend on its direction only)
+          // and the next product takes the scale 1 / ||v||
+          for (int p = i + tid; p < k1; p += nt) lw[p] = R_(p, j0);
           __syncthreads();
-          rt_mv(lv, lw, i);
-          const T nv = sumsq(lv, i);
+          const T nv = rt_mv(lva, lw, i);
           rot = nv > T(0);
           if (rot) {
-            const T inv = T(1) / sqrt(nv);
-            for (int c = i + tid; c < n; c += nt) lv[c] *= inv;
-            __syncthreads();
+            T* pt = lvb;
+            T scale = T(1) / sqrt(nv);
             for (int it = 0; it < q; ++it) {
-              r_mv(lw, lv, i);
-              rt_mv(lt, lw, i);
-              const T nw = sumsq(lt, i);
+              r_mv(lw, pv, scale, i);
+              const T nw = rt_mv(pt, lw, i);
               if (!(nw > T(0))) break;  // T^T T v = 0: keep v
-              const T iw = T(1) / sqrt(nw);
-              for (int c = i + tid; c < n; c += nt) lv[c] = lt[c] * iw;
-              __syncthreads();
+              T* t = pv;
+              pv = pt;
+              pt = t;
+              scale = T(1) / sqrt(nw);
             }
           }
         }
       }
       if (rot) {
         // column rotations: (c_c, s_c) rotates (v_c, ||v(c+1:)||) onto
-        // (||v(c:)||, 0); the last pair takes v_{n-1} itself
-        for (int c = i + tid; c < n; c += nt) {
-          double s = 0.0;
-          for (int t = n - 1; t >= c; --t) s += (double)lv[t] * (double)lv[t];
-          lq[c] = s;
+        // (||v(c:)||, 0); the last pair takes v_{n-1} itself.  Suffix sums of
+        // squares by one warp: a serial run per lane, then a shuffle scan.
+        if (warp == 0) {
+          const int m = n - i, per = (m + 31) / 32;
+          const int b0 = i + lane * per, b1 = min(b0 + per, n);
+          double loc = 0.0;
+          for (int t = b1 - 1; t >= b0; --t) loc += (double)pv[t] * (double)pv[t];
+          double suf = loc;  // sum over lanes >= lane
+          for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_down_sync(full, suf, o);
+            if (lane + o < 32) suf += y;
+          }
+          double acc = __shfl_down_sync(full, suf, 1);
+          if (lane == 31) acc = 0.0;
+          for (int t = b1 - 1; t >= b0; --t) {
+            acc += (double)pv[t] * (double)pv[t];
+            lq[t] = acc;
+          }
         }
         __syncthreads();
         for (int c = i + tid; c < n - 1; c += nt) {
           const double h = sqrt(lq[c]);
-          const double b = c == n - 2 ? (double)lv[n - 1] : sqrt(lq[c + 1]);
-          lcs[c] = h > 0.0 ? (T)((double)lv[c] / h) : T(1);
+          const double b = c == n - 2 ? (double)pv[n - 1] : sqrt(lq[c + 1]);
+          lcs[c] = h > 0.0 ? (T)((double)pv[c] / h) : T(1);
           lsn[c] = h > 0.0 ? (T)(b / h) : T(0);
         }
         __syncthreads();
-        if (tid < half) {
-          for (int p = tid; p < k1; p += half) {
-            T carry = Rt[(n - 1) * n + p];
-            ldg[p] = Rt[p * n + p];
-            for (int c = n - 2; c >= i; --c) {
-              const T a = Rt[c * n + p], cs = lcs[c], sn = lsn[c];
-              const T na = cs * a + sn * carry;
-              if (c == p) {
-                lx[p] = carry;
-                ly[p] = na;
+        // threads [0, half): rows of R; [half, nt): rows of V
+        const bool onR = tid < half;
+        T* M = onR ? Rb : Vb;
+        const int msp = onR ? rsp : 1, msc = onR ? rsc : vsc;
+        const int rows = onR ? k1 : n;
+        for (int p = onR ? tid : tid - half; p < rows; p += half) {
+          T* row = M + (size_t)p * msp;  // entry c at row[c * msc]
+          if (onR) ldg[p] = row[p * msc];
+          T carry = row[(n - 1) * msc];
+          for (int c0 = n - 2; c0 >= i; c0 -= 8) {
+            T a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = c0 - u >= i ? row[(c0 - u) * msc] : T(0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int c = c0 - u;
+              if (c >= i) {
+                const T cs = lcs[c], sn = lsn[c];
+                const T na = cs * a[u] + sn * carry;
+                if (onR && c == p) ly[p] = na;
+                row[(c + 1) * msc] = -sn * a[u] + cs * carry;
+                carry = na;
               }
-              Rt[(c + 1) * n + p] = -sn * a + cs * carry;
-              carry = na;
             }
-            Rt[i * n + p] = carry;
           }
-        } else {
-          for (int p = tid - half; p < n; p += nt - half) {
-            T carry = Vt[(n - 1) * n + p];
-            for (int c = n - 2; c >= i; --c) {
-              const T a = Vt[c * n + p], cs = lcs[c], sn = lsn[c];
-              Vt[(c + 1) * n + p] = -sn * a + cs * carry;
-              carry = cs * a + sn * carry;
-            }
-            Vt[i * n + p] = carry;
-          }
+          row[i * msc] = carry;
         }
         __syncthreads();
         // row rotations on (p, p+1), p from P0 down to i (rows below k1 only)
         const int P0 = min(n - 2, k1 - 2);
         if (P0 >= i) {
           const double rc0 = P0 + 1 <= n - 2 ? (double)ly[P0 + 1] : (double)ldg[P0 + 1];
-          if (tid == 0) {
-            double acc = rc0 * rc0;
-            for (int p = P0; p >= i; --p) {
+          if (warp == 0) {
+            // rho_p^2 = a_p x + b_p applied to x = rho_{p+1}^2, from x = rc0^2;
+            // lane L composes the maps of its run of p (descending), then an
+            // exclusive shuffle scan gives the value entering the run
+            const int m = P0 - i + 1, per = (m + 31) / 32;
+            const int t0 = lane * per, t1 = min(t0 + per, m);  // t = P0 - p
+            double ca = 1.0, cb = 0.0;  // composed map x -> ca x + cb
+            for (int t = t0; t < t1; ++t) {
+              const int p = P0 - t;
               const double sp = (double)lsn[p], yp = (double)ly[p];
-              acc = fma(yp, yp, sp * sp * acc);
-              lq[p] = acc;
+              const double a = sp * sp, b = yp * yp;
+              cb = fma(a, cb, b);
+              ca = a * ca;
+            }
+            // inclusive scan over lanes: G_L = F_L o ... o F_0
+            double ga = ca, gb = cb;
+            for (int o = 1; o < 32; o <<= 1) {
+              const double pa = __shfl_up_sync(full, ga, o), pb = __shfl_up_sync(full, gb, o);
+              if (lane >= o) {
+                gb = fma(ga, pb, gb);
+                ga = ga * pa;
+              }
+            }
+            double ea = __shfl_up_sync(full, ga, 1), eb = __shfl_up_sync(full, gb, 1);
+            if (lane == 0) {
+              ea = 1.0;
+              eb = 0.0;
+            }
+            double x = fma(ea, rc0 * rc0, eb);
+            for (int t = t0; t < t1; ++t) {
+              const int p = P0 - t;
+              const double sp = (double)lsn[p], yp = (double)ly[p];
+              x = fma(sp * sp, x, yp * yp);
+              lq[p] = x;
             }
           }
           __syncthreads();
@@ -769,15 +850,24 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
           }
           __syncthreads();
           for (int c = i + tid; c < n; c += nt) {
-            T* col = Rt + (size_t)c * n;
-            T carry = col[P0 + 1];
-            for (int p = P0; p >= i; --p) {
-              const T a = col[p], cr = lcr[p], sr = lsr[p];
-              col[p + 1] = -sr * a + cr * carry;
-              carry = cr * a + sr * carry;
+            T* col = Rb + (size_t)c * rsc;  // entry p at col[p * rsp]
+            T carry = col[(P0 + 1) * rsp];
+            for (int p0 = P0; p0 >= i; p0 -= 8) {
+              T a[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) a[u] = p0 - u >= i ? col[(p0 - u) * rsp] : T(0);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int p = p0 - u;
+                if (p >= i) {
+                  const T cr = lcr[p], sr = lsr[p];
+                  col[(p + 1) * rsp] = -sr * a[u] + cr * carry;
+                  carry = cr * a[u] + sr * carry;
+                }
+              }
             }
-            col[i] = carry;
-            for (int p = max(c + 1, i); p < k1; ++p) col[p] = T(0);
+            col[i * rsp] = carry;
+            for (int p = max(c + 1, i); p < k1; ++p) col[p * rsp] = T(0);
           }
           __syncthreads();
         }
@@ -793,9 +883,9 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
       T z = T(0);
       if (c < r) {
         if (prm.Gw)
-          for (int k = row; k < n; ++k) z += Ti[row * n + k] * Vt[c * n + k];
+          for (int k = row; k < n; ++k) z += Ti[row * n + k] * Vb[k + c * vsc];
         else
-          z = Vt[c * n + row];
+          z = Vb[row + c * vsc];
       }
       Z[(size_t)row * ldz + c] = (ZT)z;
     }
@@ -805,6 +895,7 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
       info->nsteps = r;
       info->s1 = s1;
       info->tail = tail;
+      if (prm.lurv_smem) info->status |= 4 * prm.lurv_smem;
     }
     return;
   }
@@ -1011,8 +1102,40 @@ cudaError_t launch_small(const double* G, SmallParams prm, void* Z, int ldz, voi
   T* work = (T*)ws;
   size_t off = ((size_t)(4 * n * n + 2 * n) * sizeof(T) + 255) & ~(size_t)255;
   int* iwork = (int*)((char*)ws + off);
+  size_t dyn = 0;
+  prm.lurv_smem = 0;
+  if (prm.mode == SM_LURV) {
+    // R (and V) in shared memory when they fit beside the kernel's static
+    // arrays; the opt-in limit is raised once
+    static int room = -1;
+    if (room < 0) {
+      int dev = 0, optin = 0;
+      cudaFuncAttributes fa;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+              cudaSuccess ||
+          cudaFuncGetAttributes(&fa, small_kernel<T, ZT>) != cudaSuccess)
+        return cudaGetLastError();
+      room = max(0, optin - (int)fa.sharedSizeBytes);
+      if (room > 0 && cudaFuncSetAttribute(small_kernel<T, ZT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           room) != cudaSuccess) {
+        (void)cudaGetLastError();
+        room = 0;
+      }
+    }
+    // R, then V, each n x (n | 1)
+    const size_t need = (size_t)n * (n | 1) * sizeof(T);
+    if (2 * need <= (size_t)room) {
+      dyn = 2 * need;
+      prm.lurv_smem = 2;
+    } else if (need <= (size_t)room) {
+      dyn = need;
+      prm.lurv_smem = 1;
+    }
+  }
   count_launch();
-  small_kernel<T, ZT><<<1, NT, 0, st>>>(G, prm, work, iwork, (ZT*)Z, ldz, info);
+  small_kernel<T, ZT><<<1, NT, dyn, st>>>(G, prm, work, iwork, (ZT*)Z, ldz, info);
   return cudaGetLastError();
 }
 
