@@ -332,6 +332,15 @@ def run_ours(args, wl, rank, world):
 
     # accuracy of this run (untimed): error equality, RSE, sampled diff vs the oracle
     acc = accuracy(tu, torch, A, res, args.workload)
+    # the same sweep once more (untimed) with every non-tight step's error
+    # summed directly from its residual: same ranks and cores, exact tails
+    rd = tu.tt_utv(A, direct_tails=True, **kw)
+    err2, normA2 = tu.tt_rse(A.to(rd.cores[0].dtype), rd.cores)
+    acc["direct_tails"] = {
+        "same_cores": bool(all(torch.equal(a, b) for a, b in zip(rd.cores, res.cores))),
+        "tails_over_err2": sum(rd.tail_sq) / err2 if err2 > 0 else None,
+        "tails_rel": [float(t) / normA2 for t in rd.tail_sq]}
+    del rd
 
     # end to end through the C ABI with host buffers
     e2e = None

@@ -130,6 +130,16 @@ typedef struct {
                                in [0, 64], default 8 */
   int32_t lhat;             /* tt_lhat: the kept middle block of TT-ULV right-to-left (the
                                appendix's Alg. 4), default TT_LHAT_FULL */
+  int32_t direct_tails;     /* 0 or 1 (default 0).  1: every step that would report
+                               ||C||^2 - ||carry||^2 (exact or sketched, tolerance not tight, not
+                               an identity sketch) reports instead its error ||E_k||_F^2 (the
+                               summands of Thm 3.1's equality) summed directly from the residual
+                               E_k = C - carry Z_1^T (TT-URV; TT-ULV: C - Z_1 carry), formed slab
+                               by slab of C's rows and summed in FP64: one more pass over the
+                               unfolding and a product per slab.  The difference of two squared
+                               norms carries the products' rounding (~1e-6 of ||C||^2 on the
+                               tensor cores), the size of a sketched step's range miss.  Ranks
+                               and cores are unchanged; ignored with TT_LHAT_L11. */
 } tt_opts;
 
 /* Middle block kept by TT-ULV right-to-left (appendix, Alg. 4), whose inner

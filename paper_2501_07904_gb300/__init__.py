@@ -66,7 +66,8 @@ class tt_opts(ctypes.Structure):
                 ("orth_precision", ctypes.c_int32), ("reverse", ctypes.c_int32),
                 ("phase_ms", ctypes.POINTER(ctypes.c_double)),
                 ("power_iters", ctypes.c_int32), ("inner", ctypes.c_int32),
-                ("usvp_iters", ctypes.c_int32), ("lhat", ctypes.c_int32)]
+                ("usvp_iters", ctypes.c_int32), ("lhat", ctypes.c_int32),
+                ("direct_tails", ctypes.c_int32)]
 
 
 class tt_result(ctypes.Structure):
@@ -251,7 +252,7 @@ class TTResult:
 
 def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small, weights, stream,
            timing=False, orth="auto", reverse=False, power_iters=0, dims=None, shard=None,
-           inner="qlp", usvp_iters=8, lhat="full"):
+           inner="qlp", usvp_iters=8, lhat="full", direct_tails=False):
     if not isinstance(A, torch.Tensor):
         raise TypeError("A must be a torch.Tensor")
     if A.dtype not in (torch.float32, torch.float64):
@@ -276,6 +277,7 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
     opts.inner = INNER[inner]
     opts.usvp_iters = int(usvp_iters)
     opts.lhat = {"full": 0, "l11": 1}[lhat]
+    opts.direct_tails = 1 if direct_tails else 0
     wbuf = None
     if weights is not None:
         wbuf = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
@@ -318,7 +320,7 @@ def _sweep(fn, A, eps, ranks, extra, precision, seed, oversample, l_full, small,
 def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, oversample=16,
            l_full=256, small="auto", weights=None, stream=None, timing=False, orth="auto",
            reverse=False, direction=None, power_iters=0, inner="qlp", usvp_iters=8,
-           lhat="full"):
+           lhat="full", direct_tails=False):
     """TT-URV right-to-left (Alg. 3) or TT-ULV left-to-right (Alg. 1/2).
 
     Give ``eps`` (prescribed relative accuracy, Alg. 2) or ``ranks``
@@ -336,7 +338,10 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
     vector.
     ``lhat="l11"`` with variant "ULV" and direction "RL" runs the appendix's
     Alg. 4 as printed: the carry keeps L_11 alone and the default weights are
-    1/(d-1).
+    1/(d-1).  ``direct_tails`` makes every non-tight step report its error
+    ||E_k||^2 summed directly from its residual (one more pass over the
+    unfolding) instead of as ||C||^2 - ||carry||^2; ranks and cores are the
+    same.
     """
     if (eps is None) == (ranks is None):
         raise ValueError("give exactly one of eps or ranks")
@@ -345,7 +350,7 @@ def tt_utv(A, eps=None, ranks=None, variant="URV", precision="fp32", seed=0, ove
     v = ({"URV": TT_URV, "ULV": TT_ULV}[variant], {"RL": TT_RL, "LR": TT_LR}[direction])
     return _sweep(lib().tt_utv, A, eps, ranks, v, precision, seed, oversample, l_full, small,
                   weights, stream, timing, orth, reverse, power_iters, inner=inner,
-                  usvp_iters=usvp_iters, lhat=lhat)
+                  usvp_iters=usvp_iters, lhat=lhat, direct_tails=direct_tails)
 
 
 class _DevBuf:
@@ -437,17 +442,19 @@ def slab(A, nranks, rank, direction="RL"):
 
 def tt_utv_sharded(A_local, dims, comm, eps=None, ranks=None, variant="URV", direction=None,
                    precision="fp32", seed=0, oversample=16, l_full=256, small="auto", weights=None,
-                   stream=None, timing=False, orth="auto", power_iters=0):
+                   stream=None, timing=False, orth="auto", power_iters=0, direct_tails=False):
     """tt_utv of a tensor partitioned over ranks (one GPU each): A_local is this
     rank's slab (see slab()), dims the whole tensor's mode sizes, comm a
-    ShardComm.  Every rank returns the whole result."""
+    ShardComm.  Every rank returns the whole result (with ``direct_tails`` a
+    sketched step's residual is summed per slab and all-reduced)."""
     if (eps is None) == (ranks is None):
         raise ValueError("give exactly one of eps or ranks")
     if direction is None:
         direction = "RL" if variant == "URV" else "LR"
     v = ({"URV": TT_URV, "ULV": TT_ULV}[variant], {"RL": TT_RL, "LR": TT_LR}[direction])
     return _sweep(lib().tt_utv_sharded, A_local, eps, ranks, v, precision, seed, oversample, l_full,
-                  small, weights, stream, timing, orth, False, power_iters, dims=dims, shard=comm)
+                  small, weights, stream, timing, orth, False, power_iters, dims=dims, shard=comm,
+                  direct_tails=direct_tails)
 
 
 def tt_svd(A, eps=None, ranks=None, direction="LR", precision="fp32", l_full=256, small="auto",

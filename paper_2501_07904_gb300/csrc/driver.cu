@@ -367,6 +367,14 @@ bool host_pointer(const void* p) {
   return pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeUnregistered;
 }
 
+// Rows of C per slab of the direct residual: about 64 MiB of residual at a
+// time, a multiple of 4 rows (slab offsets stay 16-byte aligned for TMA).
+int64_t residual_slab(int64_t rows, int64_t cols, size_t elem) {
+  int64_t per = (int64_t)((64ull << 20) / ((size_t)std::max<int64_t>(cols, 1) * elem));
+  per = std::max<int64_t>(4, per & ~(int64_t)3);
+  return std::max<int64_t>(1, std::min<int64_t>(rows, per));
+}
+
 template <typename W>
 tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* dims, double eps,
                     const int64_t* fixed, SweepCfg cfg, const tt_opts& o, Alloc& al,
@@ -937,6 +945,8 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         if (l >= no_g && r < l)  // the identity sketch's residual product
           wsz = std::max(wsz, cfg.urv ? mm_ws<W>(mm, m, l, r, false) : mm_ws<W>(mm, n, l, r, false));
       }
+      if (o.direct_tails)  // the residual product of one slab of rows
+        wsz = std::max(wsz, mm_ws<W>(mm, residual_slab(m, n, sizeof(W)), n, r, false));
       if (sq_pass) wsz = std::max(wsz, ttk::sumsq_ws_bytes(crow * ccol));
       if (wsz > ws_bytes) {
         TT_ALLOC(ws_extra, wsz);
@@ -1006,6 +1016,41 @@ tt_status run_sweep(const void* A_in, int32_t dtype_in, int d, const int64_t* di
         TT_CK(mm_run<W>(mm, {Wm, l, true}, {Zp, ldz, true}, m, r, l, core.as<W>(), r, nullptr, false,
                         nullptr, ws.p, precise, true, true, false), "core W Z1");
       tm.end();
+    }
+    // Opt-in (tt_opts.direct_tails): the step's error ||E_k||^2 summed
+    // directly from its residual, URV E = C - carry Z1^T, ULV E = C - Z1
+    // carry (the core is Z1^T, resp. Z1), formed slab by slab of C's rows
+    // and summed in FP64 -- instead of ||C||^2 - ||carry||^2, whose
+    // tensor-core rounding (~1e-6 of ||C||^2) is the size of a sketched
+    // step's range miss.  Exact and sketched steps alike (identity sketches
+    // and tight steps already report direct errors).  Ranks and cores are
+    // unchanged.  On a partitioned sweep every rank sums its slab and the
+    // sums are all-reduced.
+    if (o.direct_tails && !has_direct[s] && !cfg.l11 && ftail[s] < 0.0) {
+      const int64_t slab = residual_slab(m, n, sizeof(W));
+      const size_t pbytes = align256(ttk::diff_sumsq_parts_bytes());
+      Buf trail(&al);
+      TT_ALLOC(trail, align256((size_t)slab * n * sizeof(W)) + pbytes + 2 * sizeof(double));
+      W* Pm = trail.as<W>();
+      double* part = (double*)((char*)trail.p + align256((size_t)slab * n * sizeof(W)));
+      double* pair = (double*)((char*)part + pbytes);
+      for (int64_t a = 0; a < m; a += slab) {
+        const int64_t h = std::min(slab, m - a);
+        if (cfg.urv)
+          TT_CK(mm_run<W>(mm, {carry.as<W>() + a * r, r, true}, {core.as<W>(), n, true}, h, n, r, Pm,
+                          n, nullptr, false, nullptr, ws.p, precise, true, true, false),
+                "step residual: carry Z1^T");
+        else
+          TT_CK(mm_run<W>(mm, {core.as<W>() + a * r, r, true}, {carry.as<W>(), n, true}, h, n, r, Pm,
+                          n, nullptr, false, nullptr, ws.p, precise, true, true, false),
+                "step residual: Z1 carry");
+        TT_CK(ttk::diff_sumsq(C + a * n, Pm, W64, h * n, part, a == 0, st), "step residual");
+      }
+      TT_CK(ttk::sum_pairs(part, pair, st), "step residual");
+      TT_CK(cudaMemcpyAsync(d_tdirect + s, pair, sizeof(double), cudaMemcpyDeviceToDevice, st),
+            "step residual");
+      TT_RED(d_tdirect + s, 1);
+      has_direct[s] = 1;
     }
     if (sq_pass)
       TT_CK(ttk::sumsq(carry.p, W64, crow * ccol, d_carry2 + s, ws.p, st), "carry sum of squares");
@@ -1100,6 +1145,7 @@ tt_status validate(const void* A, int32_t dtype, int32_t d, const int64_t* dims,
   if (o.inner != TT_INNER_QLP && o.inner != TT_INNER_USVP && o.inner != TT_INNER_LURV)
     return fail(TT_EINVAL, "bad inner factor");
   if (o.usvp_iters < 0 || o.usvp_iters > 64) return fail(TT_EINVAL, "usvp_iters must be in [0, 64]");
+  if (o.direct_tails != 0 && o.direct_tails != 1) return fail(TT_EINVAL, "direct_tails must be 0 or 1");
   if (o.lhat != TT_LHAT_FULL && o.lhat != TT_LHAT_L11) return fail(TT_EINVAL, "bad lhat");
   if (o.lhat == TT_LHAT_L11 && o.inner != TT_INNER_QLP)
     return fail(TT_EINVAL, "the L_11-only carry needs the pivoted QLP inner factor");

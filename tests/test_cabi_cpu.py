@@ -172,6 +172,15 @@ def test_power_iters_option(L):
         assert _call(L, opts=ctypes.byref(o)) == 1
 
 
+def test_direct_tails_option(L):
+    o = tu.tt_opts()
+    L.tt_opts_default(ctypes.byref(o))
+    assert o.direct_tails == 0
+    for bad in (-1, 2):
+        o.direct_tails = bad
+        assert _call(L, opts=ctypes.byref(o)) == 1
+
+
 def test_binding_structs_match_the_header(tmp_path):
     # every field offset and the size of tt_opts and tt_result, from the C
     # compiler's view of include/ttutv.h, against the ctypes declarations
