@@ -1107,12 +1107,15 @@ cudaError_t launch_small(const double* G, SmallParams prm, void* Z, int ldz, voi
   if (prm.mode == SM_LURV) {
     // R (and V) in shared memory when they fit beside the kernel's static
     // arrays; the opt-in limit is raised once
-    static int room = -1;
+    // (per device: each device holds its own copy of the kernel's attributes)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+    static int room_p1[64];  // 1 + the room found on each device; 0: not yet
+    int room = (dev >= 0 && dev < 64) ? room_p1[dev] - 1 : -1;
     if (room < 0) {
-      int dev = 0, optin = 0;
+      int optin = 0;
       cudaFuncAttributes fa;
-      if (cudaGetDevice(&dev) != cudaSuccess ||
-          cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
               cudaSuccess ||
           cudaFuncGetAttributes(&fa, small_kernel<T, ZT>) != cudaSuccess)
         return cudaGetLastError();
@@ -1123,6 +1126,7 @@ cudaError_t launch_small(const double* G, SmallParams prm, void* Z, int ldz, voi
         (void)cudaGetLastError();
         room = 0;
       }
+      if (dev >= 0 && dev < 64) room_p1[dev] = room + 1;
     }
     // R, then V, each n x (n | 1)
     const size_t need = (size_t)n * (n | 1) * sizeof(T);
