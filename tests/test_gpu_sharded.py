@@ -149,3 +149,24 @@ def test_sharded_one_rank_is_tt_utv(tu):
     assert res.ranks == whole.ranks
     for a, b in zip(res.cores, whole.cores):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("variant", ["URV", "ULV"])
+def test_sharded_direct_tails(tu, variant):
+    # noise 1e-3 at eps 1e-2: no step is tight, so every step but an identity
+    # sketch sums its residual per slab and all-reduces it
+    dims = (16, 29, 41, 24) if variant == "URV" else (24, 41, 29, 16)
+    ranks = (1, 5, 7, 4, 1) if variant == "URV" else (1, 4, 7, 5, 1)
+    A = synth.gaussian_tt(dims, ranks, 1e-3, seed=63, dtype=np.float32)
+    kw = dict(eps=1e-2, variant=variant, precision="mixed", l_full=24, direct_tails=True)
+    A_t = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    whole = tu.tt_utv(A_t, **kw)
+    outs = run_sharded(tu, A, 2, **kw)
+    t0 = outs[0][0].tail_sq
+    for res, _ in outs:
+        assert res.ranks == whole.ranks
+        assert res.tail_sq == t0                   # the all-reduced sums are the same bits
+        err2, normA2 = tu.tt_rse(A_t, res.cores)
+        assert abs(sum(res.tail_sq) - err2) <= 0.03 * err2, (res.tail_sq, err2)
+        for a, b in zip(res.tail_sq, whole.tail_sq):
+            assert abs(a - b) <= 0.02 * b + 1e-9 * normA2, (res.tail_sq, whole.tail_sq)
