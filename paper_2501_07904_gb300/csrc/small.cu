@@ -174,7 +174,7 @@ __device__ int cholesky_drop(T* A, int n, int* keep, double tol_rel, T* redt, in
 }
 
 template <typename T, typename ZT>
-__global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G, SmallParams prm,
+__global__ void __launch_bounds__(NT, 1) small_kernel(const double* __restrict__ G, SmallParams prm,
                                                    T* __restrict__ work, int* __restrict__ iwork,
                                                    ZT* __restrict__ Z, int ldz,
                                                    StepInfo* __restrict__ info) {
@@ -666,18 +666,29 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
       }
       return block_sum(part, redd);
     };
-    // dst[c] = sum_p R(p, c) src[p] over rows [i0, k1), columns c >= i0;
-    // returns ||dst||^2 (every thread, the warps' partials summed in one order)
+    // dst[c] = sum_p R(p, c) src[p] over rows [i0, min(c + 1, k1)), columns
+    // c >= i0: four threads per column, each a quarter of the rows, combined
+    // by shuffles; returns ||dst||^2 (every thread, the warps' partial sums
+    // added in one order)
     auto rt_mv = [&](T* dst, const T* src, int i0) -> T {
+      const int cols = n - i0, qr = (k1 - i0 + 3) >> 2;
       T part = T(0);
-      for (int c = i0 + warp; c < n; c += nwarps) {
+      for (int b0 = 0; b0 < 4 * cols; b0 += nt) {
+        const int t = b0 + tid, pc = t >> 2, q4 = t & 3;
         T acc = T(0);
-        const int pe = min(c + 1, k1);
-        for (int p = i0 + lane; p < pe; p += 32) acc += R_(p, c) * src[p];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(full, acc, o);
-        if (lane == 0) dst[c] = acc;
-        part += acc * acc;
+        if (pc < cols) {
+          const int c = i0 + pc;
+          const int p0 = i0 + q4 * qr, p1 = min(min(c + 1, k1), p0 + qr);
+          for (int p = p0; p < p1; ++p) acc += R_(p, c) * src[p];
+        }
+        acc += __shfl_xor_sync(full, acc, 1);
+        acc += __shfl_xor_sync(full, acc, 2);
+        if (pc < cols && q4 == 0) {
+          dst[i0 + pc] = acc;
+          part += acc * acc;
+        }
       }
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(full, part, o);
       if (lane == 0) wpart[warp] = part;
       __syncthreads();
       T s = T(0);
@@ -685,20 +696,21 @@ __global__ void __launch_bounds__(NT) small_kernel(const double* __restrict__ G,
       return s;
     };
     // dst[p] = scale * sum_c R(p, c) src[c] over rows [i0, k1), columns
-    // c >= i0 (the zeros below the diagonal included: a warp reads one column
-    // at a time); four partial sums break the dependency chain
+    // c >= p: four threads per row, each a quarter of the columns, combined
+    // by shuffles
     auto r_mv = [&](T* dst, const T* src, T scale, int i0) {
-      for (int p = i0 + tid; p < k1; p += nt) {
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        int c = i0;
-        for (; c + 3 < n; c += 4) {
-          a0 += R_(p, c) * src[c];
-          a1 += R_(p, c + 1) * src[c + 1];
-          a2 += R_(p, c + 2) * src[c + 2];
-          a3 += R_(p, c + 3) * src[c + 3];
+      const int rows = k1 - i0, qc = (n - i0 + 3) >> 2;
+      for (int b0 = 0; b0 < 4 * rows; b0 += nt) {
+        const int t = b0 + tid, pr = t >> 2, q4 = t & 3;
+        T acc = T(0);
+        if (pr < rows) {
+          const int p = i0 + pr;
+          const int c0 = i0 + q4 * qc, c1 = min(n, c0 + qc);
+          for (int c = max(c0, p); c < c1; ++c) acc += R_(p, c) * src[c];
         }
-        for (; c < n; ++c) a0 += R_(p, c) * src[c];
-        dst[p] = ((a0 + a1) + (a2 + a3)) * scale;
+        acc += __shfl_xor_sync(full, acc, 1);
+        acc += __shfl_xor_sync(full, acc, 2);
+        if (pr < rows && q4 == 0) dst[i0 + pr] = acc * scale;
       }
       __syncthreads();
     };
